@@ -1,0 +1,424 @@
+/*
+ * cdoracle.c -- plain, slow FP64 CPU oracle for the Cholesky-decomposed ERI path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the benchmark's
+ * CPU-baseline leg may load this file's library.  It shares no code, header,
+ * table or constant with the CUDA path.
+ *
+ * What it computes, each piece written out from its definition:
+ *   - Boys function F_m(T) (series + downward recursion; asymptotic form and
+ *     upward recursion for large T) -- the standard textbook construction
+ *     (Helgaker, Jorgensen, Olsen, "Molecular Electronic-Structure Theory",
+ *     sec. 9.8).
+ *   - Primitive Cartesian ERIs by the four-centre Obara-Saika recurrence
+ *     (Obara & Saika, J. Chem. Phys. 84, 3963 (1986)), recursing on the first
+ *     centre that still carries angular momentum.
+ *   - Contracted, normalised s and Cartesian p functions.
+ *   - Schwarz screening at shell-pair level (the paper only says integrals are
+ *     prescreened, Sec. 1).
+ *   - Fully pivoted, threshold-truncated Cholesky decomposition of the ERI
+ *     matrix over composite pair indices (Sec. 2: D^1, argmax pivot, Eq. (subtr),
+ *     Eq. (diag), stop when max D < tau), with a forced-pivot mode.
+ *   - The exact ERI matrix over a list of pair indices (for J/K from exact
+ *     integrals and for the dense checks in the tests).
+ *
+ * Pair index convention: functions are numbered shell by shell (s; then p as
+ * x, y, z); a composite pair (mu, nu) with mu >= nu has packed index
+ * mu*(mu+1)/2 + nu.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------- */
+/* Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt, for m = 0..mmax.     */
+/* For T < 35: F_mmax from the convergent series                              */
+/*   F_m(T) = exp(-T) sum_{i>=0} (2T)^i / [(2m+1)(2m+3)...(2m+2i+1)]          */
+/* then the downward recursion F_m = (2T F_{m+1} + exp(-T)) / (2m+1).         */
+/* For T >= 35: F_0 = (1/2) sqrt(pi/T) (erf(sqrt T) = 1 to double precision   */
+/* there) and the upward recursion F_{m+1} = ((2m+1) F_m - exp(-T)) / (2T).   */
+/* ------------------------------------------------------------------------- */
+void or_boys(int mmax, double T, double* F)
+{
+    double emT = exp(-T);
+    if (T < 35.0) {
+        double term = 1.0 / (2 * mmax + 1), sum = term;
+        for (int i = 1; i < 2000; ++i) {
+            term *= 2.0 * T / (2 * mmax + 2 * i + 1);
+            sum += term;
+            if (term < 1e-18 * sum) break;
+        }
+        F[mmax] = emT * sum;
+        for (int m = mmax - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + emT) / (2 * m + 1);
+    } else {
+        F[0] = 0.5 * sqrt(OR_PI / T);
+        for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - emT) / (2.0 * T);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Obara-Saika recurrence for one primitive quartet.                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double PA[3], PB[3], QC[3], QD[3], WP[3], WQ[3];
+    double o2p, o2q, o2pq;   /* 1/(2p), 1/(2q), 1/(2(p+q)) */
+    double rp, rq;           /* rho/p, rho/q, rho = pq/(p+q) */
+    double base;             /* 2 pi^{5/2} / (p q sqrt(p+q)) exp(-mu_ab AB^2) exp(-mu_cd CD^2) */
+    double F[32];
+} osq_t;
+
+static int lsum(const int* a) { return a[0] + a[1] + a[2]; }
+
+static double os_rec(const osq_t* s, const int* a, const int* b, const int* c, const int* d, int m)
+{
+    int la = lsum(a), lb = lsum(b), lc = lsum(c), ld = lsum(d);
+    if (la + lb + lc + ld == 0) return s->base * s->F[m];
+    int a1[3], b1[3], c1[3], d1[3], t[3];
+    memcpy(a1, a, sizeof a1); memcpy(b1, b, sizeof b1);
+    memcpy(c1, c, sizeof c1); memcpy(d1, d, sizeof d1);
+    double v;
+    if (la > 0 || lb > 0) {
+        /* electron 1: lower the bra centre that carries angular momentum */
+        int onA = la > 0;
+        const int* x = onA ? a : b;
+        int i = x[0] ? 0 : (x[1] ? 1 : 2);
+        const double* PX = onA ? s->PA : s->PB;
+        int* xr = onA ? a1 : b1;        /* the lowered function */
+        xr[i] -= 1;
+        const int* A = onA ? xr : a1;   /* (A B| after lowering */
+        const int* B = onA ? b1 : xr;
+        v = PX[i] * os_rec(s, A, B, c, d, m) + s->WP[i] * os_rec(s, A, B, c, d, m + 1);
+        if (A[i] > 0) {  /* N_i(a)/(2p) [ (a-1_i b|cd)^m - rho/p (a-1_i b|cd)^{m+1} ] */
+            memcpy(t, A, sizeof t); t[i] -= 1;
+            v += A[i] * s->o2p * (os_rec(s, t, B, c, d, m) - s->rp * os_rec(s, t, B, c, d, m + 1));
+        }
+        if (B[i] > 0) {
+            memcpy(t, B, sizeof t); t[i] -= 1;
+            v += B[i] * s->o2p * (os_rec(s, A, t, c, d, m) - s->rp * os_rec(s, A, t, c, d, m + 1));
+        }
+        if (c[i] > 0) {  /* N_i(c)/(2(p+q)) (ab|c-1_i d)^{m+1} */
+            memcpy(t, c, sizeof t); t[i] -= 1;
+            v += c[i] * s->o2pq * os_rec(s, A, B, t, d, m + 1);
+        }
+        if (d[i] > 0) {
+            memcpy(t, d, sizeof t); t[i] -= 1;
+            v += d[i] * s->o2pq * os_rec(s, A, B, c, t, m + 1);
+        }
+        return v;
+    }
+    /* electron 2: lower the ket centre that carries angular momentum */
+    int onC = lc > 0;
+    const int* x = onC ? c : d;
+    int i = x[0] ? 0 : (x[1] ? 1 : 2);
+    const double* QX = onC ? s->QC : s->QD;
+    int* xr = onC ? c1 : d1;
+    xr[i] -= 1;
+    const int* C = onC ? xr : c1;
+    const int* D = onC ? d1 : xr;
+    v = QX[i] * os_rec(s, a, b, C, D, m) + s->WQ[i] * os_rec(s, a, b, C, D, m + 1);
+    if (C[i] > 0) {
+        memcpy(t, C, sizeof t); t[i] -= 1;
+        v += C[i] * s->o2q * (os_rec(s, a, b, t, D, m) - s->rq * os_rec(s, a, b, t, D, m + 1));
+    }
+    if (D[i] > 0) {
+        memcpy(t, D, sizeof t); t[i] -= 1;
+        v += D[i] * s->o2q * (os_rec(s, a, b, C, t, m) - s->rq * os_rec(s, a, b, C, t, m + 1));
+    }
+    /* bra sides are already zero here (la = lb = 0), so no cross terms */
+    return v;
+}
+
+static void os_setup(osq_t* s, double ea, const double* A, double eb, const double* B,
+                     double ec, const double* C, double ed, const double* D, int L)
+{
+    double p = ea + eb, q = ec + ed, pq = p + q;
+    double P[3], Q[3], W[3], AB2 = 0, CD2 = 0, PQ2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        P[k] = (ea * A[k] + eb * B[k]) / p;
+        Q[k] = (ec * C[k] + ed * D[k]) / q;
+        W[k] = (p * P[k] + q * Q[k]) / pq;
+        AB2 += (A[k] - B[k]) * (A[k] - B[k]);
+        CD2 += (C[k] - D[k]) * (C[k] - D[k]);
+        PQ2 += (P[k] - Q[k]) * (P[k] - Q[k]);
+        s->PA[k] = P[k] - A[k]; s->PB[k] = P[k] - B[k];
+        s->QC[k] = Q[k] - C[k]; s->QD[k] = Q[k] - D[k];
+        s->WP[k] = W[k] - P[k]; s->WQ[k] = W[k] - Q[k];
+    }
+    double rho = p * q / pq;
+    s->o2p = 0.5 / p; s->o2q = 0.5 / q; s->o2pq = 0.5 / pq;
+    s->rp = rho / p; s->rq = rho / q;
+    s->base = 2.0 * pow(OR_PI, 2.5) / (p * q * sqrt(pq)) * exp(-ea * eb / p * AB2) * exp(-ec * ed / q * CD2);
+    or_boys(L, rho * PQ2, s->F);
+}
+
+/* Primitive ERI of unnormalised Cartesian Gaussians x^a... exp(-ea r^2) etc. */
+double or_eri_prim(const int* a, double ea, const double* A, const int* b, double eb, const double* B,
+                   const int* c, double ec, const double* C, const int* d, double ed, const double* D)
+{
+    osq_t s;
+    int L = lsum(a) + lsum(b) + lsum(c) + lsum(d);
+    if (L > 30) return NAN;
+    os_setup(&s, ea, A, eb, B, ec, C, ed, D, L);
+    return os_rec(&s, a, b, c, d, 0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Basis: contracted, normalised s and Cartesian p functions.                */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int nsh, nbf;
+    double* cen;     /* [nsh][3] */
+    int* l;          /* [nsh] */
+    int* nprim;      /* [nsh] */
+    int* pofs;       /* [nsh] first primitive */
+    double* exps;    /* [nprim_total] */
+    double* dcoef;   /* [nprim_total] coefficient x primitive norm x contraction norm */
+    int* bf_shell;   /* [nbf] */
+    int* bf_cart;    /* [nbf][3] */
+    int* sh_bf0;     /* [nsh] first function of the shell */
+} obasis_t;
+
+/* Normalised primitive: s -> (2a/pi)^{3/4}, Cartesian p -> (2a/pi)^{3/4} (4a)^{1/2}.
+ * Same-centre overlaps of unnormalised primitives: s.s -> (pi/(a+b))^{3/2},
+ * p_x.p_x -> (pi/(a+b))^{3/2} / (2(a+b)).  The contracted function is then
+ * rescaled to unit self-overlap. */
+void* or_basis_new(int nsh, const double* cen, const int* l, const int* nprim,
+                   const double* exps, const double* coefs)
+{
+    obasis_t* b = (obasis_t*)calloc(1, sizeof(obasis_t));
+    b->nsh = nsh;
+    int np = 0, nbf = 0;
+    for (int s = 0; s < nsh; ++s) {
+        if (l[s] < 0 || l[s] > 1 || nprim[s] <= 0) { free(b); return NULL; }
+        np += nprim[s];
+        nbf += 2 * l[s] + 1;
+    }
+    b->nbf = nbf;
+    b->cen = (double*)malloc(sizeof(double) * 3 * nsh);
+    b->l = (int*)malloc(sizeof(int) * nsh);
+    b->nprim = (int*)malloc(sizeof(int) * nsh);
+    b->pofs = (int*)malloc(sizeof(int) * nsh);
+    b->sh_bf0 = (int*)malloc(sizeof(int) * nsh);
+    b->exps = (double*)malloc(sizeof(double) * np);
+    b->dcoef = (double*)malloc(sizeof(double) * np);
+    b->bf_shell = (int*)malloc(sizeof(int) * nbf);
+    b->bf_cart = (int*)calloc(3 * nbf, sizeof(int));
+    memcpy(b->cen, cen, sizeof(double) * 3 * nsh);
+    memcpy(b->l, l, sizeof(int) * nsh);
+    memcpy(b->nprim, nprim, sizeof(int) * nsh);
+    memcpy(b->exps, exps, sizeof(double) * np);
+    int po = 0, fo = 0;
+    for (int s = 0; s < nsh; ++s) {
+        b->pofs[s] = po;
+        b->sh_bf0[s] = fo;
+        for (int k = 0; k < 2 * l[s] + 1; ++k) {
+            b->bf_shell[fo + k] = s;
+            if (l[s] == 1) b->bf_cart[3 * (fo + k) + k] = 1;
+        }
+        /* primitive norms */
+        for (int i = 0; i < nprim[s]; ++i) {
+            double a = exps[po + i];
+            double n = pow(2.0 * a / OR_PI, 0.75);
+            if (l[s] == 1) n *= sqrt(4.0 * a);
+            b->dcoef[po + i] = coefs[po + i] * n;
+        }
+        /* contraction norm: <chi|chi> over same-centre primitive overlaps */
+        double S = 0.0;
+        for (int i = 0; i < nprim[s]; ++i)
+            for (int j = 0; j < nprim[s]; ++j) {
+                double ab = exps[po + i] + exps[po + j];
+                double ov = pow(OR_PI / ab, 1.5);
+                if (l[s] == 1) ov /= 2.0 * ab;
+                S += b->dcoef[po + i] * b->dcoef[po + j] * ov;
+            }
+        for (int i = 0; i < nprim[s]; ++i) b->dcoef[po + i] /= sqrt(S);
+        po += nprim[s];
+        fo += 2 * l[s] + 1;
+    }
+    return b;
+}
+
+void or_basis_free(void* h)
+{
+    obasis_t* b = (obasis_t*)h;
+    if (!b) return;
+    free(b->cen); free(b->l); free(b->nprim); free(b->pofs); free(b->sh_bf0);
+    free(b->exps); free(b->dcoef); free(b->bf_shell); free(b->bf_cart); free(b);
+}
+
+int or_nbf(void* h) { return ((obasis_t*)h)->nbf; }
+
+/* effective coefficients (c_i x N_i / sqrt<chi|chi>) of one shell */
+void or_shell_coefs(void* h, int s, double* out)
+{
+    obasis_t* b = (obasis_t*)h;
+    for (int i = 0; i < b->nprim[s]; ++i) out[i] = b->dcoef[b->pofs[s] + i];
+}
+
+/* Contracted ERI (i j | k l) over normalised functions. */
+double or_eri(void* h, int i, int j, int k, int l)
+{
+    obasis_t* b = (obasis_t*)h;
+    int f[4] = {i, j, k, l};
+    int sh[4]; const int* cart[4]; const double* cen[4];
+    for (int t = 0; t < 4; ++t) {
+        sh[t] = b->bf_shell[f[t]];
+        cart[t] = b->bf_cart + 3 * f[t];
+        cen[t] = b->cen + 3 * sh[t];
+    }
+    int L = lsum(cart[0]) + lsum(cart[1]) + lsum(cart[2]) + lsum(cart[3]);
+    double sum = 0.0;
+    osq_t s;
+    for (int pa = 0; pa < b->nprim[sh[0]]; ++pa)
+        for (int pb = 0; pb < b->nprim[sh[1]]; ++pb)
+            for (int pc = 0; pc < b->nprim[sh[2]]; ++pc)
+                for (int pd = 0; pd < b->nprim[sh[3]]; ++pd) {
+                    int ia = b->pofs[sh[0]] + pa, ib = b->pofs[sh[1]] + pb;
+                    int ic = b->pofs[sh[2]] + pc, id = b->pofs[sh[3]] + pd;
+                    os_setup(&s, b->exps[ia], cen[0], b->exps[ib], cen[1],
+                             b->exps[ic], cen[2], b->exps[id], cen[3], L);
+                    double v = os_rec(&s, cart[0], cart[1], cart[2], cart[3], 0);
+                    sum += b->dcoef[ia] * b->dcoef[ib] * b->dcoef[ic] * b->dcoef[id] * v;
+                }
+    return sum;
+}
+
+static void unpack_pair(int64_t p, int* mu, int* nu)
+{
+    int64_t m = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) / 2.0);
+    while (m * (m + 1) / 2 > p) --m;
+    while ((m + 1) * (m + 2) / 2 <= p) ++m;
+    *mu = (int)m;
+    *nu = (int)(p - m * (m + 1) / 2);
+}
+
+/* ERI matrix A[r][c] = (rows[r] | cols[c]) for packed pair indices. */
+void or_eri_matrix(void* h, const int64_t* rows, int nr, const int64_t* cols, int nc, double* out)
+{
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int r = 0; r < nr; ++r) {
+        int i, j; unpack_pair(rows[r], &i, &j);
+        for (int c = 0; c < nc; ++c) {
+            int k, l; unpack_pair(cols[c], &k, &l);
+            out[(int64_t)r * nc + c] = or_eri(h, i, j, k, l);
+        }
+    }
+}
+
+/* Diagonal (mu nu|mu nu) over all N(N+1)/2 packed pairs. */
+void or_diag_all(void* h, double* out)
+{
+    obasis_t* b = (obasis_t*)h;
+    int64_t np = (int64_t)b->nbf * (b->nbf + 1) / 2;
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < np; ++p) {
+        int i, j; unpack_pair(p, &i, &j);
+        out[p] = or_eri(h, i, j, i, j);
+    }
+}
+
+/* Shell-pair Schwarz screening.  diag: the full packed diagonal.  A shell pair
+ * (SA >= SB) is kept iff sqrt(max over its function pairs of D * max_all D) >= thr.
+ * Writes the kept packed pair indices in increasing order; returns their count. */
+int64_t or_screen(void* h, const double* diag, double thr, int64_t* rows_out)
+{
+    obasis_t* b = (obasis_t*)h;
+    int64_t np = (int64_t)b->nbf * (b->nbf + 1) / 2;
+    double dmax = 0.0;
+    for (int64_t p = 0; p < np; ++p) if (diag[p] > dmax) dmax = diag[p];
+    /* per shell pair maximum */
+    int nsh = b->nsh;
+    double* spmax = (double*)calloc((size_t)nsh * nsh, sizeof(double));
+    for (int64_t p = 0; p < np; ++p) {
+        int i, j; unpack_pair(p, &i, &j);
+        int si = b->bf_shell[i], sj = b->bf_shell[j];
+        double* x = &spmax[(size_t)si * nsh + sj];
+        if (diag[p] > *x) *x = diag[p];
+    }
+    int64_t n = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        int i, j; unpack_pair(p, &i, &j);
+        int si = b->bf_shell[i], sj = b->bf_shell[j];
+        if (sqrt(spmax[(size_t)si * nsh + sj] * dmax) >= thr) rows_out[n++] = p;
+    }
+    free(spmax);
+    return n;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fully pivoted incomplete Cholesky decomposition (Sec. 2).                  */
+/*                                                                           */
+/*   D^1_r = (r|r)                                   over the screened rows   */
+/*   loop K = 0, 1, ...                                                       */
+/*     Dmax = max_r D_r, p = argmax (ties -> lowest row)                      */
+/*     stop when Dmax < tau                                                   */
+/*     col_r = (r|p) - sum_{J<K} L^J_r L^J_p                  Eq. (subtr)     */
+/*     L^K_r = col_r / sqrt(D_p)                              Eq. (subtr)     */
+/*     D_r  -= (L^K_r)^2                                      Eq. (diag)      */
+/*                                                                           */
+/* Forced mode (nforced >= 0): the pivot of step K is forced[K] instead of    */
+/* the argmax, for K < nforced, and the run stops after nforced steps; gap[K] */
+/* records Dmax - D_forced at each step.                                      */
+/* L is row-major [mcap][npairs].  Returns M >= 0, or                         */
+/*   -1 if M would exceed mcap, -2 if a pivot diagonal is not positive or a   */
+/*   residual diagonal is below -1e-10 * max D^1 (matrix not PSD).            */
+/* ------------------------------------------------------------------------- */
+int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
+          const int64_t* forced, int nforced, int mcap,
+          int64_t* piv_out, double* L, double* D, double* gap, double* pivD)
+{
+    int* ri = (int*)malloc(sizeof(int) * npairs);
+    int* rj = (int*)malloc(sizeof(int) * npairs);
+    for (int64_t r = 0; r < npairs; ++r) unpack_pair(rows[r], &ri[r], &rj[r]);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < npairs; ++r) D[r] = or_eri(h, ri[r], rj[r], ri[r], rj[r]);
+    double d1max = 0.0;
+    for (int64_t r = 0; r < npairs; ++r) if (D[r] > d1max) d1max = D[r];
+
+    int K = 0, status = 0;
+    for (;;) {
+        double dmax = -INFINITY; int64_t am = -1;
+        for (int64_t r = 0; r < npairs; ++r)
+            if (D[r] > dmax) { dmax = D[r]; am = r; }
+        int64_t p;
+        if (nforced >= 0) {
+            if (K >= nforced) break;
+            p = forced[K];
+            if (p < 0 || p >= npairs) { status = -3; break; }
+        } else {
+            if (!(dmax >= tau)) break;
+            p = am;
+        }
+        if (K >= mcap) { status = -1; break; }
+        if (!(D[p] > 0.0)) { status = -2; break; }
+        if (gap) gap[K] = dmax - D[p];
+        if (pivD) pivD[K] = D[p];
+        double sq = sqrt(D[p]);
+        int k = ri[p], l = rj[p];
+        double* LK = L + (int64_t)K * npairs;
+        #pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t r = 0; r < npairs; ++r) {
+            double col = or_eri(h, ri[r], rj[r], k, l);
+            for (int J = 0; J < K; ++J)
+                col -= L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + p];
+            LK[r] = col / sq;
+        }
+        int bad = 0;
+        for (int64_t r = 0; r < npairs; ++r) {
+            D[r] -= LK[r] * LK[r];
+            if (D[r] < -1e-10 * d1max) bad = 1;
+        }
+        piv_out[K] = p;
+        ++K;
+        if (bad) { status = -2; break; }
+    }
+    free(ri); free(rj);
+    return status < 0 ? status : K;
+}
