@@ -1,0 +1,170 @@
+/*
+ * cderi.h -- C ABI of the B300 Cholesky-decomposed ERI library (libcderi.so).
+ *
+ * The library computes, on one GPU (sm_103a):
+ *   1. the threshold-truncated, fully pivoted Cholesky decomposition of the
+ *      atomic-orbital electron-repulsion matrix over composite pair indices,
+ *      (mu nu|sigma rho) ~ sum_P L^P_{mu nu} L^P_{sigma rho}, with the ERI
+ *      columns computed on demand (arXiv 2609.00306, Sec. 2: diagonal D^1,
+ *      argmax pivot, Eq. (subtr), Eq. (diag), stop when max D < tau);
+ *   2. the Coulomb and exchange matrices J, K of a closed-shell density
+ *      D = 2 C C^T from those vectors (Sec. 4.1: J at O(N^2 M), K at O(O N^2 M)).
+ *
+ * Conventions used by every entry point
+ *   - Basis functions are numbered shell by shell; a Cartesian p shell holds
+ *     x, y, z in that order.  A composite pair (mu, nu), mu >= nu, has packed
+ *     index mu*(mu+1)/2 + nu.  The *rows* of a factor are the screened pairs in
+ *     increasing packed index; every Cholesky vector has one entry per row.
+ *   - Matrices are row-major.  "Host" pointers are ordinary CPU memory;
+ *     "device" pointers are CUDA global memory of the current device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Entry points that return results to host memory synchronise that stream.
+ *   - Every entry point returns CD_OK (0) or a negative CD_E* code; the message
+ *     of the last failure on the calling thread is returned by cd_last_error().
+ *     On failure nothing is allocated and output handles are set to NULL.
+ *   - Ownership: the caller owns every buffer it passes in; objects created by
+ *     the library (cd_system_t, cd_factor_t) are freed with their *_free call.
+ */
+#ifndef CDERI_H
+#define CDERI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define CD_OK        0
+#define CD_EINVAL   -1   /* malformed argument (NaN, l > 1, bad size, ...) */
+#define CD_ENOMEM   -2   /* device footprint over the budget or allocation failed */
+#define CD_ENOTPSD  -3   /* pivot diagonal <= 0 while max D >= tau, or D < -1e-10 max D^1 */
+#define CD_ETIMEOUT -4   /* a bounded device wait gave up */
+#define CD_ECUDA    -5   /* CUDA runtime error */
+
+/* ---- precision / mode flags --------------------------------------------- */
+#define CD_FP64          0  /* vectors stored FP64; J/K in FP64 */
+#define CD_VEC_FP32      1  /* after the (FP64) factorisation, vectors rounded once to FP32 */
+
+#define CD_JK_FP64       0  /* J and K contractions in FP64 */
+#define CD_JK_BF16X3     1  /* FP32 vectors, 3-way BF16 split tensor-core products, FP32 accumulate */
+#define CD_JK_DEVICE     0x100 /* flag: C_occ, J, K are device pointers (else host) */
+#define CD_JK_ONLY_J     0x200 /* flag: compute J only (K may be NULL) */
+#define CD_JK_ONLY_K     0x400 /* flag: compute K only (J may be NULL) */
+
+/* ---- inputs --------------------------------------------------------------- */
+/* Basis of contracted Cartesian Gaussian shells (all host pointers, read-only,
+ * caller-owned).  Coefficients multiply normalised primitives; the library
+ * rescales each contracted function to unit self-overlap. */
+typedef struct {
+  int32_t n_shells;
+  const double*  center;   /* [n_shells][3], bohr */
+  const int32_t* l;        /* [n_shells], 0 = s, 1 = p (x, y, z) */
+  const int32_t* nprim;    /* [n_shells], 1 .. CD_MAX_PRIM */
+  const double*  exps;     /* [sum nprim], > 0 */
+  const double*  coefs;    /* [sum nprim] */
+} cd_basis_t;
+
+#define CD_MAX_PRIM 16
+
+typedef struct {
+  double  tau;          /* decomposition threshold: stop when max residual diagonal < tau (Sec. 2) */
+  double  schwarz;      /* shell-pair screening threshold (0 keeps every pair) */
+  int32_t vec_precision;/* CD_FP64 or CD_VEC_FP32 */
+  int32_t block;        /* speculative column block b (0 = default 64; 1 .. 256) */
+  int64_t max_vectors;  /* cap on M (0 = min(rows, 16 N)); CD_ENOMEM when exceeded */
+  double  mem_budget_gb;/* device footprint cap for the factor (0 = 90% of free memory) */
+  const int64_t* forced_pivots; /* test hook: host list of pivot rows to follow (NULL = argmax) */
+  int64_t n_forced;
+} cd_opts_t;
+
+typedef struct cd_system cd_system_t;   /* basis + screened pair list on the device */
+typedef struct cd_factor cd_factor_t;   /* Cholesky basis and vectors on the device */
+
+/* ---- system (basis, screening) ------------------------------------------ */
+/* Validate and normalise the basis, compute the diagonal (mu nu|mu nu) of every
+ * pair on the GPU (kernel: ERI diagonal) and keep the shell pairs (AB) with
+ * sqrt(max_{mu nu in AB} D_{mu nu} * max D) >= schwarz.  Errors: CD_EINVAL on a
+ * malformed basis, CD_ECUDA, CD_ENOMEM. */
+int cd_system_create(const cd_basis_t* basis, double schwarz, void* stream, cd_system_t** out);
+void cd_system_free(cd_system_t* sys);
+/* n_basis, number of rows (screened pairs), number of kept shell pairs. */
+int cd_system_info(const cd_system_t* sys, int32_t* n_basis, int64_t* n_rows, int64_t* n_shell_pairs);
+/* Host copies: packed index of each row [n_rows] (may be NULL) and the row's
+ * diagonal (row|row) [n_rows] (may be NULL). */
+int cd_system_rows(const cd_system_t* sys, int64_t* packed, double* diag);
+
+/* ERI columns (kernel a, column mode): out[j][r] = (row r | row cols[j]) for
+ * j < ncols, r < n_rows.  cols: host array of row indices.  out: device
+ * pointer, row-major with leading dimension ld >= n_rows (doubles).  Runs on
+ * `stream`, asynchronous. */
+int cd_eri_columns(const cd_system_t* sys, const int64_t* cols, int32_t ncols,
+                   double* out, int64_t ld, void* stream);
+
+/* ---- factorisation -------------------------------------------------------- */
+/* Full pipeline: cd_system_create + the pivoted decomposition (Sec. 2).
+ * Blocked speculative scheme: the b largest candidates' ERI columns are computed
+ * at once (kernel a) and brought up to date by one GEMM against the existing
+ * vectors (kernel c, FP64); each step then takes the global argmax of the
+ * residual diagonal (kernel b) -- so the pivot sequence is the one of the plain
+ * recursion -- and finalises the vector from its column if it is in the block,
+ * otherwise starts a new block.  *out is NULL on failure. */
+int cd_eri_factor(const cd_basis_t* basis, const cd_opts_t* opts, void* stream, cd_factor_t** out);
+/* Same on an existing system (the factor keeps a reference; free the factor
+ * before the system). */
+int cd_eri_factor_sys(cd_system_t* sys, const cd_opts_t* opts, void* stream, cd_factor_t** out);
+void cd_factor_free(cd_factor_t* f);
+/* M, number of rows, N, residual max diagonal at exit. */
+int cd_factor_info(const cd_factor_t* f, int64_t* M, int64_t* n_rows, int32_t* n_basis, double* max_resid_diag);
+/* Host copies: pivots as row indices [M], their packed pair indices [M] (either
+ * may be NULL), gaps [M] (max D - D_pivot when each pivot was taken; 0 unless
+ * forced), and the final residual diagonal [n_rows] (may be NULL). */
+int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packed, double* gaps, double* resid_diag);
+/* Vectors: if L_host != NULL it receives [M][n_rows] doubles (converted from
+ * FP32 when stored so).  *L_dev (may be NULL) receives the device pointer of
+ * the stored array, leading dimension *ld (elements), *dtype 0 = FP64, 1 = FP32. */
+int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, int64_t* ld, int32_t* dtype);
+/* Statistics of the factorisation, 16 doubles: [0] system set-up ms (host
+ * clock), [1] ERI-column kernels ms, [2] column-update kernels ms (CUDA
+ * events), [3] pivot steps ms, [4] candidate selection ms, [5] total ms;
+ * [6] blocks, [7] ERI columns computed, [8] column-update flops (2 x rows x
+ * columns x vectors applied), [9] ERI column entries computed, [10] M;
+ * [11..15] reserved (0). */
+int cd_factor_stats(const cd_factor_t* f, double* stats16);
+/* Number of CUDA kernel launches issued by this library in this process. */
+long long cd_kernel_launches(void);
+
+/* ---- J and K (Sec. 4.1) ------------------------------------------------- */
+/* J_{mu nu} = sum_P L^P_{mu nu} sum_{sigma rho} L^P_{sigma rho} D_{sigma rho},
+ * K_{mu nu} = sum_P sum_{sigma rho} L^P_{mu sigma} D_{sigma rho} L^P_{rho nu},
+ * D = 2 C_occ C_occ^T.  C_occ [N][n_occ], J, K [N][N], row-major; host pointers
+ * unless CD_JK_DEVICE.  mode: CD_JK_FP64 or CD_JK_BF16X3 (needs FP32 vectors,
+ * converts on the fly when they are FP64).  J (kernel d): two streamed GEMVs
+ * over the vectors.  K (kernel e): B^P = L^P C_occ, K = 2 sum_P B^P B^P^T. */
+int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ,
+          double* J, double* K, int32_t mode, void* stream);
+
+/* ---- building block: exact-slice tensor-core product ------------------------ */
+/* out[i][j] = sum_k X[i][k] Y[j][k] for FP64 device matrices X [m][k] (leading
+ * dimension ldx) and Y [n][k] (ldy); out FP64 device [m][n] (ldo).  Each row is
+ * scaled by a power of two to |x| <= 1 and split into `slices` BF16 integer
+ * slices (1, 3 or 7; 8 bits each), the slice products with s + t <= slices + 1
+ * run on the tcgen05 tensor cores with exact FP32 accumulation over chunks of
+ * k, and are summed in 64-bit fixed point (error-free splitting of Ozaki et
+ * al., Numer. Algorithms 59 (2012) 95).  Error <= ~2^-(8 slices - 1) of
+ * sum_k |x||y| scaled back.  This is the kernel behind the column update
+ * (Eq. (subtr), 7 slices) and the mixed-precision exchange build (3 slices).
+ * Allocates its own scratch; synchronises `stream`.  CD_ETIMEOUT if a bounded
+ * pipeline wait gave up. */
+int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const double* Y, int64_t ldy, int64_t n,
+                    int64_t k, int32_t slices, double* out, int64_t ldo, void* stream);
+
+/* ---- errors ---------------------------------------------------------------- */
+const char* cd_last_error(void);
+/* Library version string. */
+const char* cd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDERI_H */

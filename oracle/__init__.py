@@ -199,8 +199,13 @@ class Oracle:
         return out[:n].copy()
 
     # -- Cholesky decomposition -------------------------------------------
-    def cd(self, rows, tau: float, forced=None, mcap: Optional[int] = None) -> CDResult:
+    def cd(self, rows, tau: float, forced=None, mcap: Optional[int] = None,
+           max_steps: Optional[int] = None) -> CDResult:
+        """Run the decomposition; ``max_steps`` stops after that many vectors
+        (a bounded sample of a large run; the result is then partial)."""
         rows = np.ascontiguousarray(rows, dtype=np.int64)
+        if max_steps is not None:
+            mcap = int(max_steps)
         n = rows.shape[0]
         if forced is not None:
             forced = np.ascontiguousarray(forced, dtype=np.int64)
@@ -217,7 +222,9 @@ class Oracle:
             M = self._lib.or_cd(self._h, _ptr(rows), n, float(tau),
                                 _ptr(forced) if forced is not None else None, nf, mcap,
                                 _ptr(piv), _ptr(L), _ptr(D), _ptr(gap), _ptr(pivD))
-            if M == -1 and mcap < n:
+            if M == -1 and max_steps is not None:
+                M = int(max_steps)
+            elif M == -1 and mcap < n:
                 mcap = min(n, 2 * mcap)
                 continue
             if M == -2:

@@ -1,0 +1,710 @@
+// api.cu -- the C ABI (include/cderi.h): system set-up, the blocked pivoted
+// decomposition driver, J/K, error reporting.
+#include <math.h>
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+#include "internal.cuh"
+#include "pivot.cuh"
+
+namespace cd {
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_counter() { return g_launches.load(); }
+int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st);
+int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
+             const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
+             cudaStream_t st);
+}  // namespace cd
+
+using namespace cd;
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class T>
+static int dalloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return CD_OK;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("cudaMalloc of ") + std::to_string(sizeof(T) * n) + " bytes failed: " + cudaGetErrorString(e));
+    *p = nullptr;
+    return CD_ENOMEM;
+  }
+  return CD_OK;
+}
+
+// ---------------------------------------------------------------- system ----
+static void system_release(cd_system* s) {
+  if (!s) return;
+  free_pairs(&s->all);
+  free_pairs(&s->bra);
+  cudaFree(s->diag_dev);
+  cudaFree(s->row_mu_dev);
+  cudaFree(s->row_nu_dev);
+  delete s;
+}
+
+static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStream_t st, cd_system** out) {
+  double t0 = now_ms();
+  if (!(schwarz >= 0.0) || !std::isfinite(schwarz)) { set_error("schwarz threshold must be finite and >= 0"); return CD_EINVAL; }
+  cd_system* s = new cd_system();
+  s->schwarz = schwarz;
+  int rc = validate_and_normalise(basis, &s->hb);
+  if (rc != CD_OK) { delete s; return rc; }
+  const HostBasis& hb = s->hb;
+  s->boys = boys_table_device(&rc);
+  if (rc != CD_OK) { delete s; return rc; }
+  const int nsh = hb.nsh, nbf = hb.nbf;
+  // every shell pair S1 >= S2, grouped by canonical class (ss, ps, pp)
+  std::vector<int32_t> cs1[3], cs2[3];
+  for (int a = 0; a < nsh; ++a)
+    for (int b = 0; b <= a; ++b) {
+      int cls = hb.l[a] + hb.l[b];
+      cs1[cls].push_back(a);
+      cs2[cls].push_back(b);
+    }
+  std::vector<int32_t> s1, s2;
+  for (int c = 0; c < 3; ++c) {
+    s->all_class_off[c] = (int64_t)s1.size();
+    s1.insert(s1.end(), cs1[c].begin(), cs1[c].end());
+    s2.insert(s2.end(), cs2[c].begin(), cs2[c].end());
+  }
+  s->all_class_off[3] = (int64_t)s1.size();
+  PairSetHost hall;
+  build_pairs(hb, s1, s2, &hall);
+  rc = upload_pairs(hall, &s->all, st);
+  if (rc != CD_OK) { system_release(s); return rc; }
+  // diagonal of every packed pair (kernel a, diagonal mode)
+  const int64_t npk = (int64_t)nbf * (nbf + 1) / 2;
+  double* dall = nullptr;
+  rc = dalloc(&dall, (size_t)npk);
+  if (rc != CD_OK) { system_release(s); return rc; }
+  rc = launch_eri_diag(s->all, nullptr, s->all_class_off, dall, s->boys, st);
+  std::vector<double> hd(npk);
+  if (rc == CD_OK && cudaMemcpyAsync(hd.data(), dall, sizeof(double) * npk, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = CD_ECUDA;
+  if (rc == CD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
+  cudaFree(dall);
+  if (rc != CD_OK) { if (rc == CD_ECUDA) set_error("diagonal pass failed"); system_release(s); return rc; }
+  for (int64_t p = 0; p < npk; ++p)
+    if (!std::isfinite(hd[p])) { set_error("non-finite ERI diagonal"); system_release(s); return CD_EINVAL; }
+  double dmax = 0.0;
+  for (double v : hd) dmax = std::max(dmax, v);
+  // shell-pair screening: keep (AB) iff sqrt(max_{mu nu in AB} D * max D) >= schwarz
+  const int64_t nsp = (int64_t)s1.size();
+  std::vector<char> keep(nsp, 0);
+  std::vector<int32_t> ks1, ks2, kall;
+  for (int64_t k = 0; k < nsp; ++k) {
+    double m = 0.0;
+    for (int c = 0; c < 9; ++c) {
+      int32_t r = hall.row[9 * k + c];
+      if (r >= 0) m = std::max(m, hd[r]);
+    }
+    if (sqrt(m * dmax) >= schwarz) {
+      keep[k] = 1;
+      ks1.push_back(s1[k]); ks2.push_back(s2[k]); kall.push_back((int32_t)k);
+    }
+  }
+  for (int c = 0; c < 4; ++c) {
+    int64_t off = 0;
+    for (int64_t k = 0; k < s->all_class_off[c]; ++k) off += keep[k];
+    s->bra_class_off[c] = off;
+  }
+  // rows: packed indices of the kept pairs, increasing
+  std::vector<int64_t>& rows = s->row_packed;
+  for (int64_t k = 0; k < nsp; ++k)
+    if (keep[k])
+      for (int c = 0; c < 9; ++c)
+        if (hall.row[9 * k + c] >= 0) rows.push_back(hall.row[9 * k + c]);
+  std::sort(rows.begin(), rows.end());
+  const int64_t n = (int64_t)rows.size();
+  s->n_rows = n;
+  s->n_rows_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
+  std::vector<int32_t> p2r(npk, -1);
+  for (int64_t r = 0; r < n; ++r) p2r[rows[r]] = (int32_t)r;
+  PairSetHost hbra;
+  build_pairs(hb, ks1, ks2, &hbra);
+  for (auto& r : hbra.row)
+    if (r >= 0) r = p2r[r];
+  s->bra_to_all = kall;
+  rc = upload_pairs(hbra, &s->bra, st);
+  if (rc != CD_OK) { system_release(s); return rc; }
+  // per-row data: diagonal, (mu, nu), ket descriptor pieces
+  std::vector<int32_t> allidx((size_t)nsh * nsh, -1);
+  for (int64_t k = 0; k < nsp; ++k) allidx[(size_t)s1[k] * nsh + s2[k]] = (int32_t)k;
+  s->row_diag.resize(n);
+  s->row_allsp.resize(n);
+  s->row_kc.resize(n);
+  s->row_kd.resize(n);
+  std::vector<int32_t> rmu(n), rnu(n);
+  for (int64_t r = 0; r < n; ++r) {
+    int64_t p = rows[r];
+    s->row_diag[r] = hd[p];
+    int64_t mu = (int64_t)((sqrt(8.0 * (double)p + 1.0) - 1.0) / 2.0);
+    while (mu * (mu + 1) / 2 > p) --mu;
+    while ((mu + 1) * (mu + 2) / 2 <= p) ++mu;
+    int64_t nu = p - mu * (mu + 1) / 2;
+    rmu[r] = (int32_t)mu;
+    rnu[r] = (int32_t)nu;
+    int Sm = hb.bf_shell[mu], Sn = hb.bf_shell[nu];
+    int32_t k = allidx[(size_t)Sm * nsh + Sn];
+    s->row_allsp[r] = k;
+    int cm = hb.bf_comp[mu], cn = hb.bf_comp[nu];
+    if (hall.swapped[k]) { s->row_kc[r] = (int8_t)cn; s->row_kd[r] = (int8_t)cm; }
+    else { s->row_kc[r] = (int8_t)cm; s->row_kd[r] = (int8_t)cn; }
+  }
+  rc = dalloc(&s->diag_dev, (size_t)s->n_rows_pad);
+  if (rc == CD_OK) rc = dalloc(&s->row_mu_dev, (size_t)std::max<int64_t>(n, 1));
+  if (rc == CD_OK) rc = dalloc(&s->row_nu_dev, (size_t)std::max<int64_t>(n, 1));
+  if (rc != CD_OK) { system_release(s); return rc; }
+  CD_CUDA(cudaMemsetAsync(s->diag_dev, 0, sizeof(double) * s->n_rows_pad, st));
+  if (n > 0) {
+    CD_CUDA(cudaMemcpyAsync(s->diag_dev, s->row_diag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    CD_CUDA(cudaMemcpyAsync(s->row_mu_dev, rmu.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    CD_CUDA(cudaMemcpyAsync(s->row_nu_dev, rnu.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  }
+  CD_CUDA(cudaStreamSynchronize(st));
+  s->ms_setup = now_ms() - t0;
+  *out = s;
+  return CD_OK;
+}
+
+static KetDesc ket_of_row(const cd_system* s, int64_t r, int32_t slot) {
+  KetDesc k;
+  int32_t sp = s->row_allsp[r];
+  k.sp = sp;
+  k.slot = slot;
+  k.kc = s->row_kc[r];
+  k.kd = s->row_kd[r];
+  // canonical classes of `all`: [0, off1) ss, [off1, off2) ps, [off2, off3) pp
+  if (sp < s->all_class_off[1]) { k.lc = 0; k.ld = 0; }
+  else if (sp < s->all_class_off[2]) { k.lc = 1; k.ld = 0; }
+  else { k.lc = 1; k.ld = 1; }
+  return k;
+}
+
+// ---------------------------------------------------------------- factor ----
+struct cd_factor {
+  cd_system* sys = nullptr;
+  bool owns_sys = false;
+  int64_t M = 0, Mcap = 0, ld = 0, n = 0;
+  double* L = nullptr;
+  float* L32 = nullptr;
+  int vec_precision = CD_FP64;
+  std::vector<int64_t> piv;
+  std::vector<double> gaps;
+  std::vector<double> resid;
+  double resid_max = 0.0;
+  double stats[16] = {0};
+};
+
+static void factor_release(cd_factor* f) {
+  if (!f) return;
+  cudaFree(f->L);
+  cudaFree(f->L32);
+  if (f->owns_sys) system_release(f->sys);
+  delete f;
+}
+
+namespace {
+struct Work {  // scratch of one factorisation, freed at the end
+  double* pool = nullptr;
+  double* D0 = nullptr;
+  double* D1 = nullptr;
+  double* Bg = nullptr;
+  int32_t* slots_dev = nullptr;
+  int64_t* rows_dev = nullptr;
+  KetDesc* kets_dev = nullptr;
+  StepScratch* sc = nullptr;
+  StepResult* res_dev = nullptr;
+  StepResult* res_h = nullptr;
+  double* dh = nullptr;
+  double* dp_h = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  ~Work() {
+    cudaFree(pool); cudaFree(D0); cudaFree(D1); cudaFree(Bg); cudaFree(slots_dev); cudaFree(rows_dev);
+    cudaFree(kets_dev); cudaFree(sc); cudaFree(res_dev);
+    cudaFreeHost(res_h); cudaFreeHost(dh); cudaFreeHost(dp_h);
+    for (auto& e : ev) if (e) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
+static int grow_vectors(cd_factor* f, int64_t newcap, int64_t K, cudaStream_t st) {
+  double* nL = nullptr;
+  CD_TRY(dalloc(&nL, (size_t)newcap * f->ld));
+  if (K > 0) CD_CUDA(cudaMemcpyAsync(nL, f->L, sizeof(double) * K * f->ld, cudaMemcpyDeviceToDevice, st));
+  CD_CUDA(cudaStreamSynchronize(st));
+  cudaFree(f->L);
+  f->L = nL;
+  f->Mcap = newcap;
+  return CD_OK;
+}
+
+static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_factor* f) {
+  const double t_start = now_ms();
+  const double tau = o->tau;
+  if (!(tau > 0.0) || !std::isfinite(tau)) { set_error("tau must be finite and > 0"); return CD_EINVAL; }
+  const int b = o->block ? o->block : 64;
+  if (b < 1 || b > kMaxBlock) { set_error("block must be in [1, 256]"); return CD_EINVAL; }
+  if (o->vec_precision != CD_FP64 && o->vec_precision != CD_VEC_FP32) { set_error("bad vec_precision"); return CD_EINVAL; }
+  const bool forced = o->forced_pivots != nullptr;
+  const int64_t nf = forced ? o->n_forced : 0;
+  const int64_t n = s->n_rows, ld = s->n_rows_pad, N = s->hb.nbf;
+  if (forced) {
+    if (nf < 0) { set_error("n_forced < 0"); return CD_EINVAL; }
+    for (int64_t k = 0; k < nf; ++k)
+      if (o->forced_pivots[k] < 0 || o->forced_pivots[k] >= n) { set_error("forced pivot out of range"); return CD_EINVAL; }
+  }
+  int64_t Mmax = o->max_vectors > 0 ? std::min<int64_t>(o->max_vectors, n) : std::min<int64_t>(n, 16 * N);
+  if (forced) Mmax = std::min<int64_t>(Mmax, std::max<int64_t>(nf, 1));
+  Mmax = std::max<int64_t>(Mmax, 1);
+  size_t freeb = 0, totb = 0;
+  CD_CUDA(cudaMemGetInfo(&freeb, &totb));
+  const double budget = o->mem_budget_gb > 0 ? o->mem_budget_gb * 1e9 : 0.9 * (double)freeb;
+  const double fixed = 8.0 * ld * (b + 2) + 8.0 * Mmax * b;
+  int64_t Mcap = std::min<int64_t>(Mmax, std::max<int64_t>(256, 6 * N));
+  if (fixed + 8.0 * ld * Mcap > budget) {
+    Mcap = (int64_t)((budget - fixed) / (8.0 * ld));
+    if (Mcap < 1) { set_error("device memory budget too small for the decomposition"); return CD_ENOMEM; }
+  }
+  f->sys = s;
+  f->n = n;
+  f->ld = ld;
+  f->vec_precision = o->vec_precision;
+  Work w;
+  CD_TRY(dalloc(&f->L, (size_t)Mcap * ld));
+  f->Mcap = Mcap;
+  CD_TRY(dalloc(&w.pool, (size_t)b * ld));
+  CD_TRY(dalloc(&w.D0, (size_t)ld));
+  CD_TRY(dalloc(&w.D1, (size_t)ld));
+  CD_TRY(dalloc(&w.Bg, (size_t)Mmax * b));
+  CD_TRY(dalloc(&w.slots_dev, (size_t)b));
+  CD_TRY(dalloc(&w.rows_dev, (size_t)b));
+  CD_TRY(dalloc(&w.kets_dev, (size_t)b));
+  CD_TRY(dalloc(&w.sc, 1));
+  CD_TRY(dalloc(&w.res_dev, 1));
+  CD_CUDA(cudaMallocHost(&w.res_h, sizeof(StepResult)));
+  CD_CUDA(cudaMallocHost(&w.dh, sizeof(double) * std::max<int64_t>(n, 1)));
+  CD_CUDA(cudaMallocHost(&w.dp_h, sizeof(double)));
+  for (auto& e : w.ev) CD_CUDA(cudaEventCreate(&e));
+  CD_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(StepScratch), st));
+  CD_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(double) * b * ld, st));
+  CD_CUDA(cudaMemsetAsync(w.D1, 0, sizeof(double) * ld, st));
+  CD_CUDA(cudaMemcpyAsync(w.D0, s->diag_dev, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+  double d1max = 0.0;
+  for (double v : s->row_diag) d1max = std::max(d1max, v);
+  const double neg_tol = -1e-10 * d1max;
+  double* Dcur = w.D0;
+  double* Dnext = w.D1;
+  StepResult res;
+  if (n > 0) {
+    CD_TRY(launch_argmax(Dcur, n, w.sc, w.res_dev, st));
+    CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+    res = *w.res_h;
+  } else {
+    res.dmax = -1.0; res.idx = -1; res.bad = 0;
+  }
+  std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
+  std::unordered_map<int64_t, int> row2slot;
+  double t_eri = 0, t_upd = 0, t_sel = 0, upd_flops = 0, eri_ints = 0;
+  int64_t nblocks = 0, ncols = 0;
+  int64_t K = 0;
+  bool done = false;
+  while (!done) {
+    if (forced ? (K >= nf) : !(res.dmax >= tau)) break;
+    // ---- candidate block
+    const double ts = now_ms();
+    std::vector<int64_t> cand;
+    if (forced) {
+      for (int64_t k = K; k < nf && (int64_t)cand.size() < b; ++k)
+        if (std::find(cand.begin(), cand.end(), o->forced_pivots[k]) == cand.end()) cand.push_back(o->forced_pivots[k]);
+    } else {
+      CD_CUDA(cudaMemcpyAsync(w.dh, Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+      CD_CUDA(cudaStreamSynchronize(st));
+      std::vector<int64_t> c;
+      c.reserve(1024);
+      for (int64_t r = 0; r < n; ++r)
+        if (w.dh[r] >= tau) c.push_back(r);
+      auto cmp = [&](int64_t x, int64_t y) { return w.dh[x] > w.dh[y] || (w.dh[x] == w.dh[y] && x < y); };
+      if ((int64_t)c.size() > b) {
+        std::nth_element(c.begin(), c.begin() + b, c.end(), cmp);
+        c.resize(b);
+      }
+      cand = c;
+    }
+    t_sel += now_ms() - ts;
+    // ---- pool: keep columns still wanted, free the rest
+    std::unordered_map<int64_t, int> want;
+    for (size_t j = 0; j < cand.size(); ++j) want[cand[j]] = (int)j;
+    for (int sl = 0; sl < b; ++sl)
+      if (slot_row[sl] >= 0 && !want.count(slot_row[sl])) {
+        row2slot.erase(slot_row[sl]);
+        slot_row[sl] = -1;
+      }
+    std::vector<KetDesc> kets;
+    std::vector<int32_t> new_slots;
+    std::vector<int64_t> new_rows;
+    int free_sl = 0;
+    for (int64_t r : cand) {
+      if (row2slot.count(r)) continue;
+      while (slot_row[free_sl] >= 0) ++free_sl;
+      slot_row[free_sl] = r;
+      slot_valid[free_sl] = 0;
+      row2slot[r] = free_sl;
+      kets.push_back(ket_of_row(s, r, free_sl));
+      new_slots.push_back(free_sl);
+      new_rows.push_back(r);
+    }
+    ++nblocks;
+    ncols += (int64_t)kets.size();
+    CD_CUDA(cudaEventRecord(w.ev[0], st));
+    if (!kets.empty()) {
+      CD_CUDA(cudaMemcpyAsync(w.kets_dev, kets.data(), sizeof(KetDesc) * kets.size(), cudaMemcpyHostToDevice, st));
+      CD_TRY(launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, w.kets_dev, (int)kets.size(), w.pool, ld,
+                                s->boys, st));
+      eri_ints += (double)kets.size() * (double)n;
+    }
+    CD_CUDA(cudaEventRecord(w.ev[1], st));
+    // ---- bring every pool column up to date with vectors [valid, K)
+    std::unordered_map<int64_t, std::vector<int>> groups;
+    for (int sl = 0; sl < b; ++sl)
+      if (slot_row[sl] >= 0 && slot_valid[sl] < K) groups[slot_valid[sl]].push_back(sl);
+    for (auto& g : groups) {
+      const int64_t k0 = g.first;
+      std::vector<int32_t> sl(g.second.begin(), g.second.end());
+      std::vector<int64_t> rr;
+      for (int x : sl) rr.push_back(slot_row[x]);
+      const int nb = (int)sl.size();
+      CD_CUDA(cudaMemcpyAsync(w.slots_dev, sl.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
+      CD_CUDA(cudaMemcpyAsync(w.rows_dev, rr.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+      CD_TRY(launch_gather(f->L, ld, w.rows_dev, nb, k0, K, w.Bg, st));
+      CD_TRY(launch_colupd(w.pool, ld, w.slots_dev, nb, f->L, k0, K, w.Bg, n, st));
+      upd_flops += 2.0 * (double)n * nb * (double)(K - k0);
+      // the host vectors must stay alive until the copies above complete
+      CD_CUDA(cudaStreamSynchronize(st));
+    }
+    CD_CUDA(cudaEventRecord(w.ev[2], st));
+    for (int sl = 0; sl < b; ++sl)
+      if (slot_row[sl] >= 0) slot_valid[sl] = K;
+    const int64_t Kb = K;
+    bool first = true;
+    // ---- serial pivot steps inside the block
+    for (;;) {
+      int64_t p;
+      double dp;
+      if (forced) {
+        if (K >= nf) { done = true; break; }
+        p = o->forced_pivots[K];
+      } else {
+        if (!(res.dmax >= tau)) { done = true; break; }
+        p = res.idx;
+      }
+      auto it = row2slot.find(p);
+      if (it == row2slot.end()) break;  // argmax outside the block: new block
+      const int sl = it->second;
+      if (forced) {
+        CD_CUDA(cudaMemcpyAsync(w.dp_h, Dcur + p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CD_CUDA(cudaStreamSynchronize(st));
+        dp = *w.dp_h;
+      } else {
+        dp = res.dmax;
+      }
+      if (!(dp > 0.0)) {
+        set_error("pivot diagonal not positive (matrix not PSD) at step " + std::to_string(K));
+        return CD_ENOTPSD;
+      }
+      if (K >= f->Mcap) {
+        if (f->Mcap >= Mmax) {
+          set_error("number of vectors exceeds max_vectors = " + std::to_string(Mmax));
+          return CD_ENOMEM;
+        }
+        int64_t nc = std::min<int64_t>(Mmax, f->Mcap + f->Mcap / 2 + 1);
+        if (fixed + 8.0 * ld * nc > budget) nc = (int64_t)((budget - fixed) / (8.0 * ld));
+        if (nc <= f->Mcap) { set_error("device memory budget exhausted at M = " + std::to_string(K)); return CD_ENOMEM; }
+        CD_TRY(grow_vectors(f, nc, K, st));
+      }
+      const double gap = forced ? res.dmax - dp : 0.0;
+      CD_TRY(launch_finalize(w.pool + (int64_t)sl * ld, f->L, ld, Kb, K, p, Dcur, Dnext, f->L + K * ld, n, neg_tol,
+                             w.sc, w.res_dev, st));
+      CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
+      CD_CUDA(cudaStreamSynchronize(st));
+      if (first) {
+        float a = 0, c = 0;
+        cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
+        cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+        t_eri += a;
+        t_upd += c;
+        first = false;
+      }
+      res = *w.res_h;
+      std::swap(Dcur, Dnext);
+      f->piv.push_back(p);
+      f->gaps.push_back(gap);
+      ++K;
+      row2slot.erase(it);
+      slot_row[sl] = -1;
+      if (res.bad) {
+        set_error("residual diagonal below -1e-10 max D (matrix not PSD) after step " + std::to_string(K));
+        return CD_ENOTPSD;
+      }
+    }
+    if (first) {  // block ended without a step (cannot happen in free mode; forced lists may)
+      CD_CUDA(cudaStreamSynchronize(st));
+      float a = 0, c = 0;
+      cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
+      cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+      t_eri += a;
+      t_upd += c;
+      if (forced && K < nf && !row2slot.count(o->forced_pivots[K])) {
+        set_error("internal: forced pivot not in block");
+        return CD_EINVAL;
+      }
+    }
+  }
+  f->M = K;
+  f->resid_max = res.dmax;
+  f->resid.resize(n);
+  if (n > 0) {
+    CD_CUDA(cudaMemcpyAsync(f->resid.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  }
+  if (f->vec_precision == CD_VEC_FP32 && K > 0) {
+    CD_TRY(dalloc(&f->L32, (size_t)K * ld));
+    CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
+  }
+  CD_CUDA(cudaStreamSynchronize(st));
+  const double t_all = now_ms() - t_start;
+  f->stats[0] = s->ms_setup;
+  f->stats[1] = t_eri;
+  f->stats[2] = t_upd;
+  f->stats[3] = t_all - t_eri - t_upd - t_sel;
+  f->stats[4] = t_sel;
+  f->stats[5] = t_all;
+  f->stats[6] = (double)nblocks;
+  f->stats[7] = (double)ncols;
+  f->stats[8] = upd_flops;
+  f->stats[9] = eri_ints;
+  f->stats[10] = (double)K;
+  return CD_OK;
+}
+
+// ---------------------------------------------------------------- C ABI ----
+extern "C" {
+
+const char* cd_last_error(void) { return g_err.c_str(); }
+const char* cd_version(void) { return "cderi 0.1 (sm_103a)"; }
+
+int cd_system_create(const cd_basis_t* basis, double schwarz, void* stream, cd_system_t** out) {
+  if (!out) { set_error("out is NULL"); return CD_EINVAL; }
+  *out = nullptr;
+  cd_system* s = nullptr;
+  int rc = system_create_impl(basis, schwarz, (cudaStream_t)stream, &s);
+  if (rc == CD_OK) *out = s;
+  return rc;
+}
+
+void cd_system_free(cd_system_t* sys) { system_release(sys); }
+
+int cd_system_info(const cd_system_t* s, int32_t* n_basis, int64_t* n_rows, int64_t* n_shell_pairs) {
+  if (!s) { set_error("system is NULL"); return CD_EINVAL; }
+  if (n_basis) *n_basis = s->hb.nbf;
+  if (n_rows) *n_rows = s->n_rows;
+  if (n_shell_pairs) *n_shell_pairs = s->bra.n;
+  return CD_OK;
+}
+
+int cd_system_rows(const cd_system_t* s, int64_t* packed, double* diag) {
+  if (!s) { set_error("system is NULL"); return CD_EINVAL; }
+  if (packed) std::memcpy(packed, s->row_packed.data(), sizeof(int64_t) * s->n_rows);
+  if (diag) std::memcpy(diag, s->row_diag.data(), sizeof(double) * s->n_rows);
+  return CD_OK;
+}
+
+int cd_eri_columns(const cd_system_t* s, const int64_t* cols, int32_t ncols, double* out, int64_t ld, void* stream) {
+  if (!s || !out || (ncols > 0 && !cols) || ncols < 0) { set_error("cd_eri_columns: bad argument"); return CD_EINVAL; }
+  if (ld < s->n_rows) { set_error("cd_eri_columns: ld < n_rows"); return CD_EINVAL; }
+  if (ncols == 0) return CD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<KetDesc> k(ncols);
+  for (int j = 0; j < ncols; ++j) {
+    if (cols[j] < 0 || cols[j] >= s->n_rows) { set_error("cd_eri_columns: column row out of range"); return CD_EINVAL; }
+    k[j] = ket_of_row(s, cols[j], j);
+  }
+  KetDesc* kd = nullptr;
+  CD_TRY(dalloc(&kd, (size_t)ncols));
+  int rc = CD_OK;
+  if (cudaMemcpyAsync(kd, k.data(), sizeof(KetDesc) * ncols, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = CD_ECUDA;
+  if (rc == CD_OK) rc = launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, kd, ncols, out, ld, s->boys, st);
+  if (rc == CD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
+  if (rc == CD_ECUDA) set_error("cd_eri_columns: CUDA failure");
+  cudaFree(kd);
+  return rc;
+}
+
+int cd_eri_factor_sys(cd_system_t* sys, const cd_opts_t* opts, void* stream, cd_factor_t** out) {
+  if (!out) { set_error("out is NULL"); return CD_EINVAL; }
+  *out = nullptr;
+  if (!sys || !opts) { set_error("system or opts is NULL"); return CD_EINVAL; }
+  cd_factor* f = new cd_factor();
+  int rc = factor_impl(sys, opts, (cudaStream_t)stream, f);
+  if (rc != CD_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    factor_release(f);
+    return rc;
+  }
+  *out = f;
+  return CD_OK;
+}
+
+int cd_eri_factor(const cd_basis_t* basis, const cd_opts_t* opts, void* stream, cd_factor_t** out) {
+  if (!out) { set_error("out is NULL"); return CD_EINVAL; }
+  *out = nullptr;
+  if (!opts) { set_error("opts is NULL"); return CD_EINVAL; }
+  cd_system* s = nullptr;
+  CD_TRY(cd_system_create(basis, opts->schwarz, stream, &s));
+  cd_factor* f = nullptr;
+  int rc = cd_eri_factor_sys(s, opts, stream, &f);
+  if (rc != CD_OK) { system_release(s); return rc; }
+  f->owns_sys = true;
+  *out = f;
+  return CD_OK;
+}
+
+void cd_factor_free(cd_factor_t* f) { factor_release(f); }
+
+int cd_factor_info(const cd_factor_t* f, int64_t* M, int64_t* n_rows, int32_t* n_basis, double* resid) {
+  if (!f) { set_error("factor is NULL"); return CD_EINVAL; }
+  if (M) *M = f->M;
+  if (n_rows) *n_rows = f->n;
+  if (n_basis) *n_basis = f->sys->hb.nbf;
+  if (resid) *resid = f->resid_max;
+  return CD_OK;
+}
+
+int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packed, double* gaps, double* resid_diag) {
+  if (!f) { set_error("factor is NULL"); return CD_EINVAL; }
+  for (int64_t k = 0; k < f->M; ++k) {
+    if (piv_rows) piv_rows[k] = f->piv[k];
+    if (piv_packed) piv_packed[k] = f->sys->row_packed[f->piv[k]];
+    if (gaps) gaps[k] = f->gaps[k];
+  }
+  if (resid_diag && f->n > 0) std::memcpy(resid_diag, f->resid.data(), sizeof(double) * f->n);
+  return CD_OK;
+}
+
+int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, int64_t* ld, int32_t* dtype) {
+  if (!f) { set_error("factor is NULL"); return CD_EINVAL; }
+  const bool f32 = f->vec_precision == CD_VEC_FP32 && f->L32;
+  if (L_dev) *L_dev = f32 ? (const void*)f->L32 : (const void*)f->L;
+  if (ld) *ld = f->ld;
+  if (dtype) *dtype = f32 ? 1 : 0;
+  if (L_host && f->M > 0) {
+    if (f32) {
+      std::vector<float> tmp((size_t)f->M * f->ld);
+      CD_CUDA(cudaMemcpy(tmp.data(), f->L32, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost));
+      for (int64_t k = 0; k < f->M; ++k)
+        for (int64_t r = 0; r < f->n; ++r) L_host[k * f->n + r] = tmp[(size_t)k * f->ld + r];
+    } else {
+      CD_CUDA(cudaMemcpy2D(L_host, sizeof(double) * f->n, f->L, sizeof(double) * f->ld, sizeof(double) * f->n, f->M,
+                           cudaMemcpyDeviceToHost));
+    }
+  }
+  return CD_OK;
+}
+
+int cd_factor_stats(const cd_factor_t* f, double* stats16) {
+  if (!f || !stats16) { set_error("cd_factor_stats: bad argument"); return CD_EINVAL; }
+  std::memcpy(stats16, f->stats, sizeof(f->stats));
+  return CD_OK;
+}
+
+long long cd_kernel_launches(void) { return cd::launch_counter(); }
+
+int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, double* K, int32_t mode, void* stream) {
+  if (!f || !C_occ || n_occ <= 0) { set_error("cd_jk: bad argument"); return CD_EINVAL; }
+  const int m = mode & 0xff;
+  const bool dev = (mode & CD_JK_DEVICE) != 0;
+  const bool wantJ = !(mode & CD_JK_ONLY_K), wantK = !(mode & CD_JK_ONLY_J);
+  if ((wantJ && !J) || (wantK && !K)) { set_error("cd_jk: J or K is NULL"); return CD_EINVAL; }
+  if (m != CD_JK_FP64 && m != CD_JK_BF16X3) { set_error("cd_jk: unknown mode"); return CD_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = f->sys->hb.nbf, O = n_occ;
+  const int64_t n = f->n, M = f->M, ld = f->ld;
+  double *dC = nullptr, *dJ = nullptr, *dK = nullptr, *d = nullptr, *v = nullptr, *Jp = nullptr;
+  double *Lfull = nullptr, *B = nullptr;
+  int rc = CD_OK;
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st);
+    if (!dev) { cudaFree(dC); cudaFree(dJ); cudaFree(dK); }
+    cudaFree(d); cudaFree(v); cudaFree(Jp); cudaFree(Lfull); cudaFree(B);
+    return code;
+  };
+  if (dev) {
+    dC = const_cast<double*>(C_occ);
+    dJ = J;
+    dK = K;
+  } else {
+    if ((rc = dalloc(&dC, (size_t)N * O)) != CD_OK) return fail(rc);
+    if (wantJ && (rc = dalloc(&dJ, (size_t)N * N)) != CD_OK) return fail(rc);
+    if (wantK && (rc = dalloc(&dK, (size_t)N * N)) != CD_OK) return fail(rc);
+    if (cudaMemcpyAsync(dC, C_occ, sizeof(double) * N * O, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_error("cd_jk: copy of C_occ failed");
+      return fail(CD_ECUDA);
+    }
+  }
+  if (m == CD_JK_BF16X3) {
+    const float* L32 = f->L32;
+    float* tmp = nullptr;
+    if (!L32) {
+      if ((rc = dalloc(&tmp, (size_t)std::max<int64_t>(M, 1) * ld)) != CD_OK) return fail(rc);
+      if ((rc = launch_to_fp32(f->L, ld, M, ld, tmp, st)) != CD_OK) { cudaFree(tmp); return fail(rc); }
+      L32 = tmp;
+    }
+    rc = jk_mixed(L32, ld, M, n, N, O, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, dJ, dK, wantJ, wantK, st);
+    if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
+    if (rc != CD_OK) return fail(rc);
+  } else {
+    if (wantJ) {
+      if ((rc = dalloc(&d, (size_t)std::max<int64_t>(n, 1))) != CD_OK) return fail(rc);
+      if ((rc = dalloc(&v, (size_t)std::max<int64_t>(M, 1))) != CD_OK) return fail(rc);
+      if ((rc = dalloc(&Jp, (size_t)std::max<int64_t>(n, 1))) != CD_OK) return fail(rc);
+      if ((rc = launch_density_packed(dC, N, O, f->sys->row_mu_dev, f->sys->row_nu_dev, n, d, st)) != CD_OK) return fail(rc);
+      if ((rc = launch_gemv_rows<double>(f->L, ld, M, n, d, v, st)) != CD_OK) return fail(rc);
+      if ((rc = launch_gemv_cols<double>(f->L, ld, M, n, v, Jp, st)) != CD_OK) return fail(rc);
+      if ((rc = launch_unpack_sym(Jp, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, dJ, st)) != CD_OK) return fail(rc);
+    }
+    if (wantK) {
+      const double perP = 8.0 * ((double)N * N + (double)N * O);
+      int Pc = (int)std::max<double>(1.0, std::min<double>((double)std::max<int64_t>(M, 1), 2.0e9 / perP));
+      if ((rc = dalloc(&Lfull, (size_t)Pc * N * N)) != CD_OK) return fail(rc);
+      if ((rc = dalloc(&B, (size_t)Pc * N * O)) != CD_OK) return fail(rc);
+      if (cudaMemsetAsync(dK, 0, sizeof(double) * N * N, st) != cudaSuccess) return fail(CD_ECUDA);
+      for (int64_t P0 = 0; P0 < M; P0 += Pc) {
+        const int pc = (int)std::min<int64_t>(Pc, M - P0);
+        if ((rc = launch_unpack_vectors<double>(f->L, ld, P0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, Lfull, st)) != CD_OK) return fail(rc);
+        // B[p] = Lfull[p] (N x N) * C (N x O)
+        if ((rc = launch_dgemm(N, O, N, pc, 1.0, Lfull, N, 1, (int64_t)N * N, dC, O, 1, 0, B, O, (int64_t)N * O, false, st)) != CD_OK) return fail(rc);
+        // K += 2 sum_p B[p] B[p]^T
+        if ((rc = launch_dgemm(N, N, O, pc, 2.0, B, O, 1, (int64_t)N * O, B, 1, O, (int64_t)N * O, dK, N, 0, true, st)) != CD_OK) return fail(rc);
+      }
+    }
+  }
+  if (!dev) {
+    if (wantJ && cudaMemcpyAsync(J, dJ, sizeof(double) * N * N, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CD_ECUDA);
+    if (wantK && cudaMemcpyAsync(K, dK, sizeof(double) * N * N, cudaMemcpyDeviceToHost, st) != cudaSuccess) return fail(CD_ECUDA);
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("cd_jk: CUDA failure"); return fail(CD_ECUDA); }
+  return fail(CD_OK);
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// internal.cuh -- shared declarations of the CUDA translation units of libcderi.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/cderi.h"
+
+namespace cd {
+
+// ----- error handling -----------------------------------------------------
+void set_error(const std::string& msg);
+// process-wide count of kernel launches issued by the library
+void count_launch(int n = 1);
+long long launch_counter();
+struct Status {
+  int code = CD_OK;
+};
+#define CD_CUDA(call)                                                         \
+  do {                                                                        \
+    cudaError_t _e = (call);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      ::cd::set_error(std::string("CUDA: ") + cudaGetErrorString(_e) + " at " \
+                      + __FILE__ + ":" + std::to_string(__LINE__));           \
+      return CD_ECUDA;                                                        \
+    }                                                                         \
+  } while (0)
+#define CD_TRY(call)                 \
+  do {                               \
+    int _rc = (call);                \
+    if (_rc != CD_OK) return _rc;    \
+  } while (0)
+
+// ----- Boys function table (Taylor expansion about grid points) ------------
+// F_m(T) at T_k = k * kBoysStep for k < kBoysPoints and m <= kBoysMaxM.
+constexpr int kBoysMaxM = 4;            // l <= 1 per centre -> L <= 4
+constexpr int kBoysTaylor = 8;          // Taylor terms
+constexpr double kBoysStep = 0.1;
+constexpr double kBoysTmax = 36.0;      // above: asymptotic form + upward recursion
+constexpr int kBoysPoints = 362;
+constexpr int kBoysCols = kBoysMaxM + kBoysTaylor + 1;   // F_0..F_12 per point
+
+// ----- shell-pair records (device, structure of arrays) -------------------
+// A shell pair joins shells S1 >= S2 (shell index).  It is stored in canonical
+// orientation: centre "A" carries the larger l (A = S1 on a tie).  Per
+// primitive pair (a on A, b on B): zeta = a + b, P, PA = P - A, and
+// Kp = sqrt(2) pi^{5/4} d_a d_b exp(-a b / zeta |A-B|^2) / zeta, so that the
+// (ss|ss) prefactor of a primitive quartet is Kp_bra Kp_ket / sqrt(zeta + eta).
+struct PairSet {
+  int64_t n = 0;          // shell pairs
+  int64_t npp = 0;        // primitive pairs
+  // per shell pair
+  int32_t* pp_off = nullptr;   // [n+1] first primitive pair
+  int8_t*  la = nullptr;       // [n] canonical l of A
+  int8_t*  lb = nullptr;       // [n]
+  double*  AB = nullptr;       // [n][3] A - B (canonical)
+  int32_t* row = nullptr;      // [n][9] output row of component (i on A)*3 + (j on B), -1 = none
+  // per primitive pair
+  double* zeta = nullptr;      // [npp]
+  double* P = nullptr;         // [npp][3]
+  double* PA = nullptr;        // [npp][3]
+  double* Kp = nullptr;        // [npp]
+};
+
+// Host-side mirror used while building.
+struct PairSetHost {
+  std::vector<int32_t> pp_off, row;
+  std::vector<int8_t> la, lb;
+  std::vector<double> AB, zeta, P, PA, Kp;
+  std::vector<int32_t> s1, s2;     // shell indices of the pair (S1 >= S2)
+  std::vector<int8_t> swapped;     // 1 if A = S2
+};
+
+struct HostBasis {
+  int nsh = 0, nbf = 0;
+  std::vector<double> cen;        // [nsh][3]
+  std::vector<int> l, nprim, pofs, bf0;
+  std::vector<double> exps, dcoef;  // effective coefficients
+  std::vector<int> bf_shell, bf_comp;
+};
+
+int validate_and_normalise(const cd_basis_t* b, HostBasis* hb);
+void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std::vector<int32_t>& s2,
+                 PairSetHost* out);
+int upload_pairs(const PairSetHost& h, PairSet* d, cudaStream_t st);
+void free_pairs(PairSet* d);
+const double* boys_table_device(int* rc);   // per device, built once
+
+// ket descriptor of one column: shell-pair index and canonical components
+struct KetDesc {
+  int32_t sp;      // shell pair index (in the pair set that holds it)
+  int32_t slot;    // output column: out + slot * ld
+  int8_t kc, kd;   // component on canonical C (0..2, or 0 for s) and D
+  int8_t lc, ld;
+};
+
+// ERI kernels (eri.cu)
+// out[j * ld + row] = (bra rows | ket j) for every bra shell pair in `bra`
+int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
+                       const PairSet& ket, const KetDesc* kets_dev, int nket,
+                       double* out, int64_t ld, const double* boys, cudaStream_t st);
+// diag[row] = (row|row) for every shell pair in `ps` (rows from ps.row)
+int launch_eri_diag(const PairSet& ps, const int64_t* order, const int64_t* class_off,
+                    double* diag, const double* boys, cudaStream_t st);
+
+}  // namespace cd
+
+// ----- opaque objects -------------------------------------------------------
+struct cd_system {
+  cd::HostBasis hb;
+  cd::PairSet all;               // every shell pair (used for kets and the diagonal)
+  cd::PairSet bra;               // screened shell pairs, sorted by class
+  int64_t* bra_order = nullptr;  // unused (bra already sorted); kept for symmetry
+  int64_t bra_class_off[4] = {0, 0, 0, 0};
+  std::vector<int32_t> bra_to_all;          // bra shell pair -> index in `all`
+  std::vector<int64_t> all_class_off_h;     // class offsets of `all` (sorted by class)
+  int64_t all_class_off[4] = {0, 0, 0, 0};
+  int64_t n_rows = 0, n_rows_pad = 0;
+  std::vector<int64_t> row_packed;          // [n_rows]
+  std::vector<double> row_diag;             // [n_rows]
+  std::vector<int32_t> row_allsp;           // [n_rows] shell pair (in `all`) of the row
+  std::vector<int8_t> row_kc, row_kd;       // canonical components of the row
+  double* diag_dev = nullptr;               // [n_rows_pad] (row|row)
+  int32_t* row_mu_dev = nullptr;            // [n_rows] mu of each row
+  int32_t* row_nu_dev = nullptr;            // [n_rows] nu of each row
+  const double* boys = nullptr;
+  double schwarz = 0.0;
+  double ms_setup = 0.0;
+};

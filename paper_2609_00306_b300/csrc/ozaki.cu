@@ -1,0 +1,374 @@
+// ozaki.cu -- exact-slice GEMM on the tcgen05 tensor cores (see ozaki.cuh).
+//
+// CTA tile 128 (rows of A) x 64 (rows of B), k-blocks of 32 BF16 (64-byte
+// rows, 64-byte swizzle) staged by TMA in a STAGES-deep ring.  Warp roles:
+// warps 0-3 drain tensor memory (one TMEM lane per thread), warp 4 issues the
+// TMA loads, warp 5 allocates tensor memory and issues the MMAs.  Every
+// mbarrier wait is bounded; on time-out the CTA stops, frees its tensor memory
+// and sets the error flag.
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <algorithm>
+#include <mutex>
+#include "internal.cuh"
+#include "ozaki.cuh"
+#include "tc.cuh"
+
+namespace cd {
+namespace {
+
+constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int kThreads = 192;
+
+// 64-byte swizzled K-major descriptor: rows of 32 bf16 (64 B), 8-row groups 512 B apart
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused: swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+  d |= (uint64_t)1 << 46;                   // version
+  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
+  return d;
+}
+
+template <int SA, int SB, int KEEP, int STAGES>
+struct Cfg {
+  static constexpr int G = KEEP - 1;                       // accumulator groups (s+t = 2..KEEP)
+  static constexpr int A_BYTES = SA * BM * BK * 2;
+  static constexpr int B_BYTES = SB * BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int TMEM_COLS = G * BN <= 32 ? 32 : (G * BN <= 64 ? 64 : (G * BN <= 128 ? 128 : (G * BN <= 256 ? 256 : 512)));
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+template <int SA, int SB, int KEEP, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             int64_t m_rows, int64_t n_rows, int nkb_total, int kb_per_split, int kcb, int F,
+             unsigned long long* __restrict__ D, int64_t ldd, int* err) {
+  using C = Cfg<SA, SB, KEEP, STAGES>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 1;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int kb0 = blockIdx.z * kb_per_split;
+  const int kb1 = min(nkb_total, kb0 + kb_per_split);
+  const int nkb = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+    tc::mbar_init(tfull, 1);
+    tc::mbar_init(tempty, 4);
+    *abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 5) tc::tmem_alloc<C::TMEM_COLS>(tmem_slot);
+  if (warp == 4 && lane == 0) { tc::prefetch_tmap(&tmA); tc::prefetch_tmap(&tmB); }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (nkb > 0) {
+    if (warp == 4) {
+      if (lane == 0) {
+        // ---------------- TMA producer
+        for (int i = 0; i < nkb; ++i) {
+          const int s = i % STAGES;
+          const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) break;
+          uint8_t* a = smem + s * C::STAGE_BYTES;
+          uint8_t* b = a + C::A_BYTES;
+          tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
+          const int kx = (kb0 + i) * BK;
+          tc::tma_load_3d(a, &tmA, kx, (int32_t)m0, 0, &full[s]);
+          tc::tma_load_3d(b, &tmB, kx, (int32_t)n0, 0, &full[s]);
+        }
+      }
+    } else if (warp == 5) {
+      if (lane == 0) {
+        // ---------------- MMA issuer
+        constexpr uint32_t idesc = tc::idesc_bf16_f32<BM, BN>();
+        int chunk = 0;
+        for (int i = 0; i < nkb; ++i) {
+          const int s = i % STAGES;
+          const uint32_t ph = (uint32_t)((i / STAGES) & 1);
+          const bool chunk_start = (i % kcb) == 0;
+          if (chunk_start && chunk > 0) {
+            if (!tc::mbar_wait(tempty, (uint32_t)((chunk - 1) & 1), abort_flag, err)) break;
+            tc::tc_fence_after();
+          }
+          if (!tc::mbar_wait(&full[s], ph, abort_flag, err)) break;
+          tc::tc_fence_after();
+          const uint32_t a = tc::smem_u32(smem + s * C::STAGE_BYTES);
+          const uint32_t b = a + C::A_BYTES;
+#pragma unroll
+          for (int sa = 0; sa < SA; ++sa)
+#pragma unroll
+            for (int sb = 0; sb < SB; ++sb) {
+              const int g = sa + sb;  // 0-based: s + t - 2
+              if (g > KEEP - 2) continue;
+              // first product of this group inside the chunk overwrites
+              bool first_of_group = chunk_start;
+              if (first_of_group) {
+                // earlier (sa', sb') with the same g in this loop nest?
+                const int sa_first = g < SB ? 0 : g - (SB - 1);
+                first_of_group = (sa == sa_first);
+              }
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                const uint64_t ad = sdesc_k_sw64(a + sa * (BM * BK * 2) + kk * 32);
+                const uint64_t bd = sdesc_k_sw64(b + sb * (BN * BK * 2) + kk * 32);
+                tc::umma_bf16(tmem + g * BN, ad, bd, idesc, (first_of_group && kk == 0) ? 0u : 1u);
+              }
+            }
+          tc::umma_commit(&empty[s]);
+          if ((i % kcb) == kcb - 1 || i == nkb - 1) {
+            tc::umma_commit(tfull);
+            ++chunk;
+          }
+        }
+      }
+    } else {
+      // ---------------- drain (warps 0-3): thread = TMEM lane = tile row
+      const int row = warp * 32 + lane;
+      long long run[BN];
+#pragma unroll
+      for (int c = 0; c < BN; ++c) run[c] = 0;
+      const int nchunks = (nkb + kcb - 1) / kcb;
+      bool ok = true;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        if (!tc::mbar_wait(tfull, (uint32_t)(ch & 1), abort_flag, err)) { ok = false; break; }
+        tc::tc_fence_after();
+#pragma unroll
+        for (int g = 0; g < KEEP - 1; ++g) {
+          const int sh = F - 8 * (g + 2) + 2;  // weight of group g in units of 2^-F
+#pragma unroll
+          for (int cb = 0; cb < BN / 16; ++cb) {
+            uint32_t v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * BN + cb * 16, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const long long iv = (long long)__float2ll_rn(__uint_as_float(v[c]));
+              long long add;
+              if (sh >= 0) add = iv << sh;
+              else add = (iv + (1ll << (-sh - 1))) >> (-sh);
+              run[cb * 16 + c] += add;
+            }
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(tempty);
+      }
+      const int64_t m = m0 + row;
+      if (ok && m < m_rows) {
+#pragma unroll
+        for (int c = 0; c < BN; ++c) {
+          const int64_t n = n0 + c;
+          if (n < n_rows && run[c] != 0) atomicAdd(D + n * ldd + m, (unsigned long long)run[c]);
+        }
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 5) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc<C::TMEM_COLS>(tmem);
+  }
+}
+
+// ------------------------------------------------------------------ host ----
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 3D map over bf16 slices [S][rows][kpitch]; box {BK, box_rows, S}, 64-byte swizzle
+int make_map(CUtensorMap* map, const void* base, int S, int64_t rows, int64_t kdim, int64_t kpitch, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) { set_error("cuTensorMapEncodeTiled unavailable"); return CD_ECUDA; }
+  if (((uintptr_t)base & 15) || (kpitch * 2) % 16) { set_error("slice tensor not 16-byte aligned"); return CD_EINVAL; }
+  cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)(kpitch * 2), (cuuint64_t)(kpitch * 2 * rows)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)S};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r)); return CD_EINVAL; }
+  return CD_OK;
+}
+
+template <int SA, int SB, int KEEP, int STAGES>
+int run(const CUtensorMap& ta, const CUtensorMap& tb, int64_t a_rows, int64_t b_rows, int nkb, int ksplit, int kcb,
+        int F, unsigned long long* D, int64_t ldd, int* err, cudaStream_t st) {
+  using C = Cfg<SA, SB, KEEP, STAGES>;
+  auto k = ozaki_kernel<SA, SB, KEEP, STAGES>;
+  CD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  const int per = (nkb + ksplit - 1) / ksplit;
+  const int nsplit = (nkb + per - 1) / per;
+  dim3 grid((unsigned)((a_rows + BM - 1) / BM), (unsigned)((b_rows + BN - 1) / BN), (unsigned)nsplit);
+  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+__global__ void slice_rows_kernel(const double* __restrict__ src, int64_t src_rs, int64_t src_ks, int64_t rows,
+                                  int64_t kcount, const int32_t* __restrict__ row_exp, int S,
+                                  __nv_bfloat16* __restrict__ dst, int64_t dst_rows, int64_t kpitch, int64_t k0) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * kcount) return;
+  const int64_t r = t / kcount, k = t % kcount;
+  double x = ldexp(src[r * src_rs + k * src_ks], -row_exp[r]);
+  // first slice: 2^-7 resolution; later ones: 2^-8 of the previous
+  double w = 128.0;
+  for (int s = 0; s < S; ++s) {
+    const double a = rint(x * w);
+    dst[((int64_t)s * dst_rows + r) * kpitch + k0 + k] = __double2bfloat16(a);
+    x = fma(-a, 1.0 / w, x);
+    w *= 256.0;
+  }
+}
+
+}  // namespace
+
+int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpitch, const void* Bs, int64_t b_rows,
+               int64_t b_kpitch, int64_t kdim, unsigned long long* D, int64_t ldd, int ksplit, int* err_dev,
+               cudaStream_t st) {
+  if (kdim <= 0 || a_rows <= 0 || b_rows <= 0) return CD_OK;
+  CUtensorMap ta, tb;
+  CD_TRY(make_map(&ta, As, p.SA, a_rows, kdim, a_kpitch, BM));
+  CD_TRY(make_map(&tb, Bs, p.SB, b_rows, kdim, b_kpitch, BN));
+  const int nkb = (int)((kdim + BK - 1) / BK);
+  // exactness of the FP32 accumulation: (groups sharing an accumulator) * kc * 2^14 <= 2^24
+  const int maxg = std::min(p.KEEP - 1, std::min(p.SA, p.SB));
+  int kc = 1024 / std::max(1, maxg);
+  int kcb = std::max(1, kc / BK);
+  if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
+  if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 2>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
+  if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
+  set_error("ozaki_gemm: unsupported slice plan");
+  return CD_EINVAL;
+}
+
+int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int64_t rows, int64_t kcount,
+                          const int32_t* row_exp, int S, void* dst, int64_t dst_rows, int64_t kpitch, int64_t k0,
+                          cudaStream_t st) {
+  const int64_t tot = rows * kcount;
+  if (tot <= 0) return CD_OK;
+  slice_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, S,
+                                                                    (__nv_bfloat16*)dst, dst_rows, kpitch, k0);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+}  // namespace cd
+
+// ---------------------------------------------------------------------------
+// Stand-alone exact-slice product of two FP64 device matrices (C ABI
+// cd_slice_matmul): out[i][j] = sum_k X[i][k] Y[j][k].
+namespace cd {
+namespace {
+__global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
+                               int32_t* __restrict__ e) {
+  const int64_t r = blockIdx.x;
+  if (r >= rows) return;
+  double m = 0.0;
+  for (int64_t c = threadIdx.x; c < k; c += blockDim.x) m = fmax(m, fabs(X[r * ldx + c]));
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    m = fmax(m, sh[0]);
+    int ex = 0;
+    if (m > 0.0) frexp(m, &ex);
+    e[r] = ex;
+  }
+}
+__global__ void fixed_to_f64_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int64_t m, int64_t n,
+                                    const int32_t* __restrict__ ex, const int32_t* __restrict__ ey, int F,
+                                    double* __restrict__ out, int64_t ldo) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t i = t / n, j = t % n;
+  out[i * ldo + j] = ldexp((double)(long long)D[j * ldd + i], ex[i] + ey[j] - F);
+}
+}  // namespace
+}  // namespace cd
+
+extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const double* Y, int64_t ldy, int64_t n,
+                               int64_t k, int32_t slices, double* out, int64_t ldo, void* stream) {
+  using namespace cd;
+  if (!X || !Y || !out || m <= 0 || n <= 0 || k <= 0 || ldx < k || ldy < k || ldo < n) {
+    set_error("cd_slice_matmul: bad argument");
+    return CD_EINVAL;
+  }
+  if (slices != 1 && slices != 3 && slices != 7) { set_error("cd_slice_matmul: slices must be 1, 3 or 7"); return CD_EINVAL; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t kp = (k + 7) / 8 * 8;
+  OzakiPlan plan;
+  plan.SA = plan.SB = slices;
+  plan.KEEP = slices + 1;
+  int lk = 1;
+  while ((1ll << lk) < k) ++lk;
+  plan.F = 61 - lk;
+  void *As = nullptr, *Bs = nullptr;
+  int32_t *ex = nullptr, *ey = nullptr;
+  unsigned long long* D = nullptr;
+  int* err = nullptr;
+  int rc = CD_OK;
+  auto fin = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFree(As); cudaFree(Bs); cudaFree(ex); cudaFree(ey); cudaFree(D); cudaFree(err);
+    return code;
+  };
+  if (cudaMalloc(&As, (size_t)slices * m * kp * 2) != cudaSuccess || cudaMalloc(&Bs, (size_t)slices * n * kp * 2) != cudaSuccess ||
+      cudaMalloc(&ex, sizeof(int32_t) * m) != cudaSuccess || cudaMalloc(&ey, sizeof(int32_t) * n) != cudaSuccess ||
+      cudaMalloc(&D, sizeof(unsigned long long) * m * n) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    set_error("cd_slice_matmul: allocation failed");
+    return fin(CD_ENOMEM);
+  }
+  cudaMemsetAsync(As, 0, (size_t)slices * m * kp * 2, st);
+  cudaMemsetAsync(Bs, 0, (size_t)slices * n * kp * 2, st);
+  cudaMemsetAsync(D, 0, sizeof(unsigned long long) * m * n, st);
+  cudaMemsetAsync(err, 0, sizeof(int), st);
+  row_exp_kernel<<<(unsigned)m, 256, 0, st>>>(X, ldx, m, k, ex);
+  count_launch();
+  row_exp_kernel<<<(unsigned)n, 256, 0, st>>>(Y, ldy, n, k, ey);
+  count_launch();
+  if ((rc = launch_slice_rows_f64(X, ldx, 1, m, k, ex, slices, As, m, kp, 0, st)) != CD_OK) return fin(rc);
+  if ((rc = launch_slice_rows_f64(Y, ldy, 1, n, k, ey, slices, Bs, n, kp, 0, st)) != CD_OK) return fin(rc);
+  if ((rc = ozaki_gemm(plan, As, m, kp, Bs, n, kp, k, D, m, 1, err, st)) != CD_OK) return fin(rc);
+  fixed_to_f64_kernel<<<(unsigned)((m * n + 255) / 256), 256, 0, st>>>(D, m, m, n, ex, ey, plan.F, out, ldo);
+  count_launch();
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error(std::string("cd_slice_matmul: CUDA failure: ") + cudaGetErrorString(cudaGetLastError()));
+    return fin(CD_ECUDA);
+  }
+  if (herr) { set_error("cd_slice_matmul: tensor-core pipeline wait timed out"); return fin(CD_ETIMEOUT); }
+  return fin(CD_OK);
+}

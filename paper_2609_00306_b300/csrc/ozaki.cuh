@@ -1,0 +1,38 @@
+// ozaki.cuh -- exact-slice GEMM on the BF16 tensor cores (interface).
+//
+// A real matrix X is represented, row by row, as X[m][k] = 2^e[m] * x[m][k]
+// with |x| <= 1 and x ~ sum_{s=1..S} a_s 2^-(8s-1), a_s integers in
+// [-128, 128] (exact in BF16).  A product of two such matrices is
+//   sum_k X[m][k] Y[n][k] = 2^(e_m + f_n) sum_{s,t} 2^-(8(s+t)-2) sum_k a_s b_t .
+// Each inner sum over at most `kc` values of k is an integer below 2^24 in
+// magnitude, so the tensor cores' FP32 accumulation of it is exact (this is the
+// error-free splitting of Ozaki et al., Numer. Algorithms 59 (2012) 95).
+// Products with s + t <= KEEP are formed; products of equal s + t share one
+// tensor-memory accumulator; after every kc values of k the accumulators are
+// drained into a signed 64-bit fixed-point sum with unit 2^-F.  The result is
+// exact up to the dropped slice products and the rounding at 2^-F.
+#pragma once
+#include <cuda.h>
+#include "internal.cuh"
+
+namespace cd {
+
+struct OzakiPlan {
+  int SA = 3, SB = 3, KEEP = 4;   // slices of A and B, largest s + t kept
+  int F = 40;                     // fixed-point fraction bits of the output
+};
+
+// Slice tensors: bf16 [S][rows][kpitch] (k contiguous).  Output: int64
+// D[n][m] (leading dimension ldd, column n = row of B) accumulated with
+// atomicAdd over k in [0, kdim) split into `ksplit` CTA slabs.
+int ozaki_gemm(const OzakiPlan& plan, const void* As, int64_t a_rows, int64_t a_kpitch,
+               const void* Bs, int64_t b_rows, int64_t b_kpitch, int64_t kdim,
+               unsigned long long* D, int64_t ldd, int ksplit, int* err_dev, cudaStream_t st);
+
+// Slicing: x = X / 2^e (row exponent e given) -> S bf16 integer slices.
+// src element (r, k) at src[r * src_rs + k * src_ks]; dst[s][r][k0 + k] with pitch kpitch.
+int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int64_t rows, int64_t kcount,
+                          const int32_t* row_exp, int S, void* dst, int64_t dst_rows, int64_t kpitch, int64_t k0,
+                          cudaStream_t st);
+
+}  // namespace cd

@@ -1,0 +1,169 @@
+// pivot.cu -- kernel (b): vector finalisation, residual-diagonal update and the
+// global argmax of the residual diagonal (ties to the lowest row index).
+//
+// One step of the recursion of Sec. 2 for pivot row p:
+//   L^K_r = (col_r - sum_{J in [Kb,K)} L^J_r L^J_p) / sqrt(D_p)   Eq. (subtr)
+//   D'_r  = D_r - (L^K_r)^2                                       Eq. (diag)
+// where col already holds (r|p) - sum_{J<Kb} L^J_r L^J_p (column-update GEMM)
+// and the vectors of the current block [Kb, K) are applied here.  D is double
+// buffered (read D, write D') so that D_p stays readable by every CTA.
+// The argmax is reduced warp -> CTA (shuffles) -> grid (last CTA to finish).
+#include <float.h>
+#include "internal.cuh"
+#include "pivot.cuh"
+
+namespace cd {
+namespace {
+
+__device__ __forceinline__ bool better(double v1, int64_t i1, double v2, int64_t i2) {
+  return v1 > v2 || (v1 == v2 && i1 < i2);
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, int64_t& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    int64_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (better(v2, i2, v, i)) { v = v2; i = i2; }
+  }
+}
+
+// block-level argmax of (v, i) held by every thread; result valid in thread 0
+__device__ void block_argmax(double& v, int64_t& i) {
+  __shared__ double sv[32];
+  __shared__ int64_t si[32];
+  warp_argmax(v, i);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sv[w] = v; si[w] = i; }
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (w == 0) {
+    v = lane < nw ? sv[lane] : -DBL_MAX;
+    i = lane < nw ? si[lane] : INT64_MAX;
+    warp_argmax(v, i);
+  }
+  __syncthreads();
+}
+
+// grid-level finish: every CTA writes its partial; the last one reduces them
+__device__ void grid_finish(double v, int64_t i, int bad, StepScratch* sc, StepResult* res) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    sc->part_val[blockIdx.x] = v;
+    sc->part_idx[blockIdx.x] = i;
+    if (bad) atomicOr(&sc->bad, 1);
+    __threadfence();
+    unsigned t = atomicAdd(&sc->counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double bv = -DBL_MAX;
+  int64_t bi = INT64_MAX;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    double v2 = ((volatile double*)sc->part_val)[b];
+    int64_t i2 = ((volatile int64_t*)sc->part_idx)[b];
+    if (better(v2, i2, bv, bi)) { bv = v2; bi = i2; }
+  }
+  block_argmax(bv, bi);
+  if (threadIdx.x == 0) {
+    res->dmax = bv;
+    res->idx = bi;
+    res->bad = *(volatile int*)&sc->bad;
+    sc->bad = 0;
+    sc->counter = 0;
+    __threadfence();
+  }
+}
+
+__global__ void __launch_bounds__(kStepThreads) argmax_kernel(const double* __restrict__ D, int64_t n,
+                                                              StepScratch* sc, StepResult* res) {
+  double bv = -DBL_MAX;
+  int64_t bi = INT64_MAX;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double d = D[r];
+    if (better(d, r, bv, bi)) { bv = d; bi = r; }
+  }
+  block_argmax(bv, bi);
+  grid_finish(bv, bi, 0, sc, res);
+}
+
+__global__ void __launch_bounds__(kStepThreads) finalize_kernel(
+    const double* __restrict__ col, const double* __restrict__ L, int64_t ld, int64_t Kb, int64_t K,
+    int64_t prow, const double* __restrict__ Din, double* __restrict__ Dout, double* __restrict__ Lout,
+    int64_t n, double neg_tol, StepScratch* sc, StepResult* res) {
+  __shared__ double g[kMaxBlock];
+  const int nk = (int)(K - Kb);
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) g[k] = L[(Kb + k) * ld + prow];
+  __syncthreads();
+  const double dp = Din[prow];
+  const double inv = 1.0 / sqrt(dp);
+  double bv = -DBL_MAX;
+  int64_t bi = INT64_MAX;
+  int bad = 0;
+  const double* Lb = L + Kb * ld;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = col[r];
+    int k = 0;
+    for (; k + 4 <= nk; k += 4) {
+      double a0 = Lb[(k + 0) * ld + r], a1 = Lb[(k + 1) * ld + r];
+      double a2 = Lb[(k + 2) * ld + r], a3 = Lb[(k + 3) * ld + r];
+      acc = fma(-a0, g[k + 0], acc);
+      acc = fma(-a1, g[k + 1], acc);
+      acc = fma(-a2, g[k + 2], acc);
+      acc = fma(-a3, g[k + 3], acc);
+    }
+    for (; k < nk; ++k) acc = fma(-Lb[k * ld + r], g[k], acc);
+    const double v = acc * inv;
+    Lout[r] = v;
+    const double d = fma(-v, v, Din[r]);
+    Dout[r] = d;
+    if (d < neg_tol) bad = 1;
+    if (better(d, r, bv, bi)) { bv = d; bi = r; }
+  }
+  block_argmax(bv, bi);
+  grid_finish(bv, bi, bad, sc, res);
+}
+
+// Bg[k][j] = L[k][rows[j]] for k in [k0, k1), j < nb (row-major, leading dim nb)
+__global__ void gather_kernel(const double* __restrict__ L, int64_t ld, const int64_t* __restrict__ rows, int nb,
+                              int64_t k0, int64_t k1, double* __restrict__ Bg) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nk = k1 - k0;
+  if (t >= nk * nb) return;
+  const int64_t k = t / nb;
+  const int j = (int)(t % nb);
+  Bg[t] = L[(k0 + k) * ld + rows[j]];
+}
+
+}  // namespace
+
+int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st) {
+  argmax_kernel<<<kStepGrid, kStepThreads, 0, st>>>(D, n, sc, res);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, int64_t K, int64_t prow,
+                    const double* Din, double* Dout, double* Lout, int64_t n, double neg_tol,
+                    StepScratch* sc, StepResult* res, cudaStream_t st) {
+  if (K - Kb > kMaxBlock) { set_error("finalize: block too large"); return CD_EINVAL; }
+  finalize_kernel<<<kStepGrid, kStepThreads, 0, st>>>(col, L, ld, Kb, K, prow, Din, Dout, Lout, n, neg_tol, sc, res);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                  double* Bg, cudaStream_t st) {
+  int64_t tot = (k1 - k0) * nb;
+  if (tot <= 0) return CD_OK;
+  gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, ld, rows_dev, nb, k0, k1, Bg);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+}  // namespace cd

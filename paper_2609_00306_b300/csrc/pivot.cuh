@@ -1,0 +1,54 @@
+// pivot.cuh -- step kernels of the pivoted decomposition (see pivot.cu).
+#pragma once
+#include "internal.cuh"
+
+namespace cd {
+
+constexpr int kStepThreads = 256;
+constexpr int kStepGrid = 148 * 4;     // 4 CTAs per SM on 148 SMs
+constexpr int kMaxBlock = 256;          // largest speculative block
+
+struct StepResult {        // written by the last CTA of a step kernel
+  double dmax;             // max residual diagonal after the step
+  int64_t idx;             // its row (lowest on ties)
+  int32_t bad;             // 1 if some D < neg_tol (not PSD)
+  int32_t pad;
+};
+
+struct StepScratch {       // device scratch of the grid-wide argmax
+  double part_val[kStepGrid];
+  int64_t part_idx[kStepGrid];
+  unsigned counter;        // CTAs finished (reset by the last one)
+  int bad;
+};
+
+int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st);
+int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, int64_t K, int64_t prow,
+                    const double* Din, double* Dout, double* Lout, int64_t n, double neg_tol,
+                    StepScratch* sc, StepResult* res, cudaStream_t st);
+int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                  double* Bg, cudaStream_t st);
+
+// column update (colupd.cu): cols[slot[j]] -= L[k0:k1]^T Bg  (Bg row-major [k1-k0][nb])
+int launch_colupd(double* cols, int64_t ld, const int32_t* slots_dev, int nb, const double* L,
+                  int64_t k0, int64_t k1, const double* Bg, int64_t n, cudaStream_t st);
+
+// J / K helpers (jk.cu)
+int launch_density_packed(const double* C, int N, int O, const int32_t* mu, const int32_t* nu, int64_t n,
+                          double* d, cudaStream_t st);
+template <class T>
+int launch_gemv_rows(const T* L, int64_t ld, int64_t M, int64_t n, const double* x, double* y, cudaStream_t st);
+template <class T>
+int launch_gemv_cols(const T* L, int64_t ld, int64_t M, int64_t n, const double* v, double* y, cudaStream_t st);
+int launch_unpack_sym(const double* packed, const int32_t* mu, const int32_t* nu, int64_t n, int N, double* out,
+                      cudaStream_t st);
+template <class T>
+int launch_unpack_vectors(const T* L, int64_t ld, int64_t P0, int Pc, const int32_t* mu, const int32_t* nu,
+                          int64_t n, int N, T* out, cudaStream_t st);
+// generic FP64 GEMM: C[b] (+)= alpha * A[b] B[b]; element (i,k) of A at A + i*ars + k*acs + b*abs
+int launch_dgemm(int m, int n, int k, int batch, double alpha,
+                 const double* A, int64_t ars, int64_t acs, int64_t abs_,
+                 const double* B, int64_t brs, int64_t bcs, int64_t bbs,
+                 double* C, int64_t ldc, int64_t cbs, bool reduce_batch, cudaStream_t st);
+
+}  // namespace cd
