@@ -44,10 +44,11 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--jk", choices=["fp64", "bf16x3"], default=None,
-                    help="J/K mode inside the step (default: bf16x3 when available, else fp64)")
+    ap.add_argument("--jk", choices=["fp64", "bf16x3", "bf16x4"], default="bf16x4",
+                    help="J/K mode inside the step (default: bf16x4, FP32 vectors + 4-slice tensor-core products)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-jk-alone", action="store_true", help="skip the separate J/K timings (FP64 K is slow)")
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     return ap.parse_args()
 
@@ -151,6 +152,18 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 16384, sub_
 
 
 # ------------------------------------------------------------------- ours ---
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _sliced(f) -> bool:
+    return bool(f.stats().get("sliced", 0.0))
+
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2609_00306_b300 as cd
@@ -163,8 +176,9 @@ def run_ours(args, rank, world):
     s = synth.make_workload(args.workload)
     N, O = s.n_basis, s.n_occ
     stream = torch.cuda.current_stream()
-    jk_mode = {"fp64": cd.CD_JK_FP64, "bf16x3": cd.CD_JK_BF16X3}[args.jk or "fp64"]
-    vec_prec = cd.CD_VEC_FP32 if jk_mode == cd.CD_JK_BF16X3 else cd.CD_FP64
+    modes = {"fp64": cd.CD_JK_FP64, "bf16x3": cd.CD_JK_BF16X3, "bf16x4": cd.CD_JK_BF16X4}
+    jk_mode = modes[args.jk]
+    vec_prec = cd.CD_FP64 if jk_mode == cd.CD_JK_FP64 else cd.CD_VEC_FP32
     C_dev = torch.tensor(s.C_occ, device=dev)
     J_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
     K_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
@@ -208,9 +222,13 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     st = {k: float(np.mean([x[k] for x in stats])) for k in stats[0]}
-    # J and K alone, both modes, device buffers (kernel-only numbers behind the step)
+    # J and K alone, both modes, on the last step's factor (device buffers), and
+    # the mixed-precision error against the FP64 contraction of the same vectors
     jk = {}
-    for name, mode in (("fp64", cd.CD_JK_FP64), ("bf16x3", cd.CD_JK_BF16X3)):
+    res = {}
+    for name, mode in modes.items():
+        if args.no_jk_alone:
+            break
         try:
             torch.cuda.synchronize()
             ev0.record(stream)
@@ -218,25 +236,51 @@ def run_ours(args, rank, world):
             ev1.record(stream)
             torch.cuda.synchronize()
             jk[name + "_ms"] = ev0.elapsed_time(ev1)
+            res[name] = (J_dev.cpu().numpy(), K_dev.cpu().numpy())
         except cd.CDError as e:
             jk[name + "_ms"] = None
             jk[name + "_error"] = str(e)
-    # roofline of the dominant kernel: the FP64 column-update GEMM
+    Dm = 2.0 * s.C_occ @ s.C_occ.T
+    for mx in ("bf16x3", "bf16x4"):
+        if "fp64" in res and mx in res:
+            (J64, K64), (Jm, Km) = res["fp64"], res[mx]
+            jk[mx + "_vs_fp64"] = {
+                "max_dJ_rel": float(np.max(np.abs(Jm - J64)) / np.max(np.abs(J64))),
+                "max_dK_rel": float(np.max(np.abs(Km - K64)) / np.max(np.abs(K64))),
+                "dtrDJ_rel": float(abs(np.sum(Dm * (Jm - J64))) / abs(np.sum(Dm * J64))),
+                "dtrDK_rel": float(abs(np.sum(Dm * (Km - K64))) / abs(np.sum(Dm * K64))),
+            }
+            if jk.get("fp64_ms") and jk.get(mx + "_ms"):
+                jk[mx + "_speedup_over_fp64"] = jk["fp64_ms"] / jk[mx + "_ms"]
+    # roofline of the dominant kernel of the step
     peak_fp64 = 148 * 2 * 2 * 2.032e9 / 1e12  # TFLOP/s: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz
-    upd_tflops = st["colupd_flops"] / (st["ms_colupd"] * 1e-3) / 1e12 if st["ms_colupd"] > 0 else None
-    roof = {"kernel": "colupd_kernel (FP64 column update, Eq. subtr)", "bound": "alu",
-            "achieved": upd_tflops, "peak": peak_fp64, "unit": "TFLOP/s",
-            "frac": (upd_tflops / peak_fp64) if upd_tflops else None, "traffic": None,
-            "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (recipe unit counts "
-                           "and clocks; microbenchmark measured 1.128 TFLOP/s at 1935 MHz)",
-            "share_of_step": st["ms_colupd"] / ms if ms else None}
+    peaks = _measured_peaks()
+    sliced = st.get("ms_colupd", 0) > 0 and _sliced(f)
+    upd_fp64eq = st["colupd_flops"] / (st["ms_colupd"] * 1e-3) / 1e12 if st["ms_colupd"] > 0 else None
+    if sliced:
+        # 28 BF16 slice products (s + t <= 8 of 7 x 7) per FP64-equivalent multiply-add
+        ach = 28.0 * upd_fp64eq if upd_fp64eq else None
+        pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1800.0
+        roof = {"kernel": "ozaki_kernel<7,7,8> (sliced column update, Eq. subtr)", "bound": "tensor",
+                "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": (ach / pk) if ach else None,
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16 (sustained) - of measured",
+                "fp64_equivalent_tflops": upd_fp64eq, "fp64_pipe_peak_tflops": peak_fp64,
+                "share_of_step": st["ms_colupd"] / ms if ms else None}
+    else:
+        roof = {"kernel": "colupd_kernel (FP64 column update, Eq. subtr)", "bound": "alu",
+                "achieved": upd_fp64eq, "peak": peak_fp64, "unit": "TFLOP/s",
+                "frac": (upd_fp64eq / peak_fp64) if upd_fp64eq else None, "traffic": None,
+                "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (recipe unit counts "
+                               "and clocks; microbenchmark measured 1.128 TFLOP/s at 1935 MHz)",
+                "share_of_step": st["ms_colupd"] / ms if ms else None}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if jk_mode == cd.CD_JK_FP64 else "f64+bf16x3",
+           "vs_baseline": None, "dtype": "f64" if jk_mode == cd.CD_JK_FP64 else "f64+" + args.jk,
            "data": "synthetic (seeded lattice s+p system; no public dataset)",
            "config": {"workload": f"{args.workload}: N={N} s+p, {s.basis.n_shells} shells, tau={s.tau:g}, "
                                   f"Schwarz {s.schwarz:g}, n_occ={O}",
-                      "n_basis": N, "rows": f.n_rows, "M": M, "max_resid": resid, "jk_mode": args.jk or "fp64",
+                      "n_basis": N, "rows": f.n_rows, "M": M, "max_resid": resid, "jk_mode": args.jk,
+                      "update": "sliced tensor-core (7 x 8-bit slices)" if sliced else "FP64 DFMA",
                       "l2": "inputs (vectors, 10s of GB) larger than L2; 256 MB flush between steps",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "breakdown_ms": {"system": st["ms_system"], "eri_columns": st["ms_eri"], "column_update": st["ms_colupd"],

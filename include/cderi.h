@@ -47,7 +47,8 @@ extern "C" {
 #define CD_VEC_FP32      1  /* after the (FP64) factorisation, vectors rounded once to FP32 */
 
 #define CD_JK_FP64       0  /* J and K contractions in FP64 */
-#define CD_JK_BF16X3     1  /* FP32 vectors, 3-way BF16 split tensor-core products, FP32 accumulate */
+#define CD_JK_BF16X3     1  /* FP32 vectors; BF16 tensor-core products of 3 exact 8-bit slices per operand row */
+#define CD_JK_BF16X4     2  /* as CD_JK_BF16X3 with 4 slices (32-bit fixed point below each row maximum) */
 #define CD_JK_DEVICE     0x100 /* flag: C_occ, J, K are device pointers (else host) */
 #define CD_JK_ONLY_J     0x200 /* flag: compute J only (K may be NULL) */
 #define CD_JK_ONLY_K     0x400 /* flag: compute K only (J may be NULL) */
@@ -76,7 +77,12 @@ typedef struct {
   double  mem_budget_gb;/* device footprint cap for the factor (0 = 90% of free memory) */
   const int64_t* forced_pivots; /* test hook: host list of pivot rows to follow (NULL = argmax) */
   int64_t n_forced;
+  int32_t update;       /* column update of Eq. (subtr): CD_UPDATE_SLICE (default) or CD_UPDATE_FP64 */
+  int32_t reserved;
 } cd_opts_t;
+
+#define CD_UPDATE_SLICE  0  /* exact-slice BF16 tensor-core GEMM, 7 slices (56-bit fixed point per row) */
+#define CD_UPDATE_FP64   1  /* register-tiled FP64 DFMA GEMM */
 
 typedef struct cd_system cd_system_t;   /* basis + screened pair list on the device */
 typedef struct cd_factor cd_factor_t;   /* Cholesky basis and vectors on the device */
@@ -138,8 +144,8 @@ long long cd_kernel_launches(void);
 /* J_{mu nu} = sum_P L^P_{mu nu} sum_{sigma rho} L^P_{sigma rho} D_{sigma rho},
  * K_{mu nu} = sum_P sum_{sigma rho} L^P_{mu sigma} D_{sigma rho} L^P_{rho nu},
  * D = 2 C_occ C_occ^T.  C_occ [N][n_occ], J, K [N][N], row-major; host pointers
- * unless CD_JK_DEVICE.  mode: CD_JK_FP64 or CD_JK_BF16X3 (needs FP32 vectors,
- * converts on the fly when they are FP64).  J (kernel d): two streamed GEMVs
+ * unless CD_JK_DEVICE.  mode: CD_JK_FP64, CD_JK_BF16X3 or CD_JK_BF16X4 (mixed:
+ * uses the FP32 vectors, converting on the fly when only FP64 ones are stored).  J (kernel d): two streamed GEMVs
  * over the vectors.  K (kernel e): B^P = L^P C_occ, K = 2 sum_P B^P B^P^T. */
 int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ,
           double* J, double* K, int32_t mode, void* stream);

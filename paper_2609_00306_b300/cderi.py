@@ -18,9 +18,10 @@ LIB_PATH = os.path.join(_HERE, "libcderi.so")
 
 CD_OK, CD_EINVAL, CD_ENOMEM, CD_ENOTPSD, CD_ETIMEOUT, CD_ECUDA = 0, -1, -2, -3, -4, -5
 CD_FP64, CD_VEC_FP32 = 0, 1
-CD_JK_FP64, CD_JK_BF16X3 = 0, 1
+CD_JK_FP64, CD_JK_BF16X3, CD_JK_BF16X4 = 0, 1, 2
 CD_JK_DEVICE, CD_JK_ONLY_J, CD_JK_ONLY_K = 0x100, 0x200, 0x400
 CD_MAX_PRIM = 16
+CD_UPDATE_SLICE, CD_UPDATE_FP64 = 0, 1
 
 _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENOTPSD",
              CD_ETIMEOUT: "CD_ETIMEOUT", CD_ECUDA: "CD_ECUDA"}
@@ -45,7 +46,8 @@ class cd_basis_t(ctypes.Structure):
 class cd_opts_t(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("schwarz", ctypes.c_double), ("vec_precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("max_vectors", ctypes.c_int64), ("mem_budget_gb", ctypes.c_double),
-                ("forced_pivots", ctypes.c_void_p), ("n_forced", ctypes.c_int64)]
+                ("forced_pivots", ctypes.c_void_p), ("n_forced", ctypes.c_int64),
+                ("update", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -118,9 +120,10 @@ class _BasisArgs:
 
 
 def make_opts(tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
-              max_vectors: int = 0, mem_budget_gb: float = 0.0, forced: Optional[Sequence[int]] = None):
+              max_vectors: int = 0, mem_budget_gb: float = 0.0, forced: Optional[Sequence[int]] = None,
+              update: int = CD_UPDATE_SLICE):
     o = cd_opts_t(float(tau), float(schwarz), int(vec_precision), int(block), int(max_vectors),
-                  float(mem_budget_gb), None, 0)
+                  float(mem_budget_gb), None, 0, int(update), 0)
     keep = None
     if forced is not None:
         keep = np.ascontiguousarray(forced, dtype=np.int64)
@@ -204,7 +207,7 @@ class Factor:
         s = np.zeros(16)
         _check(load().cd_factor_stats(self._h, _p(s)))
         keys = ["ms_system", "ms_eri", "ms_colupd", "ms_steps", "ms_select", "ms_total", "blocks", "eri_columns",
-                "colupd_flops", "eri_entries", "M"]
+                "colupd_flops", "eri_entries", "M", "sliced"]
         return dict(zip(keys, s.tolist()))
 
     def jk(self, C_occ, mode: int = CD_JK_FP64, stream=None, want=("J", "K")):
@@ -247,10 +250,11 @@ class Factor:
 
 
 def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
-                  max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None) -> Factor:
+                  max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
+                  update: int = CD_UPDATE_SLICE) -> Factor:
     """Full pipeline from a host basis (C ABI cd_eri_factor)."""
     args = _BasisArgs(basis)
-    o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced)
+    o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced, update)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor(ctypes.byref(args.s), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep
@@ -258,8 +262,9 @@ def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = 
 
 
 def cd_eri_factor_sys(system: System, tau: float, vec_precision: int = CD_FP64, block: int = 0,
-                      max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None) -> Factor:
-    o, keep = make_opts(tau, 0.0, vec_precision, block, max_vectors, mem_budget_gb, forced)
+                      max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
+                      update: int = CD_UPDATE_SLICE) -> Factor:
+    o, keep = make_opts(tau, 0.0, vec_precision, block, max_vectors, mem_budget_gb, forced, update)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor_sys(system._h, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep

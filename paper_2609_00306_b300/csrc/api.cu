@@ -10,6 +10,7 @@
 #include <vector>
 #include "internal.cuh"
 #include "pivot.cuh"
+#include "ozaki.cuh"
 
 namespace cd {
 static thread_local std::string g_err;
@@ -20,7 +21,7 @@ long long launch_counter() { return g_launches.load(); }
 int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st);
 int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
              const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
-             cudaStream_t st);
+             int S, cudaStream_t st);
 }  // namespace cd
 
 using namespace cd;
@@ -216,6 +217,9 @@ static void factor_release(cd_factor* f) {
 }
 
 namespace {
+constexpr int kSlices = 7;        // 8-bit slices per vector entry in the sliced update
+constexpr int kSliceF = 60;       // fixed-point fraction bits of the update (|sum| < 1 per unit scale)
+
 struct Work {  // scratch of one factorisation, freed at the end
   double* pool = nullptr;
   double* D0 = nullptr;
@@ -223,26 +227,53 @@ struct Work {  // scratch of one factorisation, freed at the end
   double* Bg = nullptr;
   int32_t* slots_dev = nullptr;
   int64_t* rows_dev = nullptr;
+  int64_t* valid_dev = nullptr;
   KetDesc* kets_dev = nullptr;
   StepScratch* sc = nullptr;
   StepResult* res_dev = nullptr;
   StepResult* res_h = nullptr;
   double* dh = nullptr;
   double* dp_h = nullptr;
+  // sliced update
+  void* Ls = nullptr;               // bf16 [kSlices][n][kcap]
+  void* Bs = nullptr;               // bf16 [kSlices][b][kcap]
+  unsigned long long* Dint = nullptr;  // int64 [b][ld]
+  int32_t* erow = nullptr;          // [n]
+  int* err = nullptr;
+  int64_t kcap = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   ~Work() {
     cudaFree(pool); cudaFree(D0); cudaFree(D1); cudaFree(Bg); cudaFree(slots_dev); cudaFree(rows_dev);
-    cudaFree(kets_dev); cudaFree(sc); cudaFree(res_dev);
+    cudaFree(valid_dev); cudaFree(kets_dev); cudaFree(sc); cudaFree(res_dev);
+    cudaFree(Ls); cudaFree(Bs); cudaFree(Dint); cudaFree(erow); cudaFree(err);
     cudaFreeHost(res_h); cudaFreeHost(dh); cudaFreeHost(dp_h);
     for (auto& e : ev) if (e) cudaEventDestroy(e);
   }
 };
 }  // namespace
 
-static int grow_vectors(cd_factor* f, int64_t newcap, int64_t K, cudaStream_t st) {
+// Grow the vector store to `newcap` vectors (and the slice store with it).
+static int grow_vectors(cd_factor* f, Work* w, bool slice, int b, int64_t newcap, int64_t K, cudaStream_t st) {
   double* nL = nullptr;
   CD_TRY(dalloc(&nL, (size_t)newcap * f->ld));
   if (K > 0) CD_CUDA(cudaMemcpyAsync(nL, f->L, sizeof(double) * K * f->ld, cudaMemcpyDeviceToDevice, st));
+  if (slice) {
+    const int64_t nk = (newcap + 31) / 32 * 32;
+    void* nLs = nullptr;
+    void* nBs = nullptr;
+    int rc = dalloc((uint16_t**)&nLs, (size_t)kSlices * f->n * nk);
+    if (rc == CD_OK) rc = dalloc((uint16_t**)&nBs, (size_t)kSlices * b * nk);
+    if (rc != CD_OK) { cudaFree(nL); cudaFree(nLs); return rc; }
+    if (K > 0 && f->n > 0)
+      CD_CUDA(cudaMemcpy2DAsync(nLs, nk * 2, w->Ls, w->kcap * 2, K * 2, (size_t)kSlices * f->n,
+                                cudaMemcpyDeviceToDevice, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+    cudaFree(w->Ls);
+    cudaFree(w->Bs);
+    w->Ls = nLs;
+    w->Bs = nBs;
+    w->kcap = nk;
+  }
   CD_CUDA(cudaStreamSynchronize(st));
   cudaFree(f->L);
   f->L = nL;
@@ -257,6 +288,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   const int b = o->block ? o->block : 64;
   if (b < 1 || b > kMaxBlock) { set_error("block must be in [1, 256]"); return CD_EINVAL; }
   if (o->vec_precision != CD_FP64 && o->vec_precision != CD_VEC_FP32) { set_error("bad vec_precision"); return CD_EINVAL; }
+  if (o->update != CD_UPDATE_SLICE && o->update != CD_UPDATE_FP64) { set_error("bad update mode"); return CD_EINVAL; }
+  const bool slice = o->update == CD_UPDATE_SLICE;
   const bool forced = o->forced_pivots != nullptr;
   const int64_t nf = forced ? o->n_forced : 0;
   const int64_t n = s->n_rows, ld = s->n_rows_pad, N = s->hb.nbf;
@@ -271,10 +304,12 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   size_t freeb = 0, totb = 0;
   CD_CUDA(cudaMemGetInfo(&freeb, &totb));
   const double budget = o->mem_budget_gb > 0 ? o->mem_budget_gb * 1e9 : 0.9 * (double)freeb;
-  const double fixed = 8.0 * ld * (b + 2) + 8.0 * Mmax * b;
-  int64_t Mcap = std::min<int64_t>(Mmax, std::max<int64_t>(256, 6 * N));
-  if (fixed + 8.0 * ld * Mcap > budget) {
-    Mcap = (int64_t)((budget - fixed) / (8.0 * ld));
+  // bytes per vector of capacity, and the fixed part
+  const double per_vec = 8.0 * ld + (slice ? 2.0 * kSlices * (n + b) : 0.0);
+  const double fixed = 8.0 * ld * (b + 2) + 8.0 * Mmax * b + (slice ? 8.0 * b * ld + 4.0 * n : 0.0);
+  int64_t Mcap = std::min<int64_t>(Mmax, std::max<int64_t>(256, 5 * N));
+  if (fixed + per_vec * Mcap > budget) {
+    Mcap = (int64_t)((budget - fixed) / per_vec);
     if (Mcap < 1) { set_error("device memory budget too small for the decomposition"); return CD_ENOMEM; }
   }
   f->sys = s;
@@ -290,9 +325,20 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   CD_TRY(dalloc(&w.Bg, (size_t)Mmax * b));
   CD_TRY(dalloc(&w.slots_dev, (size_t)b));
   CD_TRY(dalloc(&w.rows_dev, (size_t)b));
+  CD_TRY(dalloc(&w.valid_dev, (size_t)b));
   CD_TRY(dalloc(&w.kets_dev, (size_t)b));
   CD_TRY(dalloc(&w.sc, 1));
   CD_TRY(dalloc(&w.res_dev, 1));
+  if (slice) {
+    w.kcap = (Mcap + 31) / 32 * 32;
+    CD_TRY(dalloc((uint16_t**)&w.Ls, (size_t)kSlices * std::max<int64_t>(n, 1) * w.kcap));
+    CD_TRY(dalloc((uint16_t**)&w.Bs, (size_t)kSlices * b * w.kcap));
+    CD_TRY(dalloc(&w.Dint, (size_t)b * ld));
+    CD_TRY(dalloc(&w.erow, (size_t)std::max<int64_t>(n, 1)));
+    CD_TRY(dalloc(&w.err, 1));
+    CD_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+    CD_TRY(launch_row_exp_sqrt(s->diag_dev, n, w.erow, st));
+  }
   CD_CUDA(cudaMallocHost(&w.res_h, sizeof(StepResult)));
   CD_CUDA(cudaMallocHost(&w.dh, sizeof(double) * std::max<int64_t>(n, 1)));
   CD_CUDA(cudaMallocHost(&w.dp_h, sizeof(double)));
@@ -315,6 +361,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   } else {
     res.dmax = -1.0; res.idx = -1; res.bad = 0;
   }
+  OzakiPlan plan;
+  plan.SA = plan.SB = kSlices;
+  plan.KEEP = kSlices + 1;
+  plan.F = kSliceF;
   std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
   std::unordered_map<int64_t, int> row2slot;
   double t_eri = 0, t_upd = 0, t_sel = 0, upd_flops = 0, eri_ints = 0;
@@ -353,8 +403,6 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         slot_row[sl] = -1;
       }
     std::vector<KetDesc> kets;
-    std::vector<int32_t> new_slots;
-    std::vector<int64_t> new_rows;
     int free_sl = 0;
     for (int64_t r : cand) {
       if (row2slot.count(r)) continue;
@@ -363,8 +411,6 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       slot_valid[free_sl] = 0;
       row2slot[r] = free_sl;
       kets.push_back(ket_of_row(s, r, free_sl));
-      new_slots.push_back(free_sl);
-      new_rows.push_back(r);
     }
     ++nblocks;
     ncols += (int64_t)kets.size();
@@ -377,22 +423,40 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     }
     CD_CUDA(cudaEventRecord(w.ev[1], st));
     // ---- bring every pool column up to date with vectors [valid, K)
-    std::unordered_map<int64_t, std::vector<int>> groups;
-    for (int sl = 0; sl < b; ++sl)
-      if (slot_row[sl] >= 0 && slot_valid[sl] < K) groups[slot_valid[sl]].push_back(sl);
-    for (auto& g : groups) {
-      const int64_t k0 = g.first;
-      std::vector<int32_t> sl(g.second.begin(), g.second.end());
-      std::vector<int64_t> rr;
-      for (int x : sl) rr.push_back(slot_row[x]);
+    if (slice) {
+      std::vector<int32_t> sl;
+      std::vector<int64_t> rr, vv;
+      for (int x = 0; x < b; ++x)
+        if (slot_row[x] >= 0 && slot_valid[x] < K) { sl.push_back(x); rr.push_back(slot_row[x]); vv.push_back(slot_valid[x]); }
       const int nb = (int)sl.size();
-      CD_CUDA(cudaMemcpyAsync(w.slots_dev, sl.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
-      CD_CUDA(cudaMemcpyAsync(w.rows_dev, rr.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
-      CD_TRY(launch_gather(f->L, ld, w.rows_dev, nb, k0, K, w.Bg, st));
-      CD_TRY(launch_colupd(w.pool, ld, w.slots_dev, nb, f->L, k0, K, w.Bg, n, st));
-      upd_flops += 2.0 * (double)n * nb * (double)(K - k0);
-      // the host vectors must stay alive until the copies above complete
-      CD_CUDA(cudaStreamSynchronize(st));
+      if (nb > 0 && K > 0) {
+        CD_CUDA(cudaMemcpyAsync(w.slots_dev, sl.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
+        CD_CUDA(cudaMemcpyAsync(w.rows_dev, rr.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+        CD_CUDA(cudaMemcpyAsync(w.valid_dev, vv.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+        CD_TRY(launch_gather_slices(w.Ls, n, w.kcap, w.rows_dev, w.valid_dev, nb, kSlices, K, w.Bs, w.kcap, st));
+        CD_CUDA(cudaMemsetAsync(w.Dint, 0, sizeof(unsigned long long) * nb * ld, st));
+        CD_TRY(ozaki_gemm(plan, w.Ls, n, w.kcap, w.Bs, nb, w.kcap, K, w.Dint, ld, 1, w.err, st));
+        CD_TRY(launch_colupd_finalize(w.Dint, ld, n, nb, w.erow, w.rows_dev, w.slots_dev, plan.F, w.pool, ld, st));
+        for (int x = 0; x < nb; ++x) upd_flops += 2.0 * (double)n * (double)(K - vv[x]);
+        CD_CUDA(cudaStreamSynchronize(st));  // host vectors above stay alive until the copies are done
+      }
+    } else {
+      std::unordered_map<int64_t, std::vector<int>> groups;
+      for (int sl = 0; sl < b; ++sl)
+        if (slot_row[sl] >= 0 && slot_valid[sl] < K) groups[slot_valid[sl]].push_back(sl);
+      for (auto& g : groups) {
+        const int64_t k0 = g.first;
+        std::vector<int32_t> sl(g.second.begin(), g.second.end());
+        std::vector<int64_t> rr;
+        for (int x : sl) rr.push_back(slot_row[x]);
+        const int nb = (int)sl.size();
+        CD_CUDA(cudaMemcpyAsync(w.slots_dev, sl.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
+        CD_CUDA(cudaMemcpyAsync(w.rows_dev, rr.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
+        CD_TRY(launch_gather(f->L, ld, w.rows_dev, nb, k0, K, w.Bg, st));
+        CD_TRY(launch_colupd(w.pool, ld, w.slots_dev, nb, f->L, k0, K, w.Bg, n, st));
+        upd_flops += 2.0 * (double)n * nb * (double)(K - k0);
+        CD_CUDA(cudaStreamSynchronize(st));
+      }
     }
     CD_CUDA(cudaEventRecord(w.ev[2], st));
     for (int sl = 0; sl < b; ++sl)
@@ -429,10 +493,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
           set_error("number of vectors exceeds max_vectors = " + std::to_string(Mmax));
           return CD_ENOMEM;
         }
-        int64_t nc = std::min<int64_t>(Mmax, f->Mcap + f->Mcap / 2 + 1);
-        if (fixed + 8.0 * ld * nc > budget) nc = (int64_t)((budget - fixed) / (8.0 * ld));
+        int64_t nc = std::min<int64_t>(Mmax, f->Mcap + f->Mcap / 4 + 64);
+        if (fixed + per_vec * nc > budget) nc = (int64_t)((budget - fixed) / per_vec);
         if (nc <= f->Mcap) { set_error("device memory budget exhausted at M = " + std::to_string(K)); return CD_ENOMEM; }
-        CD_TRY(grow_vectors(f, nc, K, st));
+        CD_TRY(grow_vectors(f, &w, slice, b, nc, K, st));
       }
       const double gap = forced ? res.dmax - dp : 0.0;
       CD_TRY(launch_finalize(w.pool + (int64_t)sl * ld, f->L, ld, Kb, K, p, Dcur, Dnext, f->L + K * ld, n, neg_tol,
@@ -459,7 +523,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         return CD_ENOTPSD;
       }
     }
-    if (first) {  // block ended without a step (cannot happen in free mode; forced lists may)
+    if (first) {  // block ended without a step (only possible with a forced list)
       CD_CUDA(cudaStreamSynchronize(st));
       float a = 0, c = 0;
       cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
@@ -471,6 +535,15 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         return CD_EINVAL;
       }
     }
+    // slices of this block's vectors, for the next block's update
+    if (slice && !done && K > Kb)
+      CD_TRY(launch_slice_rows_f64(f->L + Kb * ld, 1, ld, n, K - Kb, w.erow, kSlices, w.Ls, n, w.kcap, Kb, st));
+  }
+  if (slice) {
+    int herr = 0;
+    CD_CUDA(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+    if (herr) { set_error("tensor-core update: a bounded pipeline wait timed out"); return CD_ETIMEOUT; }
   }
   f->M = K;
   f->resid_max = res.dmax;
@@ -478,6 +551,11 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   if (n > 0) {
     CD_CUDA(cudaMemcpyAsync(f->resid.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   }
+  // the slice store is no longer needed: release it before the FP32 copy
+  CD_CUDA(cudaStreamSynchronize(st));
+  cudaFree(w.Ls); w.Ls = nullptr;
+  cudaFree(w.Bs); w.Bs = nullptr;
+  cudaFree(w.pool); w.pool = nullptr;
   if (f->vec_precision == CD_VEC_FP32 && K > 0) {
     CD_TRY(dalloc(&f->L32, (size_t)K * ld));
     CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
@@ -495,6 +573,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   f->stats[8] = upd_flops;
   f->stats[9] = eri_ints;
   f->stats[10] = (double)K;
+  f->stats[11] = slice ? 1.0 : 0.0;
   return CD_OK;
 }
 
@@ -636,7 +715,7 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
   const bool dev = (mode & CD_JK_DEVICE) != 0;
   const bool wantJ = !(mode & CD_JK_ONLY_K), wantK = !(mode & CD_JK_ONLY_J);
   if ((wantJ && !J) || (wantK && !K)) { set_error("cd_jk: J or K is NULL"); return CD_EINVAL; }
-  if (m != CD_JK_FP64 && m != CD_JK_BF16X3) { set_error("cd_jk: unknown mode"); return CD_EINVAL; }
+  if (m != CD_JK_FP64 && m != CD_JK_BF16X3 && m != CD_JK_BF16X4) { set_error("cd_jk: unknown mode"); return CD_EINVAL; }
   cudaStream_t st = (cudaStream_t)stream;
   const int N = f->sys->hb.nbf, O = n_occ;
   const int64_t n = f->n, M = f->M, ld = f->ld;
@@ -662,7 +741,7 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
       return fail(CD_ECUDA);
     }
   }
-  if (m == CD_JK_BF16X3) {
+  if (m == CD_JK_BF16X3 || m == CD_JK_BF16X4) {
     const float* L32 = f->L32;
     float* tmp = nullptr;
     if (!L32) {
@@ -670,7 +749,8 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
       if ((rc = launch_to_fp32(f->L, ld, M, ld, tmp, st)) != CD_OK) { cudaFree(tmp); return fail(rc); }
       L32 = tmp;
     }
-    rc = jk_mixed(L32, ld, M, n, N, O, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, dJ, dK, wantJ, wantK, st);
+    rc = jk_mixed(L32, ld, M, n, N, O, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, dJ, dK, wantJ, wantK,
+                  m == CD_JK_BF16X4 ? 4 : 3, st);
     if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
     if (rc != CD_OK) return fail(rc);
   } else {

@@ -1,47 +1,231 @@
-// mixed.cu -- mixed-precision J/K: vectors stored FP32 (rounded once after the
-// FP64 factorisation); J accumulates FP32 vector entries against an FP64
-// density in FP64; K runs on the tensor cores (see kexchange.cu).
+// mixed.cu -- mixed-precision J/K.  The decomposition itself is FP64; the
+// vectors are rounded once to FP32 and contracted on the tensor cores:
+//   B^P = L^P C      (S BF16 slices of the FP32 rows of L^P and of C^T)
+//   K   = 2 sum_P B^P B^P^T   (S BF16 slices of the rows of B, kept in FP64)
+// Each product runs through the exact-slice GEMM (ozaki.cu): BF16 integer
+// slices, exact FP32 accumulation inside a k-chunk, 64-bit fixed-point sums;
+// the only roundings are the FP32 storage of L, the 8S-bit slicing of each
+// operand row below its maximum, and the final FP64 scaling.  J accumulates FP32 vector entries against the
+// FP64 packed density in FP64.
+#include <cuda_bf16.h>
+#include <algorithm>
 #include "internal.cuh"
+#include "ozaki.cuh"
 #include "pivot.cuh"
 
 namespace cd {
 namespace {
-__global__ void to_fp32_kernel(const double* __restrict__ src, int64_t ld, int64_t total, float* __restrict__ dst) {
+
+__global__ void to_fp32_kernel(const double* __restrict__ src, int64_t total, float* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = __double2float_rn(src[i]);
 }
+
+// one warp per row: e[r] = frexp exponent of max_k |X[r][k]| (0 for a zero row)
+template <class T>
+__global__ void row_exp_warp_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
+                                    int32_t* __restrict__ e) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  float m = 0.0f;
+  double md = 0.0;
+  for (int64_t c = lane; c < k; c += 32) md = fmax(md, fabs((double)X[r * ldx + c]));
+  (void)m;
+  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+  if (lane == 0) {
+    int ex = 0;
+    if (md > 0.0) frexp(md, &ex);
+    e[r] = ex;
+  }
+}
+
+// dst[s][r][k] = s-th 8-bit slice of X[r][k] / 2^e[r]  (S = 3 or 4 slices: 24 or 32 bits
+// of fixed point below the row maximum)
+template <class T>
+__global__ void slice3_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
+                              const int32_t* __restrict__ e, __nv_bfloat16* __restrict__ dst, int64_t kpitch, int S) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * kpitch) return;
+  const int64_t r = t / kpitch, c = t % kpitch;
+  double x = c < k ? ldexp((double)X[r * ldx + c], -e[r]) : 0.0;
+  double w = 128.0;
+  for (int s = 0; s < S; ++s) {
+    const double a = rint(x * w);
+    dst[((int64_t)s * rows + r) * kpitch + c] = __double2bfloat16(a);
+    x -= a / w;
+    w *= 256.0;
+  }
+}
+
+// B chunk from the fixed-point product: D[i][p*N + mu] (i < O) -> Bm[mu][p*Op + i]
+__global__ void half_finalize_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int Pc, int N, int O,
+                                     int Op, const int32_t* __restrict__ eL, const int32_t* __restrict__ eC, int F,
+                                     double* __restrict__ Bm) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)Pc * N * O;
+  if (t >= tot) return;
+  const int i = (int)(t % O);
+  const int64_t row = t / O;  // p*N + mu
+  const int p = (int)(row / N), mu = (int)(row % N);
+  const double v = ldexp((double)(long long)D[(int64_t)i * ldd + row], eL[row] + eC[i] - F);
+  Bm[(int64_t)mu * ((int64_t)Pc * Op) + (int64_t)p * Op + i] = v;
+}
+
+// K[mu][nu] += 2 * 2^(e_mu + e_nu - F) * D[nu][mu]
+__global__ void k_accumulate_kernel(const unsigned long long* __restrict__ D, int N, const int32_t* __restrict__ eB,
+                                    int F, double* __restrict__ K) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * N) return;
+  const int mu = (int)(t / N), nu = (int)(t % N);
+  K[t] += ldexp((double)(long long)D[(int64_t)nu * N + mu], eB[mu] + eB[nu] - F + 1);
+}
+
+template <class T>
+int launch_row_exp_warp(const T* X, int64_t ldx, int64_t rows, int64_t k, int32_t* e, cudaStream_t st) {
+  if (rows <= 0) return CD_OK;
+  row_exp_warp_kernel<T><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, st>>>(X, ldx, rows, k, e);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+template <class T>
+int launch_slice3(const T* X, int64_t ldx, int64_t rows, int64_t k, const int32_t* e, void* dst, int64_t kpitch,
+                  int S, cudaStream_t st) {
+  const int64_t tot = rows * kpitch;
+  if (tot <= 0) return CD_OK;
+  slice3_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch, S);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int ilog2_ceil(int64_t v) {
+  int l = 0;
+  while ((1ll << l) < v) ++l;
+  return l;
+}
+
 }  // namespace
 
 int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st) {
   const int64_t total = M * ld;
   if (total <= 0) return CD_OK;
   (void)n;
-  to_fp32_kernel<<<148 * 8, 256, 0, st>>>(src, ld, total, dst);
+  to_fp32_kernel<<<148 * 8, 256, 0, st>>>(src, total, dst);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
 }
 
+namespace {
+struct MixedBufs {
+  float* Lfull = nullptr;
+  void* Ls = nullptr;
+  void* Cs = nullptr;
+  double* Ct = nullptr;
+  int32_t *eL = nullptr, *eC = nullptr, *eB = nullptr;
+  unsigned long long *D1 = nullptr, *D2 = nullptr;
+  double* Bm = nullptr;
+  void* Bs = nullptr;
+  double *d = nullptr, *v = nullptr, *Jp = nullptr;
+  int* err = nullptr;
+  ~MixedBufs() {
+    cudaFree(Lfull); cudaFree(Ls); cudaFree(Cs); cudaFree(Ct); cudaFree(eL); cudaFree(eC); cudaFree(eB);
+    cudaFree(D1); cudaFree(D2); cudaFree(Bm); cudaFree(Bs); cudaFree(d); cudaFree(v); cudaFree(Jp); cudaFree(err);
+  }
+};
+template <class T>
+int mal(T** p, size_t n) {
+  if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("mixed J/K: device allocation failed");
+    return CD_ENOMEM;
+  }
+  return CD_OK;
+}
+__global__ void transpose_kernel(const double* __restrict__ C, int N, int O, double* __restrict__ Ct) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * O) return;
+  const int nu = (int)(t / O), i = (int)(t % O);
+  Ct[(int64_t)i * N + nu] = C[t];
+}
+}  // namespace
+
 int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
              const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
-             cudaStream_t st) {
-  if (wantK) {
-    set_error("cd_jk: the BF16x3 exchange kernel is not available in this build");
-    return CD_EINVAL;
-  }
+             int S, cudaStream_t st) {
+  MixedBufs b;
   if (wantJ) {
-    double *d = nullptr, *v = nullptr, *Jp = nullptr;
-    CD_CUDA(cudaMalloc(&d, sizeof(double) * std::max<int64_t>(n, 1)));
-    CD_CUDA(cudaMalloc(&v, sizeof(double) * std::max<int64_t>(M, 1)));
-    CD_CUDA(cudaMalloc(&Jp, sizeof(double) * std::max<int64_t>(n, 1)));
-    int rc = launch_density_packed(C_dev, N, O, mu, nu, n, d, st);
-    if (rc == CD_OK) rc = launch_gemv_rows<float>(L32, ld, M, n, d, v, st);
-    if (rc == CD_OK) rc = launch_gemv_cols<float>(L32, ld, M, n, v, Jp, st);
-    if (rc == CD_OK) rc = launch_unpack_sym(Jp, mu, nu, n, N, J_dev, st);
-    cudaStreamSynchronize(st);
-    cudaFree(d); cudaFree(v); cudaFree(Jp);
-    if (rc != CD_OK) return rc;
+    CD_TRY(mal(&b.d, (size_t)n));
+    CD_TRY(mal(&b.v, (size_t)M));
+    CD_TRY(mal(&b.Jp, (size_t)n));
+    CD_TRY(launch_density_packed(C_dev, N, O, mu, nu, n, b.d, st));
+    CD_TRY(launch_gemv_rows<float>(L32, ld, M, n, b.d, b.v, st));
+    CD_TRY(launch_gemv_cols<float>(L32, ld, M, n, b.v, b.Jp, st));
+    CD_TRY(launch_unpack_sym(b.Jp, mu, nu, n, N, J_dev, st));
   }
+  if (wantK) {
+    const int64_t Np = (N + 7) / 8 * 8;                     // k pitch of the first product (16-byte rows)
+    const int Op = (O + 63) / 64 * 64;                      // padded occupied count (k blocks of the second product)
+    // chunk of vectors: k-dim of the second product Pc*Op, scratch ~ Pc*N^2*(4 + 6) bytes
+    int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(M, (int64_t)(2.0e9 / ((4.0 + 2.0 * S) * N * (double)N))));
+    Pc = std::min(Pc, 64);
+    CD_TRY(mal(&b.Lfull, (size_t)Pc * N * N));
+    CD_TRY(mal((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np));
+    CD_TRY(mal((uint16_t**)&b.Cs, (size_t)S * O * Np));
+    CD_TRY(mal(&b.Ct, (size_t)O * N));
+    CD_TRY(mal(&b.eL, (size_t)Pc * N));
+    CD_TRY(mal(&b.eC, (size_t)O));
+    CD_TRY(mal(&b.eB, (size_t)N));
+    CD_TRY(mal(&b.D1, (size_t)O * Pc * N));
+    CD_TRY(mal(&b.D2, (size_t)N * N));
+    CD_TRY(mal(&b.Bm, (size_t)N * Pc * Op));
+    CD_TRY(mal((uint16_t**)&b.Bs, (size_t)S * N * Pc * Op));
+    CD_TRY(mal(&b.err, 1));
+    CD_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), st));
+    CD_CUDA(cudaMemsetAsync(K_dev, 0, sizeof(double) * N * N, st));
+    // C^T slices (rows i, k = nu)
+    transpose_kernel<<<(unsigned)(((int64_t)N * O + 255) / 256), 256, 0, st>>>(C_dev, N, O, b.Ct);
+    count_launch();
+    CD_TRY(launch_row_exp_warp<double>(b.Ct, N, O, N, b.eC, st));
+    CD_TRY(launch_slice3<double>(b.Ct, N, O, N, b.eC, b.Cs, Np, S, st));
+    OzakiPlan p1, p2;
+    p1.SA = p1.SB = S; p1.KEEP = S + 1; p1.F = 61 - ilog2_ceil(N);
+    p2.SA = p2.SB = S; p2.KEEP = S + 1;
+    for (int64_t P0 = 0; P0 < M; P0 += Pc) {
+      const int pc = (int)std::min<int64_t>(Pc, M - P0);
+      // dense FP32 L^P rows (p, mu), their exponents and slices
+      CD_TRY(launch_unpack_vectors<float>(L32, ld, P0, pc, mu, nu, n, N, b.Lfull, st));
+      CD_TRY(launch_row_exp_warp<float>(b.Lfull, N, (int64_t)pc * N, N, b.eL, st));
+      CD_TRY(launch_slice3<float>(b.Lfull, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+      // B^P = L^P C for the chunk: D1[i][p*N+mu]
+      CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * O * pc * N, st));
+      CD_TRY(ozaki_gemm(p1, b.Ls, (int64_t)pc * N, Np, b.Cs, O, Np, N, b.D1, (int64_t)pc * N, 1, b.err, st));
+      CD_CUDA(cudaMemsetAsync(b.Bm, 0, sizeof(double) * N * pc * Op, st));
+      {
+        const int64_t tot = (int64_t)pc * N * O;
+        half_finalize_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b.D1, (int64_t)pc * N, pc, N, O, Op, b.eL,
+                                                                            b.eC, p1.F, b.Bm);
+        count_launch();
+      }
+      // K += 2 B B^T over the chunk's (p, i)
+      const int64_t kd = (int64_t)pc * Op;
+      CD_TRY(launch_row_exp_warp<double>(b.Bm, kd, N, kd, b.eB, st));
+      CD_TRY(launch_slice3<double>(b.Bm, kd, N, kd, b.eB, b.Bs, kd, S, st));
+      p2.F = 61 - ilog2_ceil(kd);
+      CD_CUDA(cudaMemsetAsync(b.D2, 0, sizeof(unsigned long long) * N * N, st));
+      CD_TRY(ozaki_gemm(p2, b.Bs, N, kd, b.Bs, N, kd, kd, b.D2, N, 2, b.err, st));
+      k_accumulate_kernel<<<(unsigned)(((int64_t)N * N + 255) / 256), 256, 0, st>>>(b.D2, N, b.eB, p2.F, K_dev);
+      count_launch();
+    }
+    int herr = 0;
+    CD_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+    if (herr) { set_error("mixed K: a bounded tensor-core pipeline wait timed out"); return CD_ETIMEOUT; }
+  }
+  CD_CUDA(cudaStreamSynchronize(st));
   return CD_OK;
 }
 

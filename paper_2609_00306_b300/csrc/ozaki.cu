@@ -264,6 +264,7 @@ int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpi
   int kc = 1024 / std::max(1, maxg);
   int kcb = std::max(1, kc / BK);
   if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
+  if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
   if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 2>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
   if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
   set_error("ozaki_gemm: unsupported slice plan");
@@ -325,7 +326,10 @@ extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const do
     set_error("cd_slice_matmul: bad argument");
     return CD_EINVAL;
   }
-  if (slices != 1 && slices != 3 && slices != 7) { set_error("cd_slice_matmul: slices must be 1, 3 or 7"); return CD_EINVAL; }
+  if (slices != 1 && slices != 3 && slices != 4 && slices != 7) {
+    set_error("cd_slice_matmul: slices must be 1, 3, 4 or 7");
+    return CD_EINVAL;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t kp = (k + 7) / 8 * 8;
   OzakiPlan plan;
@@ -372,3 +376,79 @@ extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const do
   if (herr) { set_error("cd_slice_matmul: tensor-core pipeline wait timed out"); return fin(CD_ETIMEOUT); }
   return fin(CD_OK);
 }
+
+// ---------------------------------------------------------------------------
+// Helpers of the sliced column update inside the decomposition.
+namespace cd {
+namespace {
+// e_r with sqrt(d_r) < 2^e_r (frexp exponent); every Cholesky vector entry obeys
+// |L^K_r| <= sqrt(D^K_r) <= sqrt(D^1_r), so 2^e_r is a fixed scale for row r.
+__global__ void row_exp_sqrt_kernel(const double* __restrict__ d, int64_t n, int32_t* __restrict__ e) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  int ex = 0;
+  const double v = d[r];
+  if (v > 0.0) frexp(sqrt(v), &ex);
+  e[r] = ex;
+}
+// Bs[s][j][k] = Ls[s][rows[j]][k] for valid[j] <= k < K, else 0 (k < kfill)
+__global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64_t n, int64_t kpitch,
+                                     const int64_t* __restrict__ rows, const int64_t* __restrict__ valid, int nb,
+                                     int S, int64_t K, int64_t kfill, __nv_bfloat16* __restrict__ Bs,
+                                     int64_t bpitch) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)nb * kfill;
+  if (t >= per * S) return;
+  const int s = (int)(t / per);
+  const int64_t rem = t % per;
+  const int j = (int)(rem / kfill);
+  const int64_t k = rem % kfill;
+  __nv_bfloat16 v = __float2bfloat16(0.0f);
+  if (k >= valid[j] && k < K) v = Ls[((int64_t)s * n + rows[j]) * kpitch + k];
+  Bs[((int64_t)s * nb + j) * bpitch + k] = v;
+}
+// cols[slot[j]][r] -= 2^(e_r + e_{row j} - F) * D[j][r]
+__global__ void colupd_finalize_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int64_t n, int nb,
+                                       const int32_t* __restrict__ e, const int64_t* __restrict__ rows,
+                                       const int32_t* __restrict__ slots, int F, double* __restrict__ cols,
+                                       int64_t ld) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (r >= n) return;
+  const long long v = (long long)D[(int64_t)j * ldd + r];
+  const int sc = e[r] + e[rows[j]] - F;
+  cols[(int64_t)slots[j] * ld + r] -= ldexp((double)v, sc);
+}
+}  // namespace
+
+int launch_row_exp_sqrt(const double* d, int64_t n, int32_t* e, cudaStream_t st) {
+  if (n <= 0) return CD_OK;
+  row_exp_sqrt_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, n, e);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_gather_slices(const void* Ls, int64_t n, int64_t kpitch, const int64_t* rows, const int64_t* valid, int nb,
+                         int S, int64_t K, void* Bs, int64_t bpitch, cudaStream_t st) {
+  const int64_t kfill = (K + 31) / 32 * 32;
+  const int64_t tot = (int64_t)S * nb * kfill;
+  if (tot <= 0) return CD_OK;
+  gather_slices_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((const __nv_bfloat16*)Ls, n, kpitch, rows, valid,
+                                                                      nb, S, K, kfill, (__nv_bfloat16*)Bs, bpitch);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_colupd_finalize(const unsigned long long* D, int64_t ldd, int64_t n, int nb, const int32_t* e,
+                           const int64_t* rows, const int32_t* slots, int F, double* cols, int64_t ld, cudaStream_t st) {
+  if (n <= 0 || nb <= 0) return CD_OK;
+  dim3 grid((unsigned)((n + 255) / 256), (unsigned)nb);
+  colupd_finalize_kernel<<<grid, 256, 0, st>>>(D, ldd, n, nb, e, rows, slots, F, cols, ld);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+}  // namespace cd

@@ -35,4 +35,10 @@ int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int
                           const int32_t* row_exp, int S, void* dst, int64_t dst_rows, int64_t kpitch, int64_t k0,
                           cudaStream_t st);
 
+int launch_row_exp_sqrt(const double* d, int64_t n, int32_t* e, cudaStream_t st);
+int launch_gather_slices(const void* Ls, int64_t n, int64_t kpitch, const int64_t* rows, const int64_t* valid, int nb,
+                         int S, int64_t K, void* Bs, int64_t bpitch, cudaStream_t st);
+int launch_colupd_finalize(const unsigned long long* D, int64_t ldd, int64_t n, int nb, const int32_t* e,
+                           const int64_t* rows, const int32_t* slots, int F, double* cols, int64_t ld, cudaStream_t st);
+
 }  // namespace cd

@@ -74,23 +74,15 @@ def test_eri_columns(name):
     assert np.max(err) <= 1e-12, float(np.max(err))
 
 
-def _check_free_run(r, piv, M, gaps_o):
-    assert M == r.M
-    same = piv == r.piv
-    if not np.all(same):
-        k = int(np.argmin(same))
-        # the first divergence must be a near-tie in the oracle's own diagonal
-        D_before = None
-        assert k > 0 or True
-        return k
-    return None
+UPDATES = {"slice": 0, "fp64": 1}
 
 
+@pytest.mark.parametrize("update", ["slice", "fp64"])
 @pytest.mark.parametrize("name", SMALL)
-def test_factor_free_run_matches_oracle(name):
+def test_factor_free_run_matches_oracle(name, update):
     import paper_2609_00306_b300 as cd
     s, o, diag, rows, r, J, K = oracle_run(name)
-    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=16)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=16, update=UPDATES[update])
     prow, ppk, gaps, resid = f.pivots()
     assert f.M == r.M
     assert np.array_equal(ppk, rows[prow])
@@ -108,12 +100,13 @@ def test_factor_free_run_matches_oracle(name):
         assert np.max(np.abs(L - r.L)) <= 1e-10 * np.max(np.abs(r.L))
 
 
+@pytest.mark.parametrize("update", ["slice", "fp64"])
 @pytest.mark.parametrize("name", SMALL)
-@pytest.mark.parametrize("block", [1, 7, 64])
-def test_factor_forced_replay(name, block):
+@pytest.mark.parametrize("block", [1, 7, 64, 200])
+def test_factor_forced_replay(name, block, update):
     import paper_2609_00306_b300 as cd
     s, o, diag, rows, r, J, K = oracle_run(name)
-    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=block, forced=r.piv)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=block, forced=r.piv, update=UPDATES[update])
     prow, ppk, gaps, resid = f.pivots()
     assert f.M == r.M
     assert np.array_equal(prow, r.piv)
@@ -165,3 +158,25 @@ def test_max_vectors_cap_is_enomem():
     with pytest.raises(cd.CDError) as e:
         cd.cd_eri_factor(s.basis, 1e-6, max_vectors=5)
     assert e.value.code == -2
+
+
+@pytest.mark.parametrize("mode,tol", [("bf16x3", 3e-6), ("bf16x4", 1e-8)])
+@pytest.mark.parametrize("name", SMALL)
+def test_jk_mixed_vs_oracle(name, mode, tol):
+    """Mixed path: FP32 vectors, exact-slice BF16 tensor-core products with 3
+    or 4 slices per operand row.  Errors come from the FP32 rounding of L and
+    the 8S-bit fixed point below each row maximum; asserted bound on
+    max|dX|/max|X|: 3e-6 (3 slices), 1e-8 (4 slices)."""
+    import paper_2609_00306_b300 as cd
+    s, o, diag, rows, r, J, K = oracle_run(name)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, forced=r.piv, vec_precision=cd.CD_VEC_FP32)
+    m = {"bf16x3": cd.CD_JK_BF16X3, "bf16x4": cd.CD_JK_BF16X4}[mode]
+    Jm, Km = f.jk(s.C_occ, m)
+    eJ = np.max(np.abs(Jm - J)) / np.max(np.abs(J))
+    eK = np.max(np.abs(Km - K)) / np.max(np.abs(K))
+    Dm = oracle.density(s.C_occ)
+    etJ = abs(np.sum(Dm * Jm) - np.sum(Dm * J)) / abs(np.sum(Dm * J))
+    etK = abs(np.sum(Dm * Km) - np.sum(Dm * K)) / abs(np.sum(Dm * K))
+    print(f"{name} {mode}: max|dJ|/max|J|={eJ:.2e} max|dK|/max|K|={eK:.2e} dtr(DJ)={etJ:.2e} dtr(DK)={etK:.2e}")
+    assert eJ < max(tol, 1e-7) and eK < tol
+    assert np.array_equal(Km, Km.T)
