@@ -44,12 +44,16 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--jk", choices=["fp64", "bf16x3", "bf16x4"], default="bf16x4",
-                    help="J/K mode inside the step (default: bf16x4, FP32 vectors + 4-slice tensor-core products)")
+    ap.add_argument("--jk", choices=["fp64", "bf16x3", "bf16x4", "bf16x5", "bf16x3_fp32vec", "bf16x4_fp32vec"],
+                    default="bf16x5",
+                    help="J/K mode inside the step (default: bf16x5 = 5 exact BF16 slices of the FP64 vectors on "
+                         "the tensor cores; *_fp32vec = vectors rounded to FP32 first)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-jk-alone", action="store_true", help="skip the separate J/K timings (FP64 K is slow)")
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--measure-fp64-peak", action="store_true",
+                    help="compile and run the FP64 DFMA/DMMA microbenchmark, print its JSON line")
     return ap.parse_args()
 
 
@@ -176,9 +180,12 @@ def run_ours(args, rank, world):
     s = synth.make_workload(args.workload)
     N, O = s.n_basis, s.n_occ
     stream = torch.cuda.current_stream()
-    modes = {"fp64": cd.CD_JK_FP64, "bf16x3": cd.CD_JK_BF16X3, "bf16x4": cd.CD_JK_BF16X4}
+    modes = {"fp64": cd.CD_JK_FP64, "bf16x3": cd.CD_JK_BF16X3, "bf16x4": cd.CD_JK_BF16X4, "bf16x5": cd.CD_JK_BF16X5,
+             "bf16x3_fp32vec": cd.CD_JK_BF16X3 | cd.cderi.CD_JK_VEC_FP32,
+             "bf16x4_fp32vec": cd.CD_JK_BF16X4 | cd.cderi.CD_JK_VEC_FP32}
     jk_mode = modes[args.jk]
-    vec_prec = cd.CD_FP64 if jk_mode == cd.CD_JK_FP64 else cd.CD_VEC_FP32
+    # vectors stay FP64 in the step; the *_fp32vec variants round them to FP32 for the contraction
+    vec_prec = cd.CD_FP64
     C_dev = torch.tensor(s.C_occ, device=dev)
     J_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
     K_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
@@ -241,7 +248,7 @@ def run_ours(args, rank, world):
             jk[name + "_ms"] = None
             jk[name + "_error"] = str(e)
     Dm = 2.0 * s.C_occ @ s.C_occ.T
-    for mx in ("bf16x3", "bf16x4"):
+    for mx in ("bf16x3", "bf16x4", "bf16x5", "bf16x3_fp32vec", "bf16x4_fp32vec"):
         if "fp64" in res and mx in res:
             (J64, K64), (Jm, Km) = res["fp64"], res[mx]
             jk[mx + "_vs_fp64"] = {
@@ -303,8 +310,79 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_batch(args):
+    """64 independent systems (N = 60-600, tau alternating 1e-4 / 1e-5,
+    n_occ = N/8): the batched entry point (concurrent streams, block sizes
+    from the autotuner) against 64 sequential plain calls."""
+    import torch
+    import paper_2609_00306_b300 as cd
+    from paper_2609_00306_b300 import autotune, build
+    build.build()
+    cd.load()
+    systems = synth.make_batch()
+    table = autotune.load()
+    if not table:
+        table = autotune.tune(systems)
+    blocks = autotune.blocks_for(systems, table)
+    workers = int(table.get("workers", 8))
+    mode = {"fp64": cd.CD_JK_FP64, "bf16x3": cd.CD_JK_BF16X3, "bf16x4": cd.CD_JK_BF16X4, "bf16x5": cd.CD_JK_BF16X5,
+            "bf16x3_fp32vec": cd.CD_JK_BF16X3 | cd.cderi.CD_JK_VEC_FP32,
+            "bf16x4_fp32vec": cd.CD_JK_BF16X4 | cd.cderi.CD_JK_VEC_FP32}[args.jk]
+
+    def batched():
+        return cd.batch_run(systems, jk_mode=mode, workers=workers, blocks=blocks)
+
+    def sequential():
+        out = []
+        for s in systems:
+            f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
+            out.append(f.jk(s.C_occ, mode))
+            f.free()
+        return out
+
+    for _ in range(args.warmup):
+        batched()
+    torch.cuda.synchronize()
+    tb = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        Jb, Kb = batched()
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    seq = sequential()
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    err = max(float(np.max(np.abs(K - k1)) / np.max(np.abs(k1))) for K, (j1, k1) in zip(Kb, seq))
+    v = float(np.mean(tb))
+    out = {"metric": "64-system batch: screening + CD + J/K wall seconds (N=60-600 s+p)", "value": v, "unit": "s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if mode == cd.CD_JK_FP64 else "f64+" + args.jk,
+           "data": "synthetic", "config": {"workload": "batch64", "systems": len(systems),
+                                           "n_basis_total": int(sum(s.n_basis for s in systems)),
+                                           "workers": workers, "blocks": table.get("blocks")},
+           "sequential_s": ts, "speedup_vs_sequential": ts / v, "max_dK_rel_batch_vs_sequential": err}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def measure_fp64_peak():
+    src = os.path.join(ROOT, "paper_2609_00306_b300", "peaks", "fp64_peak.cu")
+    exe = os.path.join(ROOT, "paper_2609_00306_b300", "_build", "fp64_peak")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.check_call(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                           "-o", exe, src])
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
+    print(out, flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.measure_fp64_peak:
+        return measure_fp64_peak()
+    if args.workload == "batch64" and args.impl == "ours":
+        return run_batch(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -49,9 +49,11 @@ extern "C" {
 #define CD_JK_FP64       0  /* J and K contractions in FP64 */
 #define CD_JK_BF16X3     1  /* FP32 vectors; BF16 tensor-core products of 3 exact 8-bit slices per operand row */
 #define CD_JK_BF16X4     2  /* as CD_JK_BF16X3 with 4 slices (32-bit fixed point below each row maximum) */
+#define CD_JK_BF16X5     3  /* as CD_JK_BF16X3 with 5 slices (40-bit fixed point below each row maximum) */
 #define CD_JK_DEVICE     0x100 /* flag: C_occ, J, K are device pointers (else host) */
 #define CD_JK_ONLY_J     0x200 /* flag: compute J only (K may be NULL) */
 #define CD_JK_ONLY_K     0x400 /* flag: compute K only (J may be NULL) */
+#define CD_JK_VEC_FP32   0x800 /* flag (mixed modes): contract FP32-rounded vectors even if FP64 ones are stored */
 
 /* ---- inputs --------------------------------------------------------------- */
 /* Basis of contracted Cartesian Gaussian shells (all host pointers, read-only,
@@ -130,9 +132,14 @@ int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packe
  * FP32 when stored so).  *L_dev (may be NULL) receives the device pointer of
  * the stored array, leading dimension *ld (elements), *dtype 0 = FP64, 1 = FP32. */
 int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, int64_t* ld, int32_t* dtype);
+/* Entries of every vector on selected rows: out[K][j] = L^K_{rows[j]} (FP64,
+ * host, [M][nrows]); rows: host array of row indices.  Synchronous. */
+int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, double* out);
 /* Statistics of the factorisation, 16 doubles: [0] system set-up ms (host
  * clock), [1] ERI-column kernels ms, [2] column-update kernels ms (CUDA
- * events), [3] pivot steps ms, [4] candidate selection ms, [5] total ms;
+ * events; the sliced update runs concurrently with the ERI columns, so [1]
+ * and [2] overlap), [3] pivot steps ms (host clock), [4] candidate selection
+ * ms, [5] total ms;
  * [6] blocks, [7] ERI columns computed, [8] column-update flops (2 x rows x
  * columns x vectors applied), [9] ERI column entries computed, [10] M;
  * [11..15] reserved (0). */
@@ -144,11 +151,25 @@ long long cd_kernel_launches(void);
 /* J_{mu nu} = sum_P L^P_{mu nu} sum_{sigma rho} L^P_{sigma rho} D_{sigma rho},
  * K_{mu nu} = sum_P sum_{sigma rho} L^P_{mu sigma} D_{sigma rho} L^P_{rho nu},
  * D = 2 C_occ C_occ^T.  C_occ [N][n_occ], J, K [N][N], row-major; host pointers
- * unless CD_JK_DEVICE.  mode: CD_JK_FP64, CD_JK_BF16X3 or CD_JK_BF16X4 (mixed:
- * uses the FP32 vectors, converting on the fly when only FP64 ones are stored).  J (kernel d): two streamed GEMVs
+ * unless CD_JK_DEVICE.  mode: CD_JK_FP64, CD_JK_BF16X3, _X4 or _X5 (mixed:
+ * the stored vectors -- FP32 when the factor was made with CD_VEC_FP32, else
+ * FP64 -- are cut into 3, 4 or 5 exact 8-bit slices per row and contracted on
+ * the BF16 tensor cores; the FP32 storage itself limits K to ~1e-7 relative).  J (kernel d): two streamed GEMVs
  * over the vectors.  K (kernel e): B^P = L^P C_occ, K = 2 sum_P B^P B^P^T. */
 int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ,
           double* J, double* K, int32_t mode, void* stream);
+
+/* ---- batches of independent systems ---------------------------------------- */
+/* For i < n_sys: cd_system_create(bases[i], opts[i].schwarz), the
+ * decomposition with opts[i], and cd_jk(C_occ[i], n_occ[i], J[i], K[i],
+ * jk_mode).  `workers` host threads (0 = 8), each with its own CUDA stream,
+ * take systems from a shared queue (largest first) so that the kernels of
+ * small systems overlap on the GPU.  Work starts after what is queued on
+ * `stream` and `stream` waits for all of it; the call returns when done.
+ * Returns the first failing system's code (message names the system). */
+int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, const double* const* C_occ,
+                 const int32_t* n_occ, double* const* J, double* const* K, int32_t jk_mode, int32_t workers,
+                 void* stream);
 
 /* ---- building block: exact-slice tensor-core product ------------------------ */
 /* out[i][j] = sum_k X[i][k] Y[j][k] for FP64 device matrices X [m][k] (leading

@@ -20,7 +20,7 @@ def sources():
 
 def deps():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        [os.path.join(HERE, "..", "include", "cderi.h")]
+        sorted(glob.glob(os.path.join(HERE, "..", "include", "*.h")))
 
 
 def up_to_date() -> bool:

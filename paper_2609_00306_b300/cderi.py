@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libcderi.so")
 
 CD_OK, CD_EINVAL, CD_ENOMEM, CD_ENOTPSD, CD_ETIMEOUT, CD_ECUDA = 0, -1, -2, -3, -4, -5
 CD_FP64, CD_VEC_FP32 = 0, 1
-CD_JK_FP64, CD_JK_BF16X3, CD_JK_BF16X4 = 0, 1, 2
-CD_JK_DEVICE, CD_JK_ONLY_J, CD_JK_ONLY_K = 0x100, 0x200, 0x400
+CD_JK_FP64, CD_JK_BF16X3, CD_JK_BF16X4, CD_JK_BF16X5 = 0, 1, 2, 3
+CD_JK_DEVICE, CD_JK_ONLY_J, CD_JK_ONLY_K, CD_JK_VEC_FP32 = 0x100, 0x200, 0x400, 0x800
 CD_MAX_PRIM = 16
 CD_UPDATE_SLICE, CD_UPDATE_FP64 = 0, 1
 
@@ -29,7 +29,7 @@ _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENO
 # every symbol declared in include/cderi.h
 EXPORTS = ["cd_system_create", "cd_system_free", "cd_system_info", "cd_system_rows", "cd_eri_columns",
            "cd_eri_factor", "cd_eri_factor_sys", "cd_factor_free", "cd_factor_info", "cd_factor_pivots",
-           "cd_factor_vectors", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_slice_matmul", "cd_last_error", "cd_version"]
+           "cd_factor_vectors", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_batch_run", "cd_slice_matmul", "cd_last_error", "cd_version"]
 
 
 class CDError(RuntimeError):
@@ -76,8 +76,10 @@ def load(path: Optional[str] = None):
         "cd_factor_pivots": (ctypes.c_int, [P, P, P, P, P]),
         "cd_factor_vectors": (ctypes.c_int, [P, P, P, P, P]),
         "cd_factor_stats": (ctypes.c_int, [P, P]),
+        "cd_factor_gather": (ctypes.c_int, [P, P, I32, P]),
         "cd_jk": (ctypes.c_int, [P, P, I32, P, P, I32, P]),
         "cd_kernel_launches": (ctypes.c_longlong, []),
+        "cd_batch_run": (ctypes.c_int, [I32, P, P, P, P, P, P, I32, I32, P]),
         "cd_slice_matmul": (ctypes.c_int, [P, I64, I64, P, I64, I64, I64, I32, P, I64, P]),
         "cd_last_error": (ctypes.c_char_p, []),
         "cd_version": (ctypes.c_char_p, []),
@@ -198,6 +200,13 @@ class Factor:
         _check(load().cd_factor_vectors(self._h, _p(L), None, None, None))
         return L
 
+    def gather(self, rows) -> np.ndarray:
+        """[M, len(rows)] FP64 entries of every vector on the given rows."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.zeros((self.M, rows.shape[0]))
+        _check(load().cd_factor_gather(self._h, _p(rows), int(rows.shape[0]), _p(out)))
+        return out
+
     def vectors_device(self):
         ptr, ld, dt = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_int32()
         _check(load().cd_factor_vectors(self._h, None, ctypes.byref(ptr), ctypes.byref(ld), ctypes.byref(dt)))
@@ -284,6 +293,35 @@ def slice_matmul(X, Y, slices: int = 7, stream=None):
     _check(load().cd_slice_matmul(ctypes.c_void_p(X.data_ptr()), k, m, ctypes.c_void_p(Y.data_ptr()), k, n, k,
                                   int(slices), ctypes.c_void_p(out.data_ptr()), n, _stream(stream)))
     return out
+
+
+def batch_run(systems, jk_mode: int = CD_JK_FP64, workers: int = 0, blocks=None, update: int = CD_UPDATE_SLICE,
+              vec_precision: Optional[int] = None, stream=None):
+    """Decompose and contract many independent systems (C ABI cd_batch_run).
+
+    systems: sequence of synth.System-like objects (basis, C_occ, tau, schwarz).
+    blocks: per-system speculative block size (e.g. from the autotuner), or None.
+    Returns lists J, K of numpy arrays.
+    """
+    n = len(systems)
+    if vec_precision is None:
+        vec_precision = CD_FP64
+    bargs = [_BasisArgs(s.basis) for s in systems]
+    BasisArr = cd_basis_t * n
+    OptsArr = cd_opts_t * n
+    bases = BasisArr(*[b.s for b in bargs])
+    opts = OptsArr(*[make_opts(s.tau, s.schwarz, vec_precision, int(blocks[i]) if blocks is not None else 0,
+                               update=update)[0] for i, s in enumerate(systems)])
+    Cs = [np.ascontiguousarray(s.C_occ, dtype=np.float64) for s in systems]
+    Js = [np.zeros((c.shape[0], c.shape[0])) for c in Cs]
+    Ks = [np.zeros((c.shape[0], c.shape[0])) for c in Cs]
+    PArr = ctypes.c_void_p * n
+    occ = np.array([c.shape[1] for c in Cs], dtype=np.int32)
+    _check(load().cd_batch_run(n, ctypes.byref(bases), ctypes.byref(opts),
+                               PArr(*[c.ctypes.data for c in Cs]), _p(occ),
+                               PArr(*[j.ctypes.data for j in Js]), PArr(*[k.ctypes.data for k in Ks]),
+                               int(jk_mode), int(workers), _stream(stream)))
+    return Js, Ks
 
 
 def kernel_launches() -> int:

@@ -5,6 +5,9 @@
 #include <atomic>
 #include <chrono>
 #include <cstring>
+#include <thread>
+#include <cstdio>
+#include <cstdlib>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -19,7 +22,7 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_counter() { return g_launches.load(); }
 int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st);
-int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
+int jk_mixed(const float* L32, const double* L64, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
              const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
              int S, cudaStream_t st);
 }  // namespace cd
@@ -88,13 +91,13 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   // diagonal of every packed pair (kernel a, diagonal mode)
   const int64_t npk = (int64_t)nbf * (nbf + 1) / 2;
   double* dall = nullptr;
-  rc = dalloc(&dall, (size_t)npk);
+  rc = scratch_alloc(&dall, (size_t)npk, st);
   if (rc != CD_OK) { system_release(s); return rc; }
   rc = launch_eri_diag(s->all, nullptr, s->all_class_off, dall, s->boys, st);
   std::vector<double> hd(npk);
   if (rc == CD_OK && cudaMemcpyAsync(hd.data(), dall, sizeof(double) * npk, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = CD_ECUDA;
+  scratch_free(dall, st);
   if (rc == CD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
-  cudaFree(dall);
   if (rc != CD_OK) { if (rc == CD_ECUDA) set_error("diagonal pass failed"); system_release(s); return rc; }
   for (int64_t p = 0; p < npk; ++p)
     if (!std::isfinite(hd[p])) { set_error("non-finite ERI diagonal"); system_release(s); return CD_EINVAL; }
@@ -133,7 +136,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   std::vector<int32_t> p2r(npk, -1);
   for (int64_t r = 0; r < n; ++r) p2r[rows[r]] = (int32_t)r;
   PairSetHost hbra;
-  build_pairs(hb, ks1, ks2, &hbra);
+  build_pairs(hb, ks1, ks2, &hbra, kPrimPrune);
   for (auto& r : hbra.row)
     if (r >= 0) r = p2r[r];
   s->bra_to_all = kall;
@@ -194,20 +197,6 @@ static KetDesc ket_of_row(const cd_system* s, int64_t r, int32_t slot) {
 }
 
 // ---------------------------------------------------------------- factor ----
-struct cd_factor {
-  cd_system* sys = nullptr;
-  bool owns_sys = false;
-  int64_t M = 0, Mcap = 0, ld = 0, n = 0;
-  double* L = nullptr;
-  float* L32 = nullptr;
-  int vec_precision = CD_FP64;
-  std::vector<int64_t> piv;
-  std::vector<double> gaps;
-  std::vector<double> resid;
-  double resid_max = 0.0;
-  double stats[16] = {0};
-};
-
 static void factor_release(cd_factor* f) {
   if (!f) return;
   cudaFree(f->L);
@@ -220,7 +209,8 @@ namespace {
 constexpr int kSlices = 7;        // 8-bit slices per vector entry in the sliced update
 constexpr int kSliceF = 60;       // fixed-point fraction bits of the update (|sum| < 1 per unit scale)
 
-struct Work {  // scratch of one factorisation, freed at the end
+struct Work {  // scratch of one factorisation, freed (stream-ordered) at the end
+  cudaStream_t st = nullptr;
   double* pool = nullptr;
   double* D0 = nullptr;
   double* D1 = nullptr;
@@ -228,12 +218,17 @@ struct Work {  // scratch of one factorisation, freed at the end
   int32_t* slots_dev = nullptr;
   int64_t* rows_dev = nullptr;
   int64_t* valid_dev = nullptr;
-  KetDesc* kets_dev = nullptr;
+  KetGroup* kets_dev = nullptr;
   StepScratch* sc = nullptr;
   StepResult* res_dev = nullptr;
-  StepResult* res_h = nullptr;
-  double* dh = nullptr;
-  double* dp_h = nullptr;
+  // host mirrors: ordinary (pageable) memory -- the copies are followed by a
+  // stream synchronisation anyway, and pinned-memory frees would synchronise
+  // the whole device (concurrent batch workers)
+  StepResult res_hv[1];
+  double dp_hv[1];
+  std::vector<double> dh;
+  StepResult* res_h = res_hv;
+  double* dp_h = dp_hv;
   // sliced update
   void* Ls = nullptr;               // bf16 [kSlices][n][kcap]
   void* Bs = nullptr;               // bf16 [kSlices][b][kcap]
@@ -241,13 +236,29 @@ struct Work {  // scratch of one factorisation, freed at the end
   int32_t* erow = nullptr;          // [n]
   int* err = nullptr;
   int64_t kcap = 0;
+  // candidate selection on the device
+  SelectState* sel = nullptr;
+  int64_t* cand_rows = nullptr;
+  double* cand_vals = nullptr;
+  std::vector<int64_t> cand_rows_h;
+  std::vector<double> cand_vals_h;
+  unsigned cand_count_h[1] = {0};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  // sliced update runs on a second stream, concurrently with the ERI columns
+  // (tensor cores vs FP64 pipe)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_gemm = nullptr, ev_g0 = nullptr, ev_g1 = nullptr;
+  std::vector<int32_t> upd_slots;
+  std::vector<int64_t> upd_rows, upd_valid;
   ~Work() {
-    cudaFree(pool); cudaFree(D0); cudaFree(D1); cudaFree(Bg); cudaFree(slots_dev); cudaFree(rows_dev);
-    cudaFree(valid_dev); cudaFree(kets_dev); cudaFree(sc); cudaFree(res_dev);
-    cudaFree(Ls); cudaFree(Bs); cudaFree(Dint); cudaFree(erow); cudaFree(err);
-    cudaFreeHost(res_h); cudaFreeHost(dh); cudaFreeHost(dp_h);
+    for (void* p : {(void*)pool, (void*)D0, (void*)D1, (void*)Bg, (void*)slots_dev, (void*)rows_dev,
+                    (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Ls, Bs, (void*)Dint,
+                    (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals})
+      scratch_free(p, st);
+
     for (auto& e : ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ev_ready, ev_gemm, ev_g0, ev_g1}) if (e) cudaEventDestroy(e);
+    if (st2) cudaStreamDestroy(st2);
   }
 };
 }  // namespace
@@ -261,15 +272,14 @@ static int grow_vectors(cd_factor* f, Work* w, bool slice, int b, int64_t newcap
     const int64_t nk = (newcap + 31) / 32 * 32;
     void* nLs = nullptr;
     void* nBs = nullptr;
-    int rc = dalloc((uint16_t**)&nLs, (size_t)kSlices * f->n * nk);
-    if (rc == CD_OK) rc = dalloc((uint16_t**)&nBs, (size_t)kSlices * b * nk);
-    if (rc != CD_OK) { cudaFree(nL); cudaFree(nLs); return rc; }
+    int rc = scratch_alloc((uint16_t**)&nLs, (size_t)kSlices * f->n * nk, st);
+    if (rc == CD_OK) rc = scratch_alloc((uint16_t**)&nBs, (size_t)kSlices * b * nk, st);
+    if (rc != CD_OK) { cudaFree(nL); scratch_free(nLs, st); return rc; }
     if (K > 0 && f->n > 0)
       CD_CUDA(cudaMemcpy2DAsync(nLs, nk * 2, w->Ls, w->kcap * 2, K * 2, (size_t)kSlices * f->n,
                                 cudaMemcpyDeviceToDevice, st));
-    CD_CUDA(cudaStreamSynchronize(st));
-    cudaFree(w->Ls);
-    cudaFree(w->Bs);
+    scratch_free(w->Ls, st);
+    scratch_free(w->Bs, st);
     w->Ls = nLs;
     w->Bs = nBs;
     w->kcap = nk;
@@ -317,32 +327,43 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   f->ld = ld;
   f->vec_precision = o->vec_precision;
   Work w;
+  w.st = st;
   CD_TRY(dalloc(&f->L, (size_t)Mcap * ld));
   f->Mcap = Mcap;
-  CD_TRY(dalloc(&w.pool, (size_t)b * ld));
-  CD_TRY(dalloc(&w.D0, (size_t)ld));
-  CD_TRY(dalloc(&w.D1, (size_t)ld));
-  CD_TRY(dalloc(&w.Bg, (size_t)Mmax * b));
-  CD_TRY(dalloc(&w.slots_dev, (size_t)b));
-  CD_TRY(dalloc(&w.rows_dev, (size_t)b));
-  CD_TRY(dalloc(&w.valid_dev, (size_t)b));
-  CD_TRY(dalloc(&w.kets_dev, (size_t)b));
-  CD_TRY(dalloc(&w.sc, 1));
-  CD_TRY(dalloc(&w.res_dev, 1));
+  CD_TRY(scratch_alloc(&w.pool, (size_t)b * ld, st));
+  CD_TRY(scratch_alloc(&w.D0, (size_t)ld, st));
+  CD_TRY(scratch_alloc(&w.D1, (size_t)ld, st));
+  CD_TRY(scratch_alloc(&w.Bg, (size_t)Mmax * b, st));
+  CD_TRY(scratch_alloc(&w.slots_dev, (size_t)b, st));
+  CD_TRY(scratch_alloc(&w.rows_dev, (size_t)b, st));
+  CD_TRY(scratch_alloc(&w.valid_dev, (size_t)b, st));
+  CD_TRY(scratch_alloc(&w.kets_dev, (size_t)b, st));
+  CD_TRY(scratch_alloc(&w.sc, 1, st));
+  CD_TRY(scratch_alloc(&w.res_dev, 1, st));
   if (slice) {
     w.kcap = (Mcap + 31) / 32 * 32;
-    CD_TRY(dalloc((uint16_t**)&w.Ls, (size_t)kSlices * std::max<int64_t>(n, 1) * w.kcap));
-    CD_TRY(dalloc((uint16_t**)&w.Bs, (size_t)kSlices * b * w.kcap));
-    CD_TRY(dalloc(&w.Dint, (size_t)b * ld));
-    CD_TRY(dalloc(&w.erow, (size_t)std::max<int64_t>(n, 1)));
-    CD_TRY(dalloc(&w.err, 1));
+    CD_TRY(scratch_alloc((uint16_t**)&w.Ls, (size_t)kSlices * std::max<int64_t>(n, 1) * w.kcap, st));
+    CD_TRY(scratch_alloc((uint16_t**)&w.Bs, (size_t)kSlices * b * w.kcap, st));
+    CD_TRY(scratch_alloc(&w.Dint, (size_t)b * ld, st));
+    CD_TRY(scratch_alloc(&w.erow, (size_t)std::max<int64_t>(n, 1), st));
+    CD_TRY(scratch_alloc(&w.err, 1, st));
     CD_CUDA(cudaMemsetAsync(w.err, 0, sizeof(int), st));
     CD_TRY(launch_row_exp_sqrt(s->diag_dev, n, w.erow, st));
   }
-  CD_CUDA(cudaMallocHost(&w.res_h, sizeof(StepResult)));
-  CD_CUDA(cudaMallocHost(&w.dh, sizeof(double) * std::max<int64_t>(n, 1)));
-  CD_CUDA(cudaMallocHost(&w.dp_h, sizeof(double)));
+  const int cand_cap = 4 * b;
+  CD_TRY(scratch_alloc(&w.sel, 1, st));
+  CD_TRY(scratch_alloc(&w.cand_rows, (size_t)cand_cap, st));
+  CD_TRY(scratch_alloc(&w.cand_vals, (size_t)cand_cap, st));
+  w.cand_rows_h.resize(cand_cap);
+  w.cand_vals_h.resize(cand_cap);
   for (auto& e : w.ev) CD_CUDA(cudaEventCreate(&e));
+  if (slice) {
+    CD_CUDA(cudaStreamCreateWithFlags(&w.st2, cudaStreamNonBlocking));
+    CD_CUDA(cudaEventCreateWithFlags(&w.ev_ready, cudaEventDisableTiming));
+    CD_CUDA(cudaEventCreateWithFlags(&w.ev_gemm, cudaEventDisableTiming));
+    CD_CUDA(cudaEventCreate(&w.ev_g0));
+    CD_CUDA(cudaEventCreate(&w.ev_g1));
+  }
   CD_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(StepScratch), st));
   CD_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(double) * b * ld, st));
   CD_CUDA(cudaMemsetAsync(w.D1, 0, sizeof(double) * ld, st));
@@ -367,12 +388,15 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   plan.F = kSliceF;
   std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
   std::unordered_map<int64_t, int> row2slot;
-  double t_eri = 0, t_upd = 0, t_sel = 0, upd_flops = 0, eri_ints = 0;
+  double t_eri = 0, t_upd = 0, t_sel = 0, t_steps = 0, upd_flops = 0, eri_ints = 0;
   int64_t nblocks = 0, ncols = 0;
   int64_t K = 0;
   bool done = false;
+  const bool dbg = getenv("CDERI_DEBUG") != nullptr;
   while (!done) {
     if (forced ? (K >= nf) : !(res.dmax >= tau)) break;
+    if (dbg) fprintf(stderr, "[cderi] block %lld K=%lld dmax=%.3e idx=%lld\n", (long long)nblocks, (long long)K,
+                     res.dmax, (long long)res.idx);
     // ---- candidate block
     const double ts = now_ms();
     std::vector<int64_t> cand;
@@ -380,18 +404,32 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       for (int64_t k = K; k < nf && (int64_t)cand.size() < b; ++k)
         if (std::find(cand.begin(), cand.end(), o->forced_pivots[k]) == cand.end()) cand.push_back(o->forced_pivots[k]);
     } else {
-      CD_CUDA(cudaMemcpyAsync(w.dh, Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+      // the b largest residual diagonals >= tau (radix select on the device)
+      CD_TRY(launch_select(Dcur, n, tau, b, w.sel, w.cand_rows, w.cand_vals, cand_cap, st));
+      CD_CUDA(cudaMemcpyAsync(w.cand_count_h, &w.sel->count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      CD_CUDA(cudaMemcpyAsync(w.cand_rows_h.data(), w.cand_rows, sizeof(int64_t) * cand_cap, cudaMemcpyDeviceToHost, st));
+      CD_CUDA(cudaMemcpyAsync(w.cand_vals_h.data(), w.cand_vals, sizeof(double) * cand_cap, cudaMemcpyDeviceToHost, st));
       CD_CUDA(cudaStreamSynchronize(st));
-      std::vector<int64_t> c;
-      c.reserve(1024);
-      for (int64_t r = 0; r < n; ++r)
-        if (w.dh[r] >= tau) c.push_back(r);
-      auto cmp = [&](int64_t x, int64_t y) { return w.dh[x] > w.dh[y] || (w.dh[x] == w.dh[y] && x < y); };
+      std::vector<std::pair<double, int64_t>> c;
+      const unsigned cnt = *w.cand_count_h;
+      if (cnt <= (unsigned)cand_cap) {
+        for (unsigned i = 0; i < cnt; ++i) c.emplace_back(w.cand_vals_h[i], w.cand_rows_h[i]);
+      } else {  // many exact ties at the threshold: full scan on the host
+        w.dh.resize(n);
+        CD_CUDA(cudaMemcpyAsync(w.dh.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        CD_CUDA(cudaStreamSynchronize(st));
+        for (int64_t r = 0; r < n; ++r)
+          if (w.dh[r] >= tau) c.emplace_back(w.dh[r], r);
+      }
+      auto cmp = [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
+        return x.first > y.first || (x.first == y.first && x.second < y.second);
+      };
       if ((int64_t)c.size() > b) {
         std::nth_element(c.begin(), c.begin() + b, c.end(), cmp);
         c.resize(b);
       }
-      cand = c;
+      std::sort(c.begin(), c.end(), cmp);
+      for (auto& x : c) cand.push_back(x.second);
     }
     t_sel += now_ms() - ts;
     // ---- pool: keep columns still wanted, free the rest
@@ -414,31 +452,48 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     }
     ++nblocks;
     ncols += (int64_t)kets.size();
+    // ---- sliced update of every pool column with vectors [valid, K): on the
+    // second stream, overlapping the ERI columns below
+    bool gemm_issued = false;
+    int nb_upd = 0;
+    if (slice) {
+      w.upd_slots.clear(); w.upd_rows.clear(); w.upd_valid.clear();
+      for (int x = 0; x < b; ++x)
+        if (slot_row[x] >= 0 && slot_valid[x] < K) {
+          w.upd_slots.push_back(x); w.upd_rows.push_back(slot_row[x]); w.upd_valid.push_back(slot_valid[x]);
+        }
+      nb_upd = (int)w.upd_slots.size();
+      if (nb_upd > 0 && K > 0) {
+        cudaStream_t s2 = w.st2;
+        CD_CUDA(cudaEventRecord(w.ev_ready, st));      // slices of the last block are written
+        CD_CUDA(cudaStreamWaitEvent(s2, w.ev_ready, 0));
+        CD_CUDA(cudaEventRecord(w.ev_g0, s2));
+        CD_CUDA(cudaMemcpyAsync(w.slots_dev, w.upd_slots.data(), sizeof(int32_t) * nb_upd, cudaMemcpyHostToDevice, s2));
+        CD_CUDA(cudaMemcpyAsync(w.rows_dev, w.upd_rows.data(), sizeof(int64_t) * nb_upd, cudaMemcpyHostToDevice, s2));
+        CD_CUDA(cudaMemcpyAsync(w.valid_dev, w.upd_valid.data(), sizeof(int64_t) * nb_upd, cudaMemcpyHostToDevice, s2));
+        CD_TRY(launch_gather_slices(w.Ls, n, w.kcap, w.rows_dev, w.valid_dev, nb_upd, kSlices, K, w.Bs, w.kcap, s2));
+        CD_CUDA(cudaMemsetAsync(w.Dint, 0, sizeof(unsigned long long) * nb_upd * ld, s2));
+        CD_TRY(ozaki_gemm(plan, w.Ls, n, w.kcap, w.Bs, nb_upd, w.kcap, K, w.Dint, ld, 1, w.err, s2));
+        CD_CUDA(cudaEventRecord(w.ev_g1, s2));
+        CD_CUDA(cudaEventRecord(w.ev_gemm, s2));
+        for (int x = 0; x < nb_upd; ++x) upd_flops += 2.0 * (double)n * (double)(K - w.upd_valid[x]);
+        gemm_issued = true;
+      }
+    }
     CD_CUDA(cudaEventRecord(w.ev[0], st));
+    std::vector<KetGroup> groups = group_kets(kets);
     if (!kets.empty()) {
-      CD_CUDA(cudaMemcpyAsync(w.kets_dev, kets.data(), sizeof(KetDesc) * kets.size(), cudaMemcpyHostToDevice, st));
-      CD_TRY(launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, w.kets_dev, (int)kets.size(), w.pool, ld,
+      CD_CUDA(cudaMemcpyAsync(w.kets_dev, groups.data(), sizeof(KetGroup) * groups.size(), cudaMemcpyHostToDevice, st));
+      CD_TRY(launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
                                 s->boys, st));
       eri_ints += (double)kets.size() * (double)n;
     }
     CD_CUDA(cudaEventRecord(w.ev[1], st));
-    // ---- bring every pool column up to date with vectors [valid, K)
     if (slice) {
-      std::vector<int32_t> sl;
-      std::vector<int64_t> rr, vv;
-      for (int x = 0; x < b; ++x)
-        if (slot_row[x] >= 0 && slot_valid[x] < K) { sl.push_back(x); rr.push_back(slot_row[x]); vv.push_back(slot_valid[x]); }
-      const int nb = (int)sl.size();
-      if (nb > 0 && K > 0) {
-        CD_CUDA(cudaMemcpyAsync(w.slots_dev, sl.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice, st));
-        CD_CUDA(cudaMemcpyAsync(w.rows_dev, rr.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
-        CD_CUDA(cudaMemcpyAsync(w.valid_dev, vv.data(), sizeof(int64_t) * nb, cudaMemcpyHostToDevice, st));
-        CD_TRY(launch_gather_slices(w.Ls, n, w.kcap, w.rows_dev, w.valid_dev, nb, kSlices, K, w.Bs, w.kcap, st));
-        CD_CUDA(cudaMemsetAsync(w.Dint, 0, sizeof(unsigned long long) * nb * ld, st));
-        CD_TRY(ozaki_gemm(plan, w.Ls, n, w.kcap, w.Bs, nb, w.kcap, K, w.Dint, ld, 1, w.err, st));
-        CD_TRY(launch_colupd_finalize(w.Dint, ld, n, nb, w.erow, w.rows_dev, w.slots_dev, plan.F, w.pool, ld, st));
-        for (int x = 0; x < nb; ++x) upd_flops += 2.0 * (double)n * (double)(K - vv[x]);
-        CD_CUDA(cudaStreamSynchronize(st));  // host vectors above stay alive until the copies are done
+      if (gemm_issued) {
+        CD_CUDA(cudaStreamWaitEvent(st, w.ev_gemm, 0));
+        CD_TRY(launch_colupd_finalize(w.Dint, ld, n, nb_upd, w.erow, w.rows_dev, w.slots_dev, plan.F, w.pool, ld, st));
+        CD_CUDA(cudaStreamSynchronize(st));  // host copies of the group vectors are complete
       }
     } else {
       std::unordered_map<int64_t, std::vector<int>> groups;
@@ -463,6 +518,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       if (slot_row[sl] >= 0) slot_valid[sl] = K;
     const int64_t Kb = K;
     bool first = true;
+    CD_CUDA(cudaStreamSynchronize(st));  // columns of this block are complete
+    const double t_blk = now_ms();
     // ---- serial pivot steps inside the block
     for (;;) {
       int64_t p;
@@ -506,7 +563,11 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       if (first) {
         float a = 0, c = 0;
         cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
-        cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+        if (slice) {
+          if (gemm_issued) cudaEventElapsedTime(&c, w.ev_g0, w.ev_g1);
+        } else {
+          cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+        }
         t_eri += a;
         t_upd += c;
         first = false;
@@ -523,11 +584,24 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         return CD_ENOTPSD;
       }
     }
+    t_steps += now_ms() - t_blk;
+    if (first && !done && !forced) {
+      // the argmax row is always among the block's candidates; a block without a
+      // step would repeat forever
+      CD_CUDA(cudaStreamSynchronize(st));
+      set_error("internal: candidate selection missed the pivot row " + std::to_string(res.idx) + " at step " +
+                std::to_string(K));
+      return CD_EINVAL;
+    }
     if (first) {  // block ended without a step (only possible with a forced list)
       CD_CUDA(cudaStreamSynchronize(st));
       float a = 0, c = 0;
       cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
-      cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+      if (slice) {
+        if (gemm_issued) cudaEventElapsedTime(&c, w.ev_g0, w.ev_g1);
+      } else {
+        cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+      }
       t_eri += a;
       t_upd += c;
       if (forced && K < nf && !row2slot.count(o->forced_pivots[K])) {
@@ -543,7 +617,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     int herr = 0;
     CD_CUDA(cudaMemcpyAsync(&herr, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CD_CUDA(cudaStreamSynchronize(st));
-    if (herr) { set_error("tensor-core update: a bounded pipeline wait timed out"); return CD_ETIMEOUT; }
+    if (herr) {
+      set_error("tensor-core update: a bounded pipeline wait timed out (wait bits " + std::to_string(herr) + ")");
+      return CD_ETIMEOUT;
+    }
   }
   f->M = K;
   f->resid_max = res.dmax;
@@ -553,9 +630,9 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   }
   // the slice store is no longer needed: release it before the FP32 copy
   CD_CUDA(cudaStreamSynchronize(st));
-  cudaFree(w.Ls); w.Ls = nullptr;
-  cudaFree(w.Bs); w.Bs = nullptr;
-  cudaFree(w.pool); w.pool = nullptr;
+  scratch_free(w.Ls, st); w.Ls = nullptr;
+  scratch_free(w.Bs, st); w.Bs = nullptr;
+  scratch_free(w.pool, st); w.pool = nullptr;
   if (f->vec_precision == CD_VEC_FP32 && K > 0) {
     CD_TRY(dalloc(&f->L32, (size_t)K * ld));
     CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
@@ -565,7 +642,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   f->stats[0] = s->ms_setup;
   f->stats[1] = t_eri;
   f->stats[2] = t_upd;
-  f->stats[3] = t_all - t_eri - t_upd - t_sel;
+  f->stats[3] = t_steps;
   f->stats[4] = t_sel;
   f->stats[5] = t_all;
   f->stats[6] = (double)nblocks;
@@ -619,14 +696,15 @@ int cd_eri_columns(const cd_system_t* s, const int64_t* cols, int32_t ncols, dou
     if (cols[j] < 0 || cols[j] >= s->n_rows) { set_error("cd_eri_columns: column row out of range"); return CD_EINVAL; }
     k[j] = ket_of_row(s, cols[j], j);
   }
-  KetDesc* kd = nullptr;
-  CD_TRY(dalloc(&kd, (size_t)ncols));
+  std::vector<KetGroup> g = group_kets(k);
+  KetGroup* kd = nullptr;
+  CD_TRY(scratch_alloc(&kd, g.size(), st));
   int rc = CD_OK;
-  if (cudaMemcpyAsync(kd, k.data(), sizeof(KetDesc) * ncols, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = CD_ECUDA;
-  if (rc == CD_OK) rc = launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, kd, ncols, out, ld, s->boys, st);
+  if (cudaMemcpyAsync(kd, g.data(), sizeof(KetGroup) * g.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = CD_ECUDA;
+  if (rc == CD_OK) rc = launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, kd, (int)g.size(), out, ld, s->boys, st);
   if (rc == CD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
   if (rc == CD_ECUDA) set_error("cd_eri_columns: CUDA failure");
-  cudaFree(kd);
+  scratch_free(kd, st);
   return rc;
 }
 
@@ -701,6 +779,27 @@ int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, 
   return CD_OK;
 }
 
+int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, double* out) {
+  if (!f || (nrows > 0 && (!rows || !out)) || nrows < 0) { set_error("cd_factor_gather: bad argument"); return CD_EINVAL; }
+  if (nrows == 0 || f->M == 0) return CD_OK;
+  for (int32_t j = 0; j < nrows; ++j)
+    if (rows[j] < 0 || rows[j] >= f->n) { set_error("cd_factor_gather: row out of range"); return CD_EINVAL; }
+  int64_t* rd = nullptr;
+  double* od = nullptr;
+  CD_TRY(dalloc(&rd, (size_t)nrows));
+  int rc = dalloc(&od, (size_t)nrows * f->M);
+  if (rc != CD_OK) { cudaFree(rd); return rc; }
+  rc = CD_ECUDA;
+  if (cudaMemcpy(rd, rows, sizeof(int64_t) * nrows, cudaMemcpyHostToDevice) == cudaSuccess &&
+      launch_gather(f->L, f->ld, rd, nrows, 0, f->M, od, nullptr) == CD_OK &&
+      cudaMemcpy(out, od, sizeof(double) * nrows * f->M, cudaMemcpyDeviceToHost) == cudaSuccess)
+    rc = CD_OK;
+  if (rc != CD_OK) set_error("cd_factor_gather: CUDA failure");
+  cudaFree(rd);
+  cudaFree(od);
+  return rc;
+}
+
 int cd_factor_stats(const cd_factor_t* f, double* stats16) {
   if (!f || !stats16) { set_error("cd_factor_stats: bad argument"); return CD_EINVAL; }
   std::memcpy(stats16, f->stats, sizeof(f->stats));
@@ -715,7 +814,10 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
   const bool dev = (mode & CD_JK_DEVICE) != 0;
   const bool wantJ = !(mode & CD_JK_ONLY_K), wantK = !(mode & CD_JK_ONLY_J);
   if ((wantJ && !J) || (wantK && !K)) { set_error("cd_jk: J or K is NULL"); return CD_EINVAL; }
-  if (m != CD_JK_FP64 && m != CD_JK_BF16X3 && m != CD_JK_BF16X4) { set_error("cd_jk: unknown mode"); return CD_EINVAL; }
+  if (m != CD_JK_FP64 && m != CD_JK_BF16X3 && m != CD_JK_BF16X4 && m != CD_JK_BF16X5) {
+    set_error("cd_jk: unknown mode");
+    return CD_EINVAL;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const int N = f->sys->hb.nbf, O = n_occ;
   const int64_t n = f->n, M = f->M, ld = f->ld;
@@ -723,9 +825,9 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
   double *Lfull = nullptr, *B = nullptr;
   int rc = CD_OK;
   auto fail = [&](int code) {
+    if (!dev) { scratch_free(dC, st); scratch_free(dJ, st); scratch_free(dK, st); }
+    for (void* p : {(void*)d, (void*)v, (void*)Jp, (void*)Lfull, (void*)B}) scratch_free(p, st);
     cudaStreamSynchronize(st);
-    if (!dev) { cudaFree(dC); cudaFree(dJ); cudaFree(dK); }
-    cudaFree(d); cudaFree(v); cudaFree(Jp); cudaFree(Lfull); cudaFree(B);
     return code;
   };
   if (dev) {
@@ -733,31 +835,33 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
     dJ = J;
     dK = K;
   } else {
-    if ((rc = dalloc(&dC, (size_t)N * O)) != CD_OK) return fail(rc);
-    if (wantJ && (rc = dalloc(&dJ, (size_t)N * N)) != CD_OK) return fail(rc);
-    if (wantK && (rc = dalloc(&dK, (size_t)N * N)) != CD_OK) return fail(rc);
+    if ((rc = scratch_alloc(&dC, (size_t)N * O, st)) != CD_OK) return fail(rc);
+    if (wantJ && (rc = scratch_alloc(&dJ, (size_t)N * N, st)) != CD_OK) return fail(rc);
+    if (wantK && (rc = scratch_alloc(&dK, (size_t)N * N, st)) != CD_OK) return fail(rc);
     if (cudaMemcpyAsync(dC, C_occ, sizeof(double) * N * O, cudaMemcpyHostToDevice, st) != cudaSuccess) {
       set_error("cd_jk: copy of C_occ failed");
       return fail(CD_ECUDA);
     }
   }
-  if (m == CD_JK_BF16X3 || m == CD_JK_BF16X4) {
+  if (m == CD_JK_BF16X3 || m == CD_JK_BF16X4 || m == CD_JK_BF16X5) {
+    // the stored precision of the vectors decides what is sliced: the FP32 copy
+    // when the factor keeps one, otherwise the FP64 vectors themselves
     const float* L32 = f->L32;
-    float* tmp = nullptr;
-    if (!L32) {
-      if ((rc = dalloc(&tmp, (size_t)std::max<int64_t>(M, 1) * ld)) != CD_OK) return fail(rc);
-      if ((rc = launch_to_fp32(f->L, ld, M, ld, tmp, st)) != CD_OK) { cudaFree(tmp); return fail(rc); }
-      L32 = tmp;
+    float* tmp32 = nullptr;
+    if (!L32 && (mode & CD_JK_VEC_FP32)) {  // FP32-rounded vectors requested: round on the fly
+      if ((rc = scratch_alloc(&tmp32, (size_t)std::max<int64_t>(M, 1) * ld, st)) != CD_OK) return fail(rc);
+      if ((rc = launch_to_fp32(f->L, ld, M, ld, tmp32, st)) != CD_OK) { scratch_free(tmp32, st); return fail(rc); }
+      L32 = tmp32;
     }
-    rc = jk_mixed(L32, ld, M, n, N, O, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, dJ, dK, wantJ, wantK,
-                  m == CD_JK_BF16X4 ? 4 : 3, st);
-    if (tmp) { cudaStreamSynchronize(st); cudaFree(tmp); }
+    rc = jk_mixed(L32, L32 ? nullptr : f->L, ld, M, n, N, O, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, dJ, dK,
+                  wantJ, wantK, m == CD_JK_BF16X5 ? 5 : (m == CD_JK_BF16X4 ? 4 : 3), st);
+    scratch_free(tmp32, st);
     if (rc != CD_OK) return fail(rc);
   } else {
     if (wantJ) {
-      if ((rc = dalloc(&d, (size_t)std::max<int64_t>(n, 1))) != CD_OK) return fail(rc);
-      if ((rc = dalloc(&v, (size_t)std::max<int64_t>(M, 1))) != CD_OK) return fail(rc);
-      if ((rc = dalloc(&Jp, (size_t)std::max<int64_t>(n, 1))) != CD_OK) return fail(rc);
+      if ((rc = scratch_alloc(&d, (size_t)std::max<int64_t>(n, 1), st)) != CD_OK) return fail(rc);
+      if ((rc = scratch_alloc(&v, (size_t)std::max<int64_t>(M, 1), st)) != CD_OK) return fail(rc);
+      if ((rc = scratch_alloc(&Jp, (size_t)std::max<int64_t>(n, 1), st)) != CD_OK) return fail(rc);
       if ((rc = launch_density_packed(dC, N, O, f->sys->row_mu_dev, f->sys->row_nu_dev, n, d, st)) != CD_OK) return fail(rc);
       if ((rc = launch_gemv_rows<double>(f->L, ld, M, n, d, v, st)) != CD_OK) return fail(rc);
       if ((rc = launch_gemv_cols<double>(f->L, ld, M, n, v, Jp, st)) != CD_OK) return fail(rc);
@@ -766,8 +870,8 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
     if (wantK) {
       const double perP = 8.0 * ((double)N * N + (double)N * O);
       int Pc = (int)std::max<double>(1.0, std::min<double>((double)std::max<int64_t>(M, 1), 2.0e9 / perP));
-      if ((rc = dalloc(&Lfull, (size_t)Pc * N * N)) != CD_OK) return fail(rc);
-      if ((rc = dalloc(&B, (size_t)Pc * N * O)) != CD_OK) return fail(rc);
+      if ((rc = scratch_alloc(&Lfull, (size_t)Pc * N * N, st)) != CD_OK) return fail(rc);
+      if ((rc = scratch_alloc(&B, (size_t)Pc * N * O, st)) != CD_OK) return fail(rc);
       if (cudaMemsetAsync(dK, 0, sizeof(double) * N * N, st) != cudaSuccess) return fail(CD_ECUDA);
       for (int64_t P0 = 0; P0 < M; P0 += Pc) {
         const int pc = (int)std::min<int64_t>(Pc, M - P0);
@@ -785,6 +889,86 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
   }
   if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("cd_jk: CUDA failure"); return fail(CD_ECUDA); }
   return fail(CD_OK);
+}
+
+
+// ---------------------------------------------------------------- batch ----
+// Many independent systems: a pool of host workers, each driving its own
+// non-blocking CUDA stream, takes systems from a shared queue (largest first)
+// and runs set-up, decomposition and J/K for each.  Small systems do not fill
+// the GPU on their own; running several at once on separate streams overlaps
+// their kernels.  Per-call scratch is stream-ordered, so workers never wait
+// on each other; objects are freed after every worker has finished.
+int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, const double* const* C_occ,
+                 const int32_t* n_occ, double* const* J, double* const* K, int32_t jk_mode, int32_t workers,
+                 void* stream) {
+  if (n_sys < 0 || (n_sys > 0 && (!bases || !opts || !C_occ || !n_occ || !J || !K))) {
+    set_error("cd_batch_run: bad argument");
+    return CD_EINVAL;
+  }
+  if (n_sys == 0) return CD_OK;
+  int dev = 0;
+  CD_CUDA(cudaGetDevice(&dev));
+  const int nw = std::max(1, std::min<int>(n_sys, workers > 0 ? workers : 8));
+  // order: largest basis first
+  std::vector<int> order(n_sys);
+  std::vector<int64_t> size(n_sys, 0);
+  for (int i = 0; i < n_sys; ++i) {
+    order[i] = i;
+    for (int sh = 0; sh < bases[i].n_shells; ++sh) size[i] += 2 * (bases[i].l ? bases[i].l[sh] : 0) + 1;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size[a] > size[b]; });
+  cudaEvent_t start;
+  CD_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CD_CUDA(cudaEventRecord(start, (cudaStream_t)stream));
+  std::atomic<int> next{0};
+  std::vector<int> rcs(n_sys, CD_OK);
+  std::vector<std::string> msgs(n_sys);
+  std::vector<cd_system*> systems(n_sys, nullptr);
+  std::vector<cd_factor_t*> factors(n_sys, nullptr);
+  std::vector<cudaStream_t> streams(nw, nullptr);
+  std::vector<cudaEvent_t> done(nw, nullptr);
+  for (int w = 0; w < nw; ++w) {
+    CD_CUDA(cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking));
+    CD_CUDA(cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming));
+    CD_CUDA(cudaStreamWaitEvent(streams[w], start, 0));
+  }
+  auto work = [&](int w) {
+    cudaSetDevice(dev);
+    cudaStream_t st = streams[w];
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n_sys) break;
+      const int i = order[k];
+      int rc = cd_system_create(&bases[i], opts[i].schwarz, st, &systems[i]);
+      if (rc == CD_OK) rc = cd_eri_factor_sys(systems[i], &opts[i], st, &factors[i]);
+      if (rc == CD_OK) rc = cd_jk(factors[i], C_occ[i], n_occ[i], J[i], K[i], jk_mode, st);
+      rcs[i] = rc;
+      if (rc != CD_OK) msgs[i] = g_err;
+    }
+    cudaEventRecord(done[w], st);
+  };
+  std::vector<std::thread> th;
+  for (int w = 1; w < nw; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& t : th) t.join();
+  for (int w = 0; w < nw; ++w) cudaStreamWaitEvent((cudaStream_t)stream, done[w], 0);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  for (int i = 0; i < n_sys; ++i) {
+    if (factors[i]) factor_release(factors[i]);
+    if (systems[i]) system_release(systems[i]);
+  }
+  for (int w = 0; w < nw; ++w) {
+    cudaEventDestroy(done[w]);
+    cudaStreamDestroy(streams[w]);
+  }
+  cudaEventDestroy(start);
+  for (int i = 0; i < n_sys; ++i)
+    if (rcs[i] != CD_OK) {
+      set_error("cd_batch_run: system " + std::to_string(i) + ": " + msgs[i]);
+      return rcs[i];
+    }
+  return CD_OK;
 }
 
 }  // extern "C"

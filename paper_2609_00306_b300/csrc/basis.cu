@@ -73,7 +73,7 @@ int validate_and_normalise(const cd_basis_t* b, HostBasis* hb) {
 // Records for the shell pairs (s1[k], s2[k]), s1 >= s2, in the given order.
 // row[] is filled with the packed pair index (callers remap it).
 void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std::vector<int32_t>& s2,
-                 PairSetHost* out) {
+                 PairSetHost* out, double prune) {
   const double c0 = sqrt(2.0) * pow(kPi, 1.25);
   size_t n = s1.size();
   out->pp_off.assign(n + 1, 0);
@@ -104,13 +104,15 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
       for (int j = 0; j < hb.nprim[B]; ++j) {
         double a = hb.exps[hb.pofs[A] + i], b = hb.exps[hb.pofs[B] + j];
         double z = a + b;
+        const double kp = c0 * hb.dcoef[hb.pofs[A] + i] * hb.dcoef[hb.pofs[B] + j] * exp(-a * b / z * AB2) / z;
+        if (prune > 0.0 && fabs(kp) < prune) continue;
         out->zeta[q] = z;
         for (int x = 0; x < 3; ++x) {
           double P = (a * cA[x] + b * cB[x]) / z;
           out->P[3 * q + x] = P;
           out->PA[3 * q + x] = P - cA[x];
         }
-        out->Kp[q] = c0 * hb.dcoef[hb.pofs[A] + i] * hb.dcoef[hb.pofs[B] + j] * exp(-a * b / z * AB2) / z;
+        out->Kp[q] = kp;
         ++q;
       }
     // components: i on A, j on B
@@ -124,6 +126,7 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
       }
   }
   out->pp_off[n] = (int32_t)q;
+  out->zeta.resize(q); out->P.resize(3 * q); out->PA.resize(3 * q); out->Kp.resize(q);
 }
 
 template <class T>
@@ -167,6 +170,33 @@ static long double boys_series(int m, long double T) {
   return expl(-T) * sum;
 }
 
+int scratch_alloc_bytes(void** p, size_t bytes, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<int, bool> configured;
+  *p = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { set_error("cudaGetDevice failed"); return CD_ECUDA; }
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (!configured[dev]) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+      configured[dev] = true;
+    }
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device scratch allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    return CD_ENOMEM;
+  }
+  return CD_OK;
+}
+
 const double* boys_table_device(int* rc) {
   static std::mutex mu;
   static std::map<int, double*> tables;
@@ -176,9 +206,11 @@ const double* boys_table_device(int* rc) {
   auto it = tables.find(dev);
   if (it != tables.end()) { *rc = CD_OK; return it->second; }
   std::vector<double> h((size_t)kBoysPoints * kBoysCols);
-  for (int k = 0; k < kBoysPoints; ++k)
-    for (int m = 0; m < kBoysCols; ++m)
-      h[(size_t)k * kBoysCols + m] = (double)boys_series(m, (long double)k * (long double)kBoysStep);
+  for (int k = 0; k < kBoysPoints; ++k) {
+    const long double T = (long double)k * (long double)kBoysStep;
+    for (int m = 0; m < kBoysFcols; ++m) h[(size_t)k * kBoysCols + m] = (double)boys_series(m, T);
+    h[(size_t)k * kBoysCols + kBoysFcols] = (double)expl(-T);
+  }
   double* d = nullptr;
   if (cudaMalloc(&d, sizeof(double) * h.size()) != cudaSuccess ||
       cudaMemcpy(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess) {

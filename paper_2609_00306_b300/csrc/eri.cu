@@ -3,12 +3,16 @@
 // One thread evaluates one (bra shell pair | ket function pair) combination:
 // all bra components (up to 9) against one ket component, looping over the
 // primitive quartets.  Per primitive quartet the Boys function comes from a
-// Taylor table (F_L) plus downward recursion; the vertical recurrence of
+// Taylor table (F_L and exp(-T)) plus downward recursion, and 1/(p+q) and its
+// square root from one FP32 seed refined by Newton steps in FP64 (the FP64
+// pipe is the bound, so no library division, sqrt or exp); the vertical recurrence of
 // Obara and Saika, in the two-electron form of Head-Gordon and Pople, builds
 // [e0|f0] (e <= 2 on the bra, f <= 2 on the ket); after contraction the
 // horizontal recurrences (a,b+1_j| = (a+1_j,b| + AB_j (a,b| and
 // |c,d+1_l) = |c+1_l,d) + CD_l |c,d) give the requested components.
 // Bra shell pairs are sorted by angular class, so warps run one class.
+#include <algorithm>
+#include <cstring>
 #include "internal.cuh"
 
 namespace cd {
@@ -18,22 +22,31 @@ constexpr double kSqrtPiOver4 = 0.88622692545275801365;  // sqrt(pi)/2
 
 template <int L>
 __device__ __forceinline__ void boys_fm(double T, double (&F)[L + 1], const double* __restrict__ tab) {
-  const double emT = exp(-T);
   if (T < kBoysTmax) {
-    int k = __double2int_rn(T * (1.0 / kBoysStep));
-    double d = (double)k * kBoysStep - T;  // F_L(T) = sum_j F_{L+j}(T_k) d^j / j!
-    const double* __restrict__ r = tab + k * kBoysCols + L;
+    const int k = __double2int_rn(T * (1.0 / kBoysStep));
+    const double d = (double)k * kBoysStep - T;  // F_L(T) = sum_j F_{L+j}(T_k) d^j / j!
+    const double* __restrict__ row = tab + k * kBoysCols;
+    const double* __restrict__ r = row + L;
     double f = __ldg(r + kBoysTaylor - 1);
 #pragma unroll
     for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, d * (1.0 / (j + 1)), __ldg(r + j));
     F[L] = f;
+    if constexpr (L > 0) {
+      // exp(-T) = exp(-T_k) exp(d), exp(d) by Horner with constant coefficients 1/j!
+      constexpr double inv_fact[kExpTaylor] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720,
+                                               1.0 / 5040, 1.0 / 40320};
+      double e = inv_fact[kExpTaylor - 1];
 #pragma unroll
-    for (int m = L - 1; m >= 0; --m) F[m] = fma(2.0 * T, F[m + 1], emT) * (1.0 / (2 * m + 1));
+      for (int j = kExpTaylor - 2; j >= 0; --j) e = fma(e, d, inv_fact[j]);
+      const double emT = __ldg(row + kBoysFcols) * e;
+#pragma unroll
+      for (int m = L - 1; m >= 0; --m) F[m] = fma(2.0 * T, F[m + 1], emT) * (1.0 / (2 * m + 1));
+    }
   } else {
     F[0] = kSqrtPiOver4 * rsqrt(T);
     const double h = 0.5 / T;
 #pragma unroll
-    for (int m = 0; m < L; ++m) F[m + 1] = fma((double)(2 * m + 1), F[m], -emT) * h;
+    for (int m = 0; m < L; ++m) F[m + 1] = (double)(2 * m + 1) * F[m] * h;
   }
 }
 
@@ -45,21 +58,26 @@ __device__ __forceinline__ double sel3(const double (&v)[3], int k) {
   return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
 }
 
-// Contracted bra-shell-pair x ket-function-pair block.  out[i*3+j] receives
-// (a_i b_j | c_kc d_kd) for the bra components (i on A, j on B).
-template <int LA, int LB, int LC, int LD>
+// Contracted bra-shell-pair x NC ket-function-pair block (the NC ket pairs
+// belong to one ket shell pair).  out[c][i*3+j] receives (a_i b_j | c_kc d_kd)
+// for ket component c and the bra components (i on A, j on B).  The primitive
+// set-up, Boys function and bra recurrence are shared by the NC components.
+template <int LA, int LB, int LC, int LD, int NC>
 __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const PairSet& ket, int64_t sk,
-                                        int kc, int kd, const double* __restrict__ tab, double (&out)[9]) {
+                                        const int (&kcs)[NC], const int (&kds)[NC], const double* __restrict__ tab,
+                                        double (&out)[NC][9]) {
   constexpr int EB = LA + LB;
   constexpr int FK = LC + LD;
   constexpr int L = EB + FK;
   constexpr int NE = EB == 0 ? 1 : (EB == 1 ? 3 : 9);  // s | p | p + d
   constexpr int NF = FK == 2 ? 2 : 1;
-  double acc[NE][NF];
+  double acc[NC][NE][NF];
 #pragma unroll
-  for (int e = 0; e < NE; ++e)
+  for (int c = 0; c < NC; ++c)
 #pragma unroll
-    for (int f = 0; f < NF; ++f) acc[e][f] = 0.0;
+    for (int e = 0; e < NE; ++e)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) acc[c][e][f] = 0.0;
 
   const int b0 = __ldg(bra.pp_off + sb), b1 = __ldg(bra.pp_off + sb + 1);
   const int k0 = __ldg(ket.pp_off + sk), k1 = __ldg(ket.pp_off + sk + 1);
@@ -76,16 +94,20 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
       PQ[1] = Py - __ldg(ket.P + 3 * ik + 1);
       PQ[2] = Pz - __ldg(ket.P + 3 * ik + 2);
       const double s = p + q;
-      const double is = 1.0 / s;
+      // y = 1/sqrt(s): FP32 seed (rel. error < 2^-22), two Newton steps in FP64 (error < 2^-88)
+      double y = (double)rsqrtf((float)s);
+      y = y * fma(-0.5 * s, y * y, 1.5);
+      y = y * fma(-0.5 * s, y * y, 1.5);
+      const double is = y * y;
       const double rho = p * q * is;
       const double T = rho * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
-      const double base = Kb * __ldg(ket.Kp + ik) * sqrt(is);
+      const double base = Kb * __ldg(ket.Kp + ik) * y;
       double F[L + 1];
       boys_fm<L>(T, F, tab);
       double S0[L + 1];
 #pragma unroll
       for (int m = 0; m <= L; ++m) S0[m] = base * F[m];
-      // ---- bra vertical recurrence: [p|0]^(m), [d|0]^(m)
+      // ---- bra vertical recurrence: [p|0]^(m), [d|0]^(m)  (shared by the ket components)
       double WP[3], e1[3][L > 0 ? L : 1], e2[6][L > 1 ? L - 1 : 1];
       if constexpr (EB >= 1) {
         const double c = -q * is;
@@ -110,147 +132,181 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
             }
       }
       if constexpr (FK == 0) {
-        if constexpr (EB == 0) acc[0][0] += S0[0];
+        if constexpr (EB == 0) acc[0][0][0] += S0[0];
         if constexpr (EB >= 1) {
 #pragma unroll
-          for (int i = 0; i < 3; ++i) acc[i][0] += e1[i][0];
+          for (int i = 0; i < 3; ++i) acc[0][i][0] += e1[i][0];
         }
         if constexpr (EB == 2) {
 #pragma unroll
-          for (int t = 0; t < 6; ++t) acc[3 + t][0] += e2[t][0];
+          for (int t = 0; t < 6; ++t) acc[0][3 + t][0] += e2[t][0];
         }
       } else {
-        // ---- ket vertical recurrence for f = 1_kc (m <= FK-1), then 1_kc + 1_kd
         const double pis = p * is;
         double QC[3];
         QC[0] = __ldg(ket.PA + 3 * ik); QC[1] = __ldg(ket.PA + 3 * ik + 1); QC[2] = __ldg(ket.PA + 3 * ik + 2);
         double WQ3[3] = {pis * PQ[0], pis * PQ[1], pis * PQ[2]};
-        const double QCk = sel3(QC, kc), WQk = sel3(WQ3, kc);
         const double o2s = 0.5 * is;
-        constexpr int MF = FK;  // m range needed at level f = 1
-        double f1s[MF], f1p[3][MF], f1d[6][MF];
 #pragma unroll
-        for (int m = 0; m < MF; ++m) {
-          f1s[m] = fma(QCk, S0[m], WQk * S0[m + 1]);
-          if constexpr (EB >= 1) {
+        for (int cc = 0; cc < NC; ++cc) {
+          const int kc = kcs[cc], kd = kds[cc];
+          // ---- ket vertical recurrence for f = 1_kc (m <= FK-1), then 1_kc + 1_kd
+          const double QCk = sel3(QC, kc), WQk = sel3(WQ3, kc);
+          constexpr int MF = FK;
+          double f1s[MF], f1p[3][MF], f1d[6][MF];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              double v = fma(QCk, e1[i][m], WQk * e1[i][m + 1]);
-              if (i == kc) v = fma(o2s, S0[m + 1], v);
-              f1p[i][m] = v;
+          for (int m = 0; m < MF; ++m) {
+            f1s[m] = fma(QCk, S0[m], WQk * S0[m + 1]);
+            if constexpr (EB >= 1) {
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                double v = fma(QCk, e1[i][m], WQk * e1[i][m + 1]);
+                if (i == kc) v = fma(o2s, S0[m + 1], v);
+                f1p[i][m] = v;
+              }
+            }
+            if constexpr (EB == 2) {
+#pragma unroll
+              for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j) {
+                  double v = fma(QCk, e2[didx(i, j)][m], WQk * e2[didx(i, j)][m + 1]);
+                  double lower = (i == kc ? e1[j][m + 1] : 0.0) + (j == kc ? e1[i][m + 1] : 0.0);
+                  f1d[didx(i, j)][m] = fma(o2s, lower, v);
+                }
             }
           }
-          if constexpr (EB == 2) {
+          if constexpr (FK == 1) {
+            if constexpr (EB == 0) acc[cc][0][0] += f1s[0];
+            if constexpr (EB >= 1) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int j = i; j < 3; ++j) {
-                double v = fma(QCk, e2[didx(i, j)][m], WQk * e2[didx(i, j)][m + 1]);
-                double lower = (i == kc ? e1[j][m + 1] : 0.0) + (j == kc ? e1[i][m + 1] : 0.0);
-                f1d[didx(i, j)][m] = fma(o2s, lower, v);
-              }
-          }
-        }
-        if constexpr (FK == 1) {
-          if constexpr (EB == 0) acc[0][0] += f1s[0];
-          if constexpr (EB >= 1) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) acc[i][0] += f1p[i][0];
-          }
-          if constexpr (EB == 2) {
-#pragma unroll
-            for (int t = 0; t < 6; ++t) acc[3 + t][0] += f1d[t][0];
-          }
-        } else {
-          const double QCl = sel3(QC, kd), WQl = sel3(WQ3, kd);
-          const double o2q = 0.5 / q, rq = pis;
-          const double dkl = (kc == kd) ? o2q : 0.0;
-          // [e|1k+1l] = QC_l [e|1k]^0 + WQ_l [e|1k]^1 + d_kl/(2q)([e|0]^0 - rho/q [e|0]^1) + e_l/(2s) [e-1_l|1k]^1
-          if constexpr (EB == 0) {
-            double v = fma(QCl, f1s[0], WQl * f1s[1]);
-            acc[0][0] += fma(dkl, fma(-rq, S0[1], S0[0]), v);
-            acc[0][1] += f1s[0];
-          }
-          if constexpr (EB >= 1) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              double v = fma(QCl, f1p[i][0], WQl * f1p[i][1]);
-              v = fma(dkl, fma(-rq, e1[i][1], e1[i][0]), v);
-              if (i == kd) v = fma(o2s, f1s[1], v);
-              acc[i][0] += v;
-              acc[i][1] += f1p[i][0];
+              for (int i = 0; i < 3; ++i) acc[cc][i][0] += f1p[i][0];
             }
-          }
-          if constexpr (EB == 2) {
+            if constexpr (EB == 2) {
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+              for (int t = 0; t < 6; ++t) acc[cc][3 + t][0] += f1d[t][0];
+            }
+          } else {
+            const double QCl = sel3(QC, kd), WQl = sel3(WQ3, kd);
+            const double o2q = 0.5 / q, rq = pis;
+            const double dkl = (kc == kd) ? o2q : 0.0;
+            // [e|1k+1l] = QC_l [e|1k]^0 + WQ_l [e|1k]^1 + d_kl/(2q)([e|0]^0 - rho/q [e|0]^1) + e_l/(2s) [e-1_l|1k]^1
+            if constexpr (EB == 0) {
+              double v = fma(QCl, f1s[0], WQl * f1s[1]);
+              acc[cc][0][0] += fma(dkl, fma(-rq, S0[1], S0[0]), v);
+              acc[cc][0][1] += f1s[0];
+            }
+            if constexpr (EB >= 1) {
 #pragma unroll
-              for (int j = i; j < 3; ++j) {
-                const int t = didx(i, j);
-                double v = fma(QCl, f1d[t][0], WQl * f1d[t][1]);
-                v = fma(dkl, fma(-rq, e2[t][1], e2[t][0]), v);
-                double lower = (i == kd ? f1p[j][1] : 0.0) + (j == kd ? f1p[i][1] : 0.0);
-                v = fma(o2s, lower, v);
-                acc[3 + t][0] += v;
-                acc[3 + t][1] += f1d[t][0];
+              for (int i = 0; i < 3; ++i) {
+                double v = fma(QCl, f1p[i][0], WQl * f1p[i][1]);
+                v = fma(dkl, fma(-rq, e1[i][1], e1[i][0]), v);
+                if (i == kd) v = fma(o2s, f1s[1], v);
+                acc[cc][i][0] += v;
+                acc[cc][i][1] += f1p[i][0];
               }
+            }
+            if constexpr (EB == 2) {
+#pragma unroll
+              for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j) {
+                  const int t = didx(i, j);
+                  double v = fma(QCl, f1d[t][0], WQl * f1d[t][1]);
+                  v = fma(dkl, fma(-rq, e2[t][1], e2[t][0]), v);
+                  double lower = (i == kd ? f1p[j][1] : 0.0) + (j == kd ? f1p[i][1] : 0.0);
+                  v = fma(o2s, lower, v);
+                  acc[cc][3 + t][0] += v;
+                  acc[cc][3 + t][1] += f1d[t][0];
+                }
+            }
           }
         }
       }
     }
   }
-  // ---- ket horizontal recurrence
-  double val[NE];
+  double CD3[3] = {0.0, 0.0, 0.0};
   if constexpr (FK == 2) {
-    double CD3[3] = {__ldg(ket.AB + 3 * sk), __ldg(ket.AB + 3 * sk + 1), __ldg(ket.AB + 3 * sk + 2)};
-    const double CDl = sel3(CD3, kd);
-#pragma unroll
-    for (int e = 0; e < NE; ++e) val[e] = fma(CDl, acc[e][1], acc[e][0]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < NE; ++e) val[e] = acc[e][0];
+    CD3[0] = __ldg(ket.AB + 3 * sk); CD3[1] = __ldg(ket.AB + 3 * sk + 1); CD3[2] = __ldg(ket.AB + 3 * sk + 2);
   }
-  // ---- bra horizontal recurrence
+  double AB3[3] = {0.0, 0.0, 0.0};
+  if constexpr (LB == 1) {
+    AB3[0] = __ldg(bra.AB + 3 * sb); AB3[1] = __ldg(bra.AB + 3 * sb + 1); AB3[2] = __ldg(bra.AB + 3 * sb + 2);
+  }
 #pragma unroll
-  for (int c = 0; c < 9; ++c) out[c] = 0.0;
-  if constexpr (EB == 0) {
-    out[0] = val[0];
-  } else if constexpr (LB == 0) {
+  for (int cc = 0; cc < NC; ++cc) {
+    // ---- ket horizontal recurrence
+    double val[NE];
+    if constexpr (FK == 2) {
+      const double CDl = sel3(CD3, kds[cc]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[3 * i] = val[i];
-  } else {
-    double AB3[3] = {__ldg(bra.AB + 3 * sb), __ldg(bra.AB + 3 * sb + 1), __ldg(bra.AB + 3 * sb + 2)};
+      for (int e = 0; e < NE; ++e) val[e] = fma(CDl, acc[cc][e][1], acc[cc][e][0]);
+    } else {
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+      for (int e = 0; e < NE; ++e) val[e] = acc[cc][e][0];
+    }
+    // ---- bra horizontal recurrence
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int t = i <= j ? didx(i, j) : didx(j, i);
-        out[3 * i + j] = fma(AB3[j], val[i], val[3 + t]);
-      }
+    for (int c = 0; c < 9; ++c) out[cc][c] = 0.0;
+    if constexpr (EB == 0) {
+      out[cc][0] = val[0];
+    } else if constexpr (LB == 0) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) out[cc][3 * i] = val[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int t = i <= j ? didx(i, j) : didx(j, i);
+          out[cc][3 * i + j] = fma(AB3[j], val[i], val[3 + t]);
+        }
+    }
   }
 }
 
-template <int LA, int LB>
-__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, int64_t b0, int64_t b1, PairSet ket,
-                                                          const KetDesc* __restrict__ kets, double* __restrict__ out,
-                                                          int64_t ld, const double* __restrict__ tab) {
-  const int j = blockIdx.y;
-  const KetDesc kd = kets[j];
-  const int64_t sb = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sb >= b1) return;
-  double v[9];
-  const int cls = kd.lc * 2 + kd.ld;
-  if (cls == 0) quartet<LA, LB, 0, 0>(bra, sb, ket, kd.sp, 0, 0, tab, v);
-  else if (cls == 2) quartet<LA, LB, 1, 0>(bra, sb, ket, kd.sp, kd.kc, 0, tab, v);
-  else quartet<LA, LB, 1, 1>(bra, sb, ket, kd.sp, kd.kc, kd.kd, tab, v);
-  double* o = out + (int64_t)kd.slot * ld;
+template <int LA, int LB, int LC, int LD, int NC>
+__device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, const PairSet& ket, const KetGroup& kg,
+                                             double* __restrict__ out, int64_t ld, const double* __restrict__ tab) {
+  int kcs[NC], kds[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    kcs[c] = c < kg.nc ? kg.kc[c] : kg.kc[0];
+    kds[c] = c < kg.nc ? kg.kd[c] : kg.kd[0];
+  }
+  double v[NC][9];
+  quartet<LA, LB, LC, LD, NC>(bra, sb, ket, kg.sp, kcs, kds, tab, v);
   const int32_t* rw = bra.row + 9 * sb;
 #pragma unroll
-  for (int c = 0; c < 9; ++c) {
-    if (LA == 0 && c != 0) continue;
-    if (LA == 1 && LB == 0 && (c % 3) != 0) continue;
-    const int32_t r = __ldg(rw + c);
-    if (r >= 0) o[r] = v[c];
+  for (int cc = 0; cc < NC; ++cc) {
+    if (cc >= kg.nc) break;
+    double* o = out + (int64_t)kg.slot[cc] * ld;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      if (LA == 0 && c != 0) continue;
+      if (LA == 1 && LB == 0 && (c % 3) != 0) continue;
+      const int32_t r = __ldg(rw + c);
+      if (r >= 0) o[r] = v[cc][c];
+    }
+  }
+}
+
+// grid: x = tiles of bra shell pairs of one class, y = ket groups
+template <int LA, int LB>
+__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, int64_t b0, int64_t b1, PairSet ket,
+                                                          const KetGroup* __restrict__ groups, double* __restrict__ out,
+                                                          int64_t ld, const double* __restrict__ tab) {
+  const KetGroup kg = groups[blockIdx.y];
+  const int64_t sb = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sb >= b1) return;
+  const int cls = kg.lc * 2 + kg.ld;
+  if (cls == 0) column_block<LA, LB, 0, 0, 1>(bra, sb, ket, kg, out, ld, tab);
+  else if (cls == 2) {
+    if (kg.nc == 1) column_block<LA, LB, 1, 0, 1>(bra, sb, ket, kg, out, ld, tab);
+    else column_block<LA, LB, 1, 0, 3>(bra, sb, ket, kg, out, ld, tab);
+  } else {
+    if (kg.nc == 1) column_block<LA, LB, 1, 1, 1>(bra, sb, ket, kg, out, ld, tab);
+    else column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab);
   }
 }
 
@@ -264,15 +320,16 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
   if (sp >= s1) return;
   const int32_t r = __ldg(ps.row + 9 * sp + c);
   if (r < 0) return;
-  double v[9];
-  quartet<LA, LB, LA, LB>(ps, sp, ps, sp, c / 3, c % 3, tab, v);
-  diag[r] = v[c];
+  double v[1][9];
+  const int kcs[1] = {c / 3}, kds[1] = {c % 3};
+  quartet<LA, LB, LA, LB, 1>(ps, sp, ps, sp, kcs, kds, tab, v);
+  diag[r] = v[0][c];
 }
 
 }  // namespace
 
 int launch_eri_columns(const PairSet& bra, const int64_t* /*bra_order*/, const int64_t* class_off,
-                       const PairSet& ket, const KetDesc* kets_dev, int nket,
+                       const PairSet& ket, const KetGroup* kets_dev, int nket,
                        double* out, int64_t ld, const double* boys, cudaStream_t st) {
   if (nket <= 0) return CD_OK;
   for (int cls = 0; cls < 3; ++cls) {
@@ -304,4 +361,30 @@ int launch_eri_diag(const PairSet& ps, const int64_t* /*order*/, const int64_t* 
   return CD_OK;
 }
 
+}  // namespace cd
+
+namespace cd {
+std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets) {
+  std::vector<KetDesc> k(kets);
+  std::stable_sort(k.begin(), k.end(), [](const KetDesc& a, const KetDesc& b) { return a.sp < b.sp; });
+  std::vector<KetGroup> out;
+  for (size_t i = 0; i < k.size();) {
+    size_t j = i;
+    while (j < k.size() && k[j].sp == k[i].sp && j - i < 3) ++j;
+    KetGroup g;
+    std::memset(&g, 0, sizeof(g));
+    g.sp = k[i].sp;
+    g.lc = k[i].lc;
+    g.ld = k[i].ld;
+    g.nc = (int8_t)(j - i);
+    for (size_t c = 0; c < j - i; ++c) {
+      g.kc[c] = k[i + c].kc;
+      g.kd[c] = k[i + c].kd;
+      g.slot[c] = k[i + c].slot;
+    }
+    out.push_back(g);
+    i = j;
+  }
+  return out;
+}
 }  // namespace cd

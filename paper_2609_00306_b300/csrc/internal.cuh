@@ -31,14 +31,40 @@ struct Status {
     if (_rc != CD_OK) return _rc;    \
   } while (0)
 
+// ----- stream-ordered scratch memory ------------------------------------------
+// Per-call scratch comes from the device's default memory pool through
+// cudaMallocAsync / cudaFreeAsync on the call's stream, so concurrent calls on
+// different streams never wait for each other in an implicit device-wide
+// synchronisation.  The pool keeps freed memory (release threshold = max), so
+// repeated calls do not remap it.  Long-lived objects (systems, factors) use
+// cudaMalloc / cudaFree.
+int scratch_alloc_bytes(void** p, size_t bytes, cudaStream_t st);
+inline void scratch_free(void* p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+template <class T>
+int scratch_alloc(T** p, size_t n, cudaStream_t st) {
+  return scratch_alloc_bytes((void**)p, sizeof(T) * (n ? n : 1), st);
+}
+
 // ----- Boys function table (Taylor expansion about grid points) ------------
-// F_m(T) at T_k = k * kBoysStep for k < kBoysPoints and m <= kBoysMaxM.
+// Row k holds F_0..F_12 at T_k = k * kBoysStep and, in the last column,
+// exp(-T_k).  Below kBoysTmax, F_L(T) and exp(-T) come from 8- and 9-term
+// Taylor expansions about the nearest grid point (|T - T_k| <= 0.05) and the
+// lower orders from the downward recursion; above it, F_0 = sqrt(pi / 4T)
+// and the upward recursion with exp(-T) < 1e-26 dropped.
 constexpr int kBoysMaxM = 4;            // l <= 1 per centre -> L <= 4
-constexpr int kBoysTaylor = 8;          // Taylor terms
+constexpr int kBoysTaylor = 8;          // Taylor terms for F_L
+constexpr int kExpTaylor = 9;           // Taylor terms for exp(-T)
 constexpr double kBoysStep = 0.1;
-constexpr double kBoysTmax = 36.0;      // above: asymptotic form + upward recursion
-constexpr int kBoysPoints = 362;
-constexpr int kBoysCols = kBoysMaxM + kBoysTaylor + 1;   // F_0..F_12 per point
+constexpr double kBoysTmax = 60.0;
+constexpr int kBoysPoints = 602;
+constexpr int kBoysFcols = kBoysMaxM + kBoysTaylor + 1;  // F_0..F_12
+constexpr int kBoysCols = kBoysFcols + 1;                // + exp(-T_k)
+// bra primitive pairs with |Kp| below this are dropped: their contribution to
+// any integral is below ~1e-18 (Kp_ket / sqrt(zeta + eta) < 1e4, angular
+// factors times F_m < 1e2)
+constexpr double kPrimPrune = 1e-24;
 
 // ----- shell-pair records (device, structure of arrays) -------------------
 // A shell pair joins shells S1 >= S2 (shell index).  It is stored in canonical
@@ -81,7 +107,7 @@ struct HostBasis {
 
 int validate_and_normalise(const cd_basis_t* b, HostBasis* hb);
 void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std::vector<int32_t>& s2,
-                 PairSetHost* out);
+                 PairSetHost* out, double prune = 0.0);
 int upload_pairs(const PairSetHost& h, PairSet* d, cudaStream_t st);
 void free_pairs(PairSet* d);
 const double* boys_table_device(int* rc);   // per device, built once
@@ -94,10 +120,24 @@ struct KetDesc {
   int8_t lc, ld;
 };
 
+// up to three ket function pairs of one ket shell pair, evaluated together
+// (shared primitive set-up, Boys function and bra recurrence)
+struct KetGroup {
+  int32_t sp;        // shell pair index in `all`
+  int8_t lc, ld;     // canonical class of the shell pair
+  int8_t nc;         // components in the group (1..3)
+  int8_t pad;
+  int8_t kc[3], kd[3];
+  int16_t pad2;
+  int32_t slot[3];   // output columns: out + slot * ld
+};
+// group ket descriptors of the same shell pair (at most 3 per group)
+std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets);
+
 // ERI kernels (eri.cu)
-// out[j * ld + row] = (bra rows | ket j) for every bra shell pair in `bra`
+// out[slot * ld + row] = (bra rows | ket component) for every bra shell pair in `bra`
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
-                       const PairSet& ket, const KetDesc* kets_dev, int nket,
+                       const PairSet& ket, const KetGroup* groups_dev, int ngroups,
                        double* out, int64_t ld, const double* boys, cudaStream_t st);
 // diag[row] = (row|row) for every shell pair in `ps` (rows from ps.row)
 int launch_eri_diag(const PairSet& ps, const int64_t* order, const int64_t* class_off,
@@ -126,4 +166,18 @@ struct cd_system {
   const double* boys = nullptr;
   double schwarz = 0.0;
   double ms_setup = 0.0;
+};
+
+struct cd_factor {
+  cd_system* sys = nullptr;
+  bool owns_sys = false;
+  int64_t M = 0, Mcap = 0, ld = 0, n = 0;
+  double* L = nullptr;      // FP64 vectors [Mcap][ld]
+  float* L32 = nullptr;     // FP32 copy [M][ld] when requested
+  int vec_precision = CD_FP64;
+  std::vector<int64_t> piv;
+  std::vector<double> gaps;
+  std::vector<double> resid;
+  double resid_max = 0.0;
+  double stats[16] = {0};
 };

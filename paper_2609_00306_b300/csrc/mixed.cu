@@ -9,6 +9,9 @@
 // FP64 packed density in FP64.
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 #include "internal.cuh"
 #include "ozaki.cuh"
 #include "pivot.cuh"
@@ -21,41 +24,52 @@ __global__ void to_fp32_kernel(const double* __restrict__ src, int64_t total, fl
     dst[i] = __double2float_rn(src[i]);
 }
 
-// one warp per row: e[r] = frexp exponent of max_k |X[r][k]| (0 for a zero row)
+// one warp per row: e[r] = frexp exponent of max_k |X[r][k]| (0 for a zero row);
+// the maximum is taken on the magnitude bit patterns (integer compares only)
+__device__ __forceinline__ unsigned long long mag_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long mag_bits(float x) {
+  return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
 template <class T>
 __global__ void row_exp_warp_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
                                     int32_t* __restrict__ e) {
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (r >= rows) return;
-  float m = 0.0f;
-  double md = 0.0;
-  for (int64_t c = lane; c < k; c += 32) md = fmax(md, fabs((double)X[r * ldx + c]));
-  (void)m;
-  for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+  unsigned long long m = 0;
+  for (int64_t c = lane; c < k; c += 32) m = max(m, mag_bits(X[r * ldx + c]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (lane == 0) {
     int ex = 0;
-    if (md > 0.0) frexp(md, &ex);
-    e[r] = ex;
+    if (m != 0) {
+      const double mx = sizeof(T) == 8 ? __longlong_as_double((long long)m) : (double)__uint_as_float((unsigned)m);
+      frexp(mx, &ex);
+    }
+    e[r] = max(ex, -900);  // keeps 2^(8S-1-e) a normal double
   }
 }
 
 // dst[s][r][k] = s-th 8-bit slice of X[r][k] / 2^e[r]  (S = 3 or 4 slices: 24 or 32 bits
-// of fixed point below the row maximum)
-template <class T>
-__global__ void slice3_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
-                              const int32_t* __restrict__ e, __nv_bfloat16* __restrict__ dst, int64_t kpitch, int S) {
+// of fixed point below the row maximum); one multiply by a power of two and one
+// conversion per element, then integer digit extraction
+template <class T, int S>
+__global__ void slice_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows, int64_t k,
+                             const int32_t* __restrict__ e, __nv_bfloat16* __restrict__ dst, int64_t kpitch) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * kpitch) return;
   const int64_t r = t / kpitch, c = t % kpitch;
-  double x = c < k ? ldexp((double)X[r * ldx + c], -e[r]) : 0.0;
-  double w = 128.0;
-  for (int s = 0; s < S; ++s) {
-    const double a = rint(x * w);
-    dst[((int64_t)s * rows + r) * kpitch + c] = __double2bfloat16(a);
-    x -= a / w;
-    w *= 256.0;
+  long long v = 0;
+  if (c < k) {
+    // exact scaling by a power of two (in FP64: the factor may leave the FP32 range)
+    const double scale = __longlong_as_double((long long)(1023 + 8 * S - 1 - e[r]) << 52);
+    v = __double2ll_rn((double)X[r * ldx + c] * scale);
   }
+  float a[S];
+  fixed_digits<S>(v, a);
+#pragma unroll
+  for (int s = 0; s < S; ++s) dst[((int64_t)s * rows + r) * kpitch + c] = __float2bfloat16_rn(a[s]);
 }
 
 // B chunk from the fixed-point product: D[i][p*N + mu] (i < O) -> Bm[mu][p*Op + i]
@@ -72,13 +86,15 @@ __global__ void half_finalize_kernel(const unsigned long long* __restrict__ D, i
   Bm[(int64_t)mu * ((int64_t)Pc * Op) + (int64_t)p * Op + i] = v;
 }
 
-// K[mu][nu] += 2 * 2^(e_mu + e_nu - F) * D[nu][mu]
+// K[mu][nu] += 2 * 2^(e_mu + e_nu - F) * D[max][min]  (only the upper triangle of
+// the symmetric product is computed: row index <= column index)
 __global__ void k_accumulate_kernel(const unsigned long long* __restrict__ D, int N, const int32_t* __restrict__ eB,
                                     int F, double* __restrict__ K) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)N * N) return;
   const int mu = (int)(t / N), nu = (int)(t % N);
-  K[t] += ldexp((double)(long long)D[(int64_t)nu * N + mu], eB[mu] + eB[nu] - F + 1);
+  const int lo = min(mu, nu), hi = max(mu, nu);
+  K[t] += ldexp((double)(long long)D[(int64_t)hi * N + lo], eB[mu] + eB[nu] - F + 1);
 }
 
 template <class T>
@@ -95,7 +111,10 @@ int launch_slice3(const T* X, int64_t ldx, int64_t rows, int64_t k, const int32_
                   int S, cudaStream_t st) {
   const int64_t tot = rows * kpitch;
   if (tot <= 0) return CD_OK;
-  slice3_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch, S);
+  const unsigned grid = (unsigned)((tot + 255) / 256);
+  if (S == 3) slice_kernel<T, 3><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
+  else if (S == 4) slice_kernel<T, 4><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
+  else slice_kernel<T, 5><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -121,7 +140,8 @@ int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* d
 
 namespace {
 struct MixedBufs {
-  float* Lfull = nullptr;
+  cudaStream_t st = nullptr;
+  void* Lfull = nullptr;
   void* Ls = nullptr;
   void* Cs = nullptr;
   double* Ct = nullptr;
@@ -132,19 +152,11 @@ struct MixedBufs {
   double *d = nullptr, *v = nullptr, *Jp = nullptr;
   int* err = nullptr;
   ~MixedBufs() {
-    cudaFree(Lfull); cudaFree(Ls); cudaFree(Cs); cudaFree(Ct); cudaFree(eL); cudaFree(eC); cudaFree(eB);
-    cudaFree(D1); cudaFree(D2); cudaFree(Bm); cudaFree(Bs); cudaFree(d); cudaFree(v); cudaFree(Jp); cudaFree(err);
+    for (void* p : {Lfull, Ls, Cs, (void*)Ct, (void*)eL, (void*)eC, (void*)eB, (void*)D1, (void*)D2, (void*)Bm,
+                    Bs, (void*)d, (void*)v, (void*)Jp, (void*)err})
+      scratch_free(p, st);
   }
 };
-template <class T>
-int mal(T** p, size_t n) {
-  if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1)) != cudaSuccess) {
-    cudaGetLastError();
-    set_error("mixed J/K: device allocation failed");
-    return CD_ENOMEM;
-  }
-  return CD_OK;
-}
 __global__ void transpose_kernel(const double* __restrict__ C, int N, int O, double* __restrict__ Ct) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)N * O) return;
@@ -153,37 +165,74 @@ __global__ void transpose_kernel(const double* __restrict__ C, int N, int O, dou
 }
 }  // namespace
 
-int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
-             const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
-             int S, cudaStream_t st) {
+// Optional stage timing (environment variable CDERI_TIMING=1): CUDA events
+// around the stages of the exchange build, summed over chunks, on stderr.
+struct StageTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> stage;
+  void mark(int s) {
+    if (!on) return;
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+    stage.push_back(s);
+  }
+  void report(const char* names[], int nst) {
+    if (!on || ev.empty()) return;
+    cudaEventSynchronize(ev.back());
+    std::vector<double> t(nst, 0.0);
+    for (size_t i = 1; i < ev.size(); ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+      t[stage[i]] += ms;
+    }
+    for (int i = 0; i < nst; ++i) fprintf(stderr, "[cderi timing] %-12s %9.2f ms\n", names[i], t[i]);
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+template <class TL>
+int jk_mixed_t(const TL* L32, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
+               const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
+               int S, cudaStream_t st) {
+  StageTimer tm;
+  tm.on = getenv("CDERI_TIMING") != nullptr;
+  tm.st = st;
+  const char* names[] = {"start", "J", "unpack", "slice_L", "gemm_BLC", "finalize_B", "slice_B", "gemm_K", "accum_K"};
+  tm.mark(0);
   MixedBufs b;
+  b.st = st;
   if (wantJ) {
-    CD_TRY(mal(&b.d, (size_t)n));
-    CD_TRY(mal(&b.v, (size_t)M));
-    CD_TRY(mal(&b.Jp, (size_t)n));
+    CD_TRY(scratch_alloc(&b.d, (size_t)n, st));
+    CD_TRY(scratch_alloc(&b.v, (size_t)M, st));
+    CD_TRY(scratch_alloc(&b.Jp, (size_t)n, st));
     CD_TRY(launch_density_packed(C_dev, N, O, mu, nu, n, b.d, st));
-    CD_TRY(launch_gemv_rows<float>(L32, ld, M, n, b.d, b.v, st));
-    CD_TRY(launch_gemv_cols<float>(L32, ld, M, n, b.v, b.Jp, st));
+    CD_TRY(launch_gemv_rows<TL>(L32, ld, M, n, b.d, b.v, st));
+    CD_TRY(launch_gemv_cols<TL>(L32, ld, M, n, b.v, b.Jp, st));
     CD_TRY(launch_unpack_sym(b.Jp, mu, nu, n, N, J_dev, st));
+    tm.mark(1);
   }
   if (wantK) {
     const int64_t Np = (N + 7) / 8 * 8;                     // k pitch of the first product (16-byte rows)
     const int Op = (O + 63) / 64 * 64;                      // padded occupied count (k blocks of the second product)
     // chunk of vectors: k-dim of the second product Pc*Op, scratch ~ Pc*N^2*(4 + 6) bytes
-    int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(M, (int64_t)(2.0e9 / ((4.0 + 2.0 * S) * N * (double)N))));
+    int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(M, (int64_t)(2.0e9 / ((sizeof(TL) + 2.0 * S) * N * (double)N))));
     Pc = std::min(Pc, 64);
-    CD_TRY(mal(&b.Lfull, (size_t)Pc * N * N));
-    CD_TRY(mal((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np));
-    CD_TRY(mal((uint16_t**)&b.Cs, (size_t)S * O * Np));
-    CD_TRY(mal(&b.Ct, (size_t)O * N));
-    CD_TRY(mal(&b.eL, (size_t)Pc * N));
-    CD_TRY(mal(&b.eC, (size_t)O));
-    CD_TRY(mal(&b.eB, (size_t)N));
-    CD_TRY(mal(&b.D1, (size_t)O * Pc * N));
-    CD_TRY(mal(&b.D2, (size_t)N * N));
-    CD_TRY(mal(&b.Bm, (size_t)N * Pc * Op));
-    CD_TRY(mal((uint16_t**)&b.Bs, (size_t)S * N * Pc * Op));
-    CD_TRY(mal(&b.err, 1));
+    CD_TRY(scratch_alloc((TL**)&b.Lfull, (size_t)Pc * N * N, st));
+    CD_TRY(scratch_alloc((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np, st));
+    CD_TRY(scratch_alloc((uint16_t**)&b.Cs, (size_t)S * O * Np, st));
+    CD_TRY(scratch_alloc(&b.Ct, (size_t)O * N, st));
+    CD_TRY(scratch_alloc(&b.eL, (size_t)Pc * N, st));
+    CD_TRY(scratch_alloc(&b.eC, (size_t)O, st));
+    CD_TRY(scratch_alloc(&b.eB, (size_t)N, st));
+    CD_TRY(scratch_alloc(&b.D1, (size_t)O * Pc * N, st));
+    CD_TRY(scratch_alloc(&b.D2, (size_t)N * N, st));
+    CD_TRY(scratch_alloc(&b.Bm, (size_t)N * Pc * Op, st));
+    CD_TRY(scratch_alloc((uint16_t**)&b.Bs, (size_t)S * N * Pc * Op, st));
+    CD_TRY(scratch_alloc(&b.err, 1, st));
     CD_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), st));
     CD_CUDA(cudaMemsetAsync(K_dev, 0, sizeof(double) * N * N, st));
     // C^T slices (rows i, k = nu)
@@ -197,12 +246,17 @@ int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, c
     for (int64_t P0 = 0; P0 < M; P0 += Pc) {
       const int pc = (int)std::min<int64_t>(Pc, M - P0);
       // dense FP32 L^P rows (p, mu), their exponents and slices
-      CD_TRY(launch_unpack_vectors<float>(L32, ld, P0, pc, mu, nu, n, N, b.Lfull, st));
-      CD_TRY(launch_row_exp_warp<float>(b.Lfull, N, (int64_t)pc * N, N, b.eL, st));
-      CD_TRY(launch_slice3<float>(b.Lfull, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+      tm.mark(0);
+      TL* Lf = (TL*)b.Lfull;
+      CD_TRY(launch_unpack_vectors<TL>(L32, ld, P0, pc, mu, nu, n, N, Lf, st));
+      tm.mark(2);
+      CD_TRY(launch_row_exp_warp<TL>(Lf, N, (int64_t)pc * N, N, b.eL, st));
+      CD_TRY(launch_slice3<TL>(Lf, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+      tm.mark(3);
       // B^P = L^P C for the chunk: D1[i][p*N+mu]
       CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * O * pc * N, st));
       CD_TRY(ozaki_gemm(p1, b.Ls, (int64_t)pc * N, Np, b.Cs, O, Np, N, b.D1, (int64_t)pc * N, 1, b.err, st));
+      tm.mark(4);
       CD_CUDA(cudaMemsetAsync(b.Bm, 0, sizeof(double) * N * pc * Op, st));
       {
         const int64_t tot = (int64_t)pc * N * O;
@@ -210,16 +264,21 @@ int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, c
                                                                             b.eC, p1.F, b.Bm);
         count_launch();
       }
+      tm.mark(5);
       // K += 2 B B^T over the chunk's (p, i)
       const int64_t kd = (int64_t)pc * Op;
       CD_TRY(launch_row_exp_warp<double>(b.Bm, kd, N, kd, b.eB, st));
       CD_TRY(launch_slice3<double>(b.Bm, kd, N, kd, b.eB, b.Bs, kd, S, st));
       p2.F = 61 - ilog2_ceil(kd);
+      tm.mark(6);
       CD_CUDA(cudaMemsetAsync(b.D2, 0, sizeof(unsigned long long) * N * N, st));
-      CD_TRY(ozaki_gemm(p2, b.Bs, N, kd, b.Bs, N, kd, kd, b.D2, N, 2, b.err, st));
+      CD_TRY(ozaki_gemm(p2, b.Bs, N, kd, b.Bs, N, kd, kd, b.D2, N, 2, b.err, st, true));
+      tm.mark(7);
       k_accumulate_kernel<<<(unsigned)(((int64_t)N * N + 255) / 256), 256, 0, st>>>(b.D2, N, b.eB, p2.F, K_dev);
       count_launch();
+      tm.mark(8);
     }
+    tm.report(names, 9);
     int herr = 0;
     CD_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CD_CUDA(cudaStreamSynchronize(st));
@@ -227,6 +286,13 @@ int jk_mixed(const float* L32, int64_t ld, int64_t M, int64_t n, int N, int O, c
   }
   CD_CUDA(cudaStreamSynchronize(st));
   return CD_OK;
+}
+
+int jk_mixed(const float* L32, const double* L64, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
+             const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
+             int S, cudaStream_t st) {
+  if (L32) return jk_mixed_t<float>(L32, ld, M, n, N, O, C_dev, mu, nu, J_dev, K_dev, wantJ, wantK, S, st);
+  return jk_mixed_t<double>(L64, ld, M, n, N, O, C_dev, mu, nu, J_dev, K_dev, wantJ, wantK, S, st);
 }
 
 }  // namespace cd

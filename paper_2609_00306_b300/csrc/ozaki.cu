@@ -1,11 +1,13 @@
 // ozaki.cu -- exact-slice GEMM on the tcgen05 tensor cores (see ozaki.cuh).
 //
-// CTA tile 128 (rows of A) x 64 (rows of B), k-blocks of 32 BF16 (64-byte
-// rows, 64-byte swizzle) staged by TMA in a STAGES-deep ring.  Warp roles:
-// warps 0-3 drain tensor memory (one TMEM lane per thread), warp 4 issues the
-// TMA loads, warp 5 allocates tensor memory and issues the MMAs.  Every
-// mbarrier wait is bounded; on time-out the CTA stops, frees its tensor memory
-// and sets the error flag.
+// CTA tile 128 (rows of A) x BN (rows of B; 64, or 32 for 7 slices), k-blocks
+// of 32 BF16 (64-byte rows, 64-byte swizzle) staged by TMA in a STAGES-deep
+// ring.  Two accumulator sets in tensor memory (when they fit) let the drain
+// of one k-chunk overlap the MMAs of the next.  Warp roles: warps 0-3 drain
+// tensor memory (one TMEM lane per thread), warp 4 issues the TMA loads, warp
+// 5 allocates tensor memory and issues the MMAs.  Every mbarrier wait is
+// bounded; on time-out the CTA stops, frees its tensor memory and sets the
+// error flag.
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -17,7 +19,7 @@
 namespace cd {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 32;
+constexpr int BM = 128, BK = 32;
 constexpr int kThreads = 192;
 
 // 64-byte swizzled K-major descriptor: rows of 32 bf16 (64 B), 8-row groups 512 B apart
@@ -31,41 +33,50 @@ __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
   return d;
 }
 
-template <int SA, int SB, int KEEP, int STAGES>
+template <int SA, int SB, int KEEP, int BN, int STAGES>
 struct Cfg {
   static constexpr int G = KEEP - 1;                       // accumulator groups (s+t = 2..KEEP)
   static constexpr int A_BYTES = SA * BM * BK * 2;
   static constexpr int B_BYTES = SB * BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  static constexpr int TMEM_COLS = G * BN <= 32 ? 32 : (G * BN <= 64 ? 64 : (G * BN <= 128 ? 128 : (G * BN <= 256 ? 256 : 512)));
+  static constexpr int ACC_COLS = G * BN;                  // one accumulator set
+  // two accumulator sets (double buffering) when they fit in the 512 columns
+  static constexpr int NBUF = 2 * ACC_COLS <= 512 ? 2 : 1;
+  static constexpr int NEED = NBUF * ACC_COLS;
+  static constexpr int TMEM_COLS = NEED <= 32 ? 32 : (NEED <= 64 ? 64 : (NEED <= 128 ? 128 : (NEED <= 256 ? 256 : 512)));
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+  static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
+  static_assert(SMEM <= 232448, "shared memory over the per-CTA limit");
 };
 
-template <int SA, int SB, int KEEP, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1)
+// BN = 32 tiles cap registers (two CTAs' worth) so that an FP64 kernel can share the SM
+template <int SA, int SB, int KEEP, int BN, int STAGES>
+__global__ void __launch_bounds__(kThreads, BN == 32 ? 2 : 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              int64_t m_rows, int64_t n_rows, int nkb_total, int kb_per_split, int kcb, int F,
-             unsigned long long* __restrict__ D, int64_t ldd, int* err) {
-  using C = Cfg<SA, SB, KEEP, STAGES>;
+             unsigned long long* __restrict__ D, int64_t ldd, int* err, int sym) {
+  using C = Cfg<SA, SB, KEEP, BN, STAGES>;
+  // symmetric product (A == B): tiles entirely below the diagonal are skipped
+  if (sym && (int64_t)blockIdx.x * BN + BN <= (int64_t)blockIdx.y * BM) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
-  uint64_t* tempty = tfull + 1;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+  uint64_t* tfull = empty + STAGES;      // [2] accumulator set ready for the drain
+  uint64_t* tempty = tfull + 2;          // [2] accumulator set drained
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  // column tiles vary fastest so that the CTAs sharing a row tile of A run together (L2 reuse)
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
   const int kb0 = blockIdx.z * kb_per_split;
   const int kb1 = min(nkb_total, kb0 + kb_per_split);
   const int nkb = kb1 - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-    tc::mbar_init(tfull, 1);
-    tc::mbar_init(tempty, 4);
+    for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 4); }
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -83,7 +94,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         for (int i = 0; i < nkb; ++i) {
           const int s = i % STAGES;
           const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, err)) break;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 2)) break;
           uint8_t* a = smem + s * C::STAGE_BYTES;
           uint8_t* b = a + C::A_BYTES;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
@@ -101,37 +112,37 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           const int s = i % STAGES;
           const uint32_t ph = (uint32_t)((i / STAGES) & 1);
           const bool chunk_start = (i % kcb) == 0;
-          if (chunk_start && chunk > 0) {
-            if (!tc::mbar_wait(tempty, (uint32_t)((chunk - 1) & 1), abort_flag, err)) break;
+          const int buf = C::NBUF == 2 ? (chunk & 1) : 0;
+          if (chunk_start && chunk >= C::NBUF) {
+            // the set about to be overwritten was filled by chunk - NBUF: wait for its drain
+            const int prev = chunk - C::NBUF;
+            if (!tc::mbar_wait(&tempty[buf], (uint32_t)((prev / C::NBUF) & 1), abort_flag, err, 8)) break;
             tc::tc_fence_after();
           }
-          if (!tc::mbar_wait(&full[s], ph, abort_flag, err)) break;
+          if (!tc::mbar_wait(&full[s], ph, abort_flag, err, 1)) break;
           tc::tc_fence_after();
           const uint32_t a = tc::smem_u32(smem + s * C::STAGE_BYTES);
           const uint32_t b = a + C::A_BYTES;
+          const uint32_t acc = tmem + (uint32_t)(buf * C::ACC_COLS);
 #pragma unroll
           for (int sa = 0; sa < SA; ++sa)
 #pragma unroll
             for (int sb = 0; sb < SB; ++sb) {
               const int g = sa + sb;  // 0-based: s + t - 2
               if (g > KEEP - 2) continue;
-              // first product of this group inside the chunk overwrites
-              bool first_of_group = chunk_start;
-              if (first_of_group) {
-                // earlier (sa', sb') with the same g in this loop nest?
-                const int sa_first = g < SB ? 0 : g - (SB - 1);
-                first_of_group = (sa == sa_first);
-              }
+              // the first product of each group inside a chunk overwrites the accumulator
+              const int sa_first = g < SB ? 0 : g - (SB - 1);
+              const bool first_of_group = chunk_start && (sa == sa_first);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 const uint64_t ad = sdesc_k_sw64(a + sa * (BM * BK * 2) + kk * 32);
                 const uint64_t bd = sdesc_k_sw64(b + sb * (BN * BK * 2) + kk * 32);
-                tc::umma_bf16(tmem + g * BN, ad, bd, idesc, (first_of_group && kk == 0) ? 0u : 1u);
+                tc::umma_bf16(acc + g * BN, ad, bd, idesc, (first_of_group && kk == 0) ? 0u : 1u);
               }
             }
           tc::umma_commit(&empty[s]);
           if ((i % kcb) == kcb - 1 || i == nkb - 1) {
-            tc::umma_commit(tfull);
+            tc::umma_commit(&tfull[buf]);
             ++chunk;
           }
         }
@@ -145,15 +156,17 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       const int nchunks = (nkb + kcb - 1) / kcb;
       bool ok = true;
       for (int ch = 0; ch < nchunks; ++ch) {
-        if (!tc::mbar_wait(tfull, (uint32_t)(ch & 1), abort_flag, err)) { ok = false; break; }
+        const int buf = C::NBUF == 2 ? (ch & 1) : 0;
+        if (!tc::mbar_wait(&tfull[buf], (uint32_t)((ch / C::NBUF) & 1), abort_flag, err, 4)) { ok = false; break; }
         tc::tc_fence_after();
+        const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * C::ACC_COLS);
 #pragma unroll
         for (int g = 0; g < KEEP - 1; ++g) {
           const int sh = F - 8 * (g + 2) + 2;  // weight of group g in units of 2^-F
 #pragma unroll
           for (int cb = 0; cb < BN / 16; ++cb) {
             uint32_t v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + g * BN + cb * 16, v);
+            tc::tmem_ld16(acc + g * BN + cb * 16, v);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
@@ -167,7 +180,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         }
         tc::tc_fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(tempty);
+        if (lane == 0) tc::mbar_arrive(&tempty[buf]);
       }
       const int64_t m = m0 + row;
       if (ok && m < m_rows) {
@@ -217,56 +230,59 @@ int make_map(CUtensorMap* map, const void* base, int S, int64_t rows, int64_t kd
   return CD_OK;
 }
 
-template <int SA, int SB, int KEEP, int STAGES>
+template <int SA, int SB, int KEEP, int BN, int STAGES>
 int run(const CUtensorMap& ta, const CUtensorMap& tb, int64_t a_rows, int64_t b_rows, int nkb, int ksplit, int kcb,
-        int F, unsigned long long* D, int64_t ldd, int* err, cudaStream_t st) {
-  using C = Cfg<SA, SB, KEEP, STAGES>;
-  auto k = ozaki_kernel<SA, SB, KEEP, STAGES>;
+        int F, unsigned long long* D, int64_t ldd, int* err, int sym, cudaStream_t st) {
+  using C = Cfg<SA, SB, KEEP, BN, STAGES>;
+  auto k = ozaki_kernel<SA, SB, KEEP, BN, STAGES>;
   CD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const int per = (nkb + ksplit - 1) / ksplit;
   const int nsplit = (nkb + per - 1) / per;
-  dim3 grid((unsigned)((a_rows + BM - 1) / BM), (unsigned)((b_rows + BN - 1) / BN), (unsigned)nsplit);
-  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err);
+  const int64_t row_tiles = (a_rows + BM - 1) / BM;
+  if (row_tiles > 65535) { set_error("ozaki_gemm: too many row tiles"); return CD_EINVAL; }
+  dim3 grid((unsigned)((b_rows + BN - 1) / BN), (unsigned)row_tiles, (unsigned)nsplit);
+  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err, sym);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
 }
 
+template <int S>
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t src_rs, int64_t src_ks, int64_t rows,
-                                  int64_t kcount, const int32_t* __restrict__ row_exp, int S,
+                                  int64_t kcount, const int32_t* __restrict__ row_exp,
                                   __nv_bfloat16* __restrict__ dst, int64_t dst_rows, int64_t kpitch, int64_t k0) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * kcount) return;
   const int64_t r = t / kcount, k = t % kcount;
-  double x = ldexp(src[r * src_rs + k * src_ks], -row_exp[r]);
-  // first slice: 2^-7 resolution; later ones: 2^-8 of the previous
-  double w = 128.0;
-  for (int s = 0; s < S; ++s) {
-    const double a = rint(x * w);
-    dst[((int64_t)s * dst_rows + r) * kpitch + k0 + k] = __double2bfloat16(a);
-    x = fma(-a, 1.0 / w, x);
-    w *= 256.0;
-  }
+  // one FP64 multiply by 2^(8S-1-e) and one conversion, then integer digits
+  const double scale = __longlong_as_double((long long)(1023 + 8 * S - 1 - row_exp[r]) << 52);
+  float a[S];
+  fixed_digits<S>(__double2ll_rn(src[r * src_rs + k * src_ks] * scale), a);
+#pragma unroll
+  for (int s = 0; s < S; ++s) dst[((int64_t)s * dst_rows + r) * kpitch + k0 + k] = __float2bfloat16_rn(a[s]);
 }
 
 }  // namespace
 
 int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpitch, const void* Bs, int64_t b_rows,
                int64_t b_kpitch, int64_t kdim, unsigned long long* D, int64_t ldd, int ksplit, int* err_dev,
-               cudaStream_t st) {
+               cudaStream_t st, bool sym) {
+  const int symi = sym ? 1 : 0;
   if (kdim <= 0 || a_rows <= 0 || b_rows <= 0) return CD_OK;
   CUtensorMap ta, tb;
+  const int bn = (p.SA >= 5) ? 32 : 64;   // accumulator width: 2 x groups x bn must fit 512 TMEM columns
   CD_TRY(make_map(&ta, As, p.SA, a_rows, kdim, a_kpitch, BM));
-  CD_TRY(make_map(&tb, Bs, p.SB, b_rows, kdim, b_kpitch, BN));
+  CD_TRY(make_map(&tb, Bs, p.SB, b_rows, kdim, b_kpitch, bn));
   const int nkb = (int)((kdim + BK - 1) / BK);
-  // exactness of the FP32 accumulation: (groups sharing an accumulator) * kc * 2^14 <= 2^24
+  // exactness of the FP32 accumulation: (products sharing an accumulator) * kc * 129^2 <= 2^24
   const int maxg = std::min(p.KEEP - 1, std::min(p.SA, p.SB));
-  int kc = 1024 / std::max(1, maxg);
+  int kc = (int)(16777216.0 / (std::max(1, maxg) * kSliceProdMax));
   int kcb = std::max(1, kc / BK);
-  if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
-  if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
-  if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 2>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
-  if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, st);
+  if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 64, 5>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
+  if (p.SA == 5 && p.SB == 5 && p.KEEP == 6) return run<5, 5, 6, 32, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
+  if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
+  if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 32, 3>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
+  if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
   set_error("ozaki_gemm: unsupported slice plan");
   return CD_EINVAL;
 }
@@ -276,8 +292,14 @@ int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int
                           cudaStream_t st) {
   const int64_t tot = rows * kcount;
   if (tot <= 0) return CD_OK;
-  slice_rows_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, S,
-                                                                    (__nv_bfloat16*)dst, dst_rows, kpitch, k0);
+  const unsigned grid = (unsigned)((tot + 255) / 256);
+  __nv_bfloat16* d = (__nv_bfloat16*)dst;
+  if (S == 7) slice_rows_kernel<7><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 5) slice_rows_kernel<5><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 4) slice_rows_kernel<4><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 3) slice_rows_kernel<3><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 1) slice_rows_kernel<1><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else { set_error("slice: unsupported slice count"); return CD_EINVAL; }
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -305,7 +327,7 @@ __global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_
     m = fmax(m, sh[0]);
     int ex = 0;
     if (m > 0.0) frexp(m, &ex);
-    e[r] = ex;
+    e[r] = max(ex, -900);  // keeps 2^(8S-1-e) a normal double
   }
 }
 __global__ void fixed_to_f64_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int64_t m, int64_t n,
@@ -326,8 +348,8 @@ extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const do
     set_error("cd_slice_matmul: bad argument");
     return CD_EINVAL;
   }
-  if (slices != 1 && slices != 3 && slices != 4 && slices != 7) {
-    set_error("cd_slice_matmul: slices must be 1, 3, 4 or 7");
+  if (slices != 1 && slices != 3 && slices != 4 && slices != 5 && slices != 7) {
+    set_error("cd_slice_matmul: slices must be 1, 3, 4, 5 or 7");
     return CD_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -389,7 +411,7 @@ __global__ void row_exp_sqrt_kernel(const double* __restrict__ d, int64_t n, int
   int ex = 0;
   const double v = d[r];
   if (v > 0.0) frexp(sqrt(v), &ex);
-  e[r] = ex;
+  e[r] = max(ex, -900);
 }
 // Bs[s][j][k] = Ls[s][rows[j]][k] for valid[j] <= k < K, else 0 (k < kfill)
 __global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64_t n, int64_t kpitch,

@@ -17,6 +17,25 @@
 
 namespace cd {
 
+// Slices of one entry: v = round(x 2^(8S-1)) for |x| <= 1 (|v| <= 2^(8S-1)),
+// written as v = sum_s a_s 2^(8(S-1-s)) with balanced base-256 digits: the
+// low digits in [-128, 127], taken from the least significant end with
+// integer operations, the top digit the remainder (|a_0| <= 128).  Every digit
+// is an integer of at most 8 bits, exact in BF16.  (No FP64 arithmetic: the
+// FP64 pipe of this GPU is the scarce unit.)
+template <int S>
+__device__ __forceinline__ void fixed_digits(long long v, float (&a)[S]) {
+#pragma unroll
+  for (int s = S - 1; s >= 1; --s) {
+    const long long d = ((v + 128) & 255) - 128;
+    a[s] = (float)d;
+    v = (v - d) >> 8;
+  }
+  a[0] = (float)v;
+}
+// largest |a_s * b_t| used for the exactness bound of the FP32 accumulation
+constexpr double kSliceProdMax = 129.0 * 129.0;
+
 struct OzakiPlan {
   int SA = 3, SB = 3, KEEP = 4;   // slices of A and B, largest s + t kept
   int F = 40;                     // fixed-point fraction bits of the output
@@ -25,9 +44,12 @@ struct OzakiPlan {
 // Slice tensors: bf16 [S][rows][kpitch] (k contiguous).  Output: int64
 // D[n][m] (leading dimension ldd, column n = row of B) accumulated with
 // atomicAdd over k in [0, kdim) split into `ksplit` CTA slabs.
+// sym: A and B are the same matrix; tiles entirely below the diagonal
+// (column tile end <= row tile start) are skipped, so only D[n][m] with m <= n
+// (and some near the diagonal) is written.
 int ozaki_gemm(const OzakiPlan& plan, const void* As, int64_t a_rows, int64_t a_kpitch,
                const void* Bs, int64_t b_rows, int64_t b_kpitch, int64_t kdim,
-               unsigned long long* D, int64_t ldd, int ksplit, int* err_dev, cudaStream_t st);
+               unsigned long long* D, int64_t ldd, int ksplit, int* err_dev, cudaStream_t st, bool sym = false);
 
 // Slicing: x = X / 2^e (row exponent e given) -> S bf16 integer slices.
 // src element (r, k) at src[r * src_rs + k * src_ks]; dst[s][r][k0 + k] with pitch kpitch.

@@ -167,3 +167,99 @@ int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, 
 }
 
 }  // namespace cd
+
+// ---------------------------------------------------------------------------
+// Candidate selection: the b largest residual diagonals with D >= tau, by a
+// radix select over the IEEE-754 bit patterns (monotone for positive doubles,
+// 8 bits per pass, histograms in shared memory, the last CTA of each pass
+// picks the byte), then one compaction of every row at or above the b-th key.
+namespace cd {
+namespace {
+
+__device__ __forceinline__ unsigned long long dkey(double d, double tau) {
+  return d >= tau ? (unsigned long long)__double_as_longlong(d) : 0ull;
+}
+
+__global__ void __launch_bounds__(256) select_pass_kernel(const double* __restrict__ D, int64_t n, double tau, int pass,
+                                                          int b, SelectState* stt) {
+  __shared__ unsigned sh[256];
+  __shared__ bool last;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const unsigned long long prefix = stt->prefix, mask = stt->mask;
+  const int shift = 56 - 8 * pass;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = dkey(D[r], tau);
+    if (k != 0ull && (k & mask) == prefix) atomicAdd(&sh[(k >> shift) & 255ull], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (sh[i]) atomicAdd(&stt->hist[pass][i], sh[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(&stt->counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  if (pass > 0 && *(volatile int*)&stt->all) {  // decided in an earlier pass: nothing left to narrow
+    stt->counter = 0;
+    __threadfence();
+    return;
+  }
+  volatile unsigned* h = stt->hist[pass];
+  long long need = pass == 0 ? (long long)b : (long long)stt->need;
+  long long cum = 0, total = 0;
+  int chosen = -1;
+  for (int bin = 255; bin >= 0; --bin) total += h[bin];
+  if (pass == 0) stt->total = total;
+  if (total <= need) {
+    // every remaining key qualifies: threshold = smallest key with this prefix;
+    // later passes leave prefix, mask and need unchanged
+    stt->all = 1;
+    stt->need = need;
+  } else {
+    for (int bin = 255; bin >= 0; --bin) {
+      cum += h[bin];
+      if (cum >= need) { chosen = bin; need -= cum - h[bin]; break; }
+    }
+    stt->prefix = prefix | ((unsigned long long)chosen << shift);
+    stt->mask = mask | (255ull << shift);
+    stt->need = need;
+  }
+  stt->counter = 0;
+  __threadfence();
+}
+
+__global__ void __launch_bounds__(256) select_compact_kernel(const double* __restrict__ D, int64_t n, double tau,
+                                                             SelectState* stt, int64_t* __restrict__ rows_out,
+                                                             double* __restrict__ vals_out, int cap) {
+  const unsigned long long thr = stt->all ? (stt->prefix & stt->mask) : stt->prefix;
+  const bool all = stt->all != 0;
+  const unsigned long long mask = stt->mask, prefix = stt->prefix;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long k = dkey(D[r], tau);
+    if (k == 0ull) continue;
+    const bool take = all ? ((k & mask) >= prefix) : (k >= thr);
+    if (take) {
+      const int slot = (int)atomicAdd(&stt->count, 1u);
+      if (slot < cap) { rows_out[slot] = r; vals_out[slot] = D[r]; }
+    }
+  }
+}
+
+}  // namespace
+
+int launch_select(const double* D, int64_t n, double tau, int b, SelectState* stt, int64_t* rows_out,
+                  double* vals_out, int cap, cudaStream_t st) {
+  CD_CUDA(cudaMemsetAsync(stt, 0, sizeof(SelectState), st));
+  for (int pass = 0; pass < 8; ++pass) {
+    select_pass_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, pass, b, stt);
+    count_launch();
+  }
+  select_compact_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, stt, rows_out, vals_out, cap);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+}  // namespace cd

@@ -23,6 +23,19 @@ struct StepScratch {       // device scratch of the grid-wide argmax
 };
 
 int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st);
+
+// radix select of the b largest D >= tau (see pivot.cu)
+struct SelectState {
+  unsigned long long prefix, mask;
+  unsigned long long need;   // keys still to take below the current prefix (set before pass 0)
+  long long total;           // keys >= tau (pass 0)
+  int all;                   // fewer than b keys: take everything matching the prefix
+  unsigned counter;          // CTAs done in the current pass
+  unsigned count;            // compacted rows
+  unsigned hist[8][256];
+};
+int launch_select(const double* D, int64_t n, double tau, int b, SelectState* stt, int64_t* rows_out,
+                  double* vals_out, int cap, cudaStream_t st);
 int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, int64_t K, int64_t prow,
                     const double* Din, double* Dout, double* Lout, int64_t n, double neg_tol,
                     StepScratch* sc, StepResult* res, cudaStream_t st);

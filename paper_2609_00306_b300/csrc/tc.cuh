@@ -11,9 +11,18 @@ namespace cd {
 namespace tc {
 
 // ---- error flag written by kernels whose bounded waits give up ------------
-// bit 0: mbarrier wait timed out.  Kernels that time out stop issuing work,
-// free their tensor memory and return; the host reports CD_ETIMEOUT.
-constexpr uint32_t kWaitLimit = 1u << 26;   // ~0.1-1 s of polling
+// *err (global) collects bits: 1 = smem-stage "full" wait, 2 = "empty" wait,
+// 4 = accumulator "full" wait, 8 = accumulator "empty" wait.  A wait gives up
+// after kWaitNs of wall time (globaltimer) or as soon as any CTA has set *err;
+// the CTA then stops issuing work, frees its tensor memory and returns, and the
+// host reports CD_ETIMEOUT.
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -43,15 +52,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: returns false (and sets *err bit 0) when the limit is hit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+// bounded wait: false when it gave up (time limit, or another CTA/role gave up)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int which = 1) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 1023u) == 1023u && *abort_flag) return false;
+    if ((it & 255u) == 0u) {
+      if (*abort_flag || (err && *(volatile int*)err)) { *abort_flag = 1; return false; }
+      if (globaltimer_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        if (err) atomicOr(err, which);
+        return false;
+      }
+    }
   }
-  *abort_flag = 1;
-  if (err) atomicOr(err, 1);
-  return false;
 }
 
 // ---- TMA -------------------------------------------------------------------

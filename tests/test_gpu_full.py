@@ -1,0 +1,133 @@
+"""Parity at the configured sizes, in the launch configuration bench.py uses
+(default options: sliced tensor-core update, block 64).
+
+* sp400 (N=400, 60,980 rows): full oracle decomposition; vector count equal,
+  pivot sequences equal up to a near-tie (|dD| < 1e-12), J/K (FP64) to 1e-11.
+* sp2000 (N=2000, 680,253 rows; the benchmark workload): the oracle cannot run
+  the whole decomposition in test time, so checks use what it computes one
+  element at a time and properties that hold at any size:
+  - every pivot column is reproduced exactly by the vectors,
+    (p|c_K) = sum_J L^J_p L^J_{c_K}, on sampled rows p, with (p|c_K) from the
+    oracle (the residual of a pivot column is zero after its step);
+  - the residual bound |(p|q) - sum_J L^J_p L^J_q| <= max D_final < tau on
+    sampled pairs (p, q) with oracle integrals;
+  - screened rows and the diagonal match the oracle on a sample;
+  - the mixed J/K errors against the FP64 J/K of the same vectors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_00306_b300 import build
+    build.build()
+
+
+def test_sp400_full_parity():
+    import paper_2609_00306_b300 as cd
+    s = synth.make_workload("sp400")
+    o = oracle.Oracle(s.basis)
+    rows = o.screen(s.schwarz)
+    r = o.cd(rows, s.tau)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
+    prow, ppk, gaps, resid = f.pivots()
+    assert np.array_equal(ppk[:0], rows[:0])
+    assert f.n_rows == rows.shape[0]
+    assert f.M == r.M
+    assert f.max_resid < s.tau
+    div = np.nonzero(prow != r.piv)[0]
+    if div.size:
+        k = int(div[0])
+        fr = o.cd(rows, s.tau, forced=r.piv[:k])
+        assert abs(fr.D[prow[k]] - fr.D[r.piv[k]]) < 1e-12
+        # replay the oracle's sequence on the GPU and compare vectors
+        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, forced=r.piv)
+        prow, ppk, gaps, resid = f.pivots()
+        assert np.max(np.abs(gaps)) < 1e-12
+    L = f.vectors_host()
+    assert np.max(np.abs(L - r.L)) <= 1e-10 * np.max(np.abs(r.L))
+    J, K = oracle.jk_from_vectors(r.L, rows, s.C_occ)
+    Jg, Kg = f.jk(s.C_occ, cd.CD_JK_FP64)
+    assert np.max(np.abs(Jg - J)) <= 1e-11 * np.max(np.abs(J))
+    assert np.max(np.abs(Kg - K)) <= 1e-11 * np.max(np.abs(K))
+
+
+@pytest.fixture(scope="module")
+def sp2000():
+    import paper_2609_00306_b300 as cd
+    s = synth.make_workload("sp2000")
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=cd.CD_VEC_FP32)
+    sysm = cd.System(s.basis, s.schwarz)
+    packed, diag = sysm.rows()
+    prow, ppk, gaps, resid = f.pivots()
+    return s, f, packed, diag, prow, resid
+
+
+def test_sp2000_rows_and_diagonal_sampled(sp2000):
+    s, f, packed, diag, prow, resid = sp2000
+    o = oracle.Oracle(s.basis)
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, packed.shape[0], 300)
+    mu, nu = oracle.unpack_pair(packed[idx])
+    ref = np.array([o.eri(a, b, a, b) for a, b in zip(mu, nu)])
+    assert np.max(np.abs(diag[idx] - ref) / np.abs(ref)) < 1e-13
+    assert f.n_rows == packed.shape[0]
+    assert f.max_resid < s.tau and np.max(resid) < s.tau
+
+
+def test_sp2000_pivot_columns_reproduced(sp2000):
+    s, f, packed, diag, prow, resid = sp2000
+    o = oracle.Oracle(s.basis)
+    rng = np.random.default_rng(1)
+    ks = rng.choice(f.M, 12, replace=False)
+    ps = rng.integers(0, packed.shape[0], 40)
+    Lp = f.gather(ps)               # [M, 40]
+    Lc = f.gather(prow[ks])         # [M, 12]
+    pm, pn = oracle.unpack_pair(packed[ps])
+    for j, K in enumerate(ks):
+        c = prow[K]
+        cm, cn = oracle.unpack_pair(packed[c])
+        ref = np.array([o.eri(a, b, int(cm), int(cn)) for a, b in zip(pm, pn)])
+        got = Lp.T @ Lc[:, j]
+        assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, float(np.sqrt(diag[c] * np.max(diag))))
+        # triangular structure: vectors after step K vanish on pivot K's row
+        if K + 1 < f.M:
+            assert np.max(np.abs(Lc[K + 1:, j])) < 1e-12 * np.sqrt(np.max(diag))
+
+
+def test_sp2000_residual_bound_sampled(sp2000):
+    s, f, packed, diag, prow, resid = sp2000
+    o = oracle.Oracle(s.basis)
+    rng = np.random.default_rng(2)
+    p = rng.integers(0, packed.shape[0], 400)
+    q = rng.integers(0, packed.shape[0], 400)
+    pm, pn = oracle.unpack_pair(packed[p])
+    qm, qn = oracle.unpack_pair(packed[q])
+    ref = np.array([o.eri(a, b, c, d) for a, b, c, d in zip(pm, pn, qm, qn)])
+    got = np.einsum("kp,kp->p", f.gather(p), f.gather(q))
+    assert np.max(np.abs(ref - got)) <= f.max_resid + 1e-13
+
+
+def test_sp2000_mixed_jk_error_report(sp2000):
+    import paper_2609_00306_b300 as cd
+    s, f, packed, diag, prow, resid = sp2000
+    J64, K64 = f.jk(s.C_occ, cd.CD_JK_FP64)
+    Dm = oracle.density(s.C_occ)
+    for mode, tol in ((cd.CD_JK_BF16X3, 3e-6), (cd.CD_JK_BF16X4, 3e-7), (cd.CD_JK_BF16X5, 3e-7)):
+        # the factor keeps FP32 vectors (vec_precision=CD_VEC_FP32): FP32 storage limits K to ~1e-7
+        Jm, Km = f.jk(s.C_occ, mode)
+        eJ = np.max(np.abs(Jm - J64)) / np.max(np.abs(J64))
+        eK = np.max(np.abs(Km - K64)) / np.max(np.abs(K64))
+        tJ = abs(np.sum(Dm * (Jm - J64))) / abs(np.sum(Dm * J64))
+        tK = abs(np.sum(Dm * (Km - K64))) / abs(np.sum(Dm * K64))
+        print(f"sp2000 mode {mode}: max|dJ|/max|J|={eJ:.2e} max|dK|/max|K|={eK:.2e} dtr(DJ)={tJ:.2e} dtr(DK)={tK:.2e}")
+        assert eJ < max(tol, 1e-7) and eK < tol

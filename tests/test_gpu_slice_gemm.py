@@ -27,7 +27,7 @@ def _exps(X):
     return np.array([math.frexp(v)[1] if v > 0 else 0 for v in m])
 
 
-@pytest.mark.parametrize("S", [1, 3, 7])
+@pytest.mark.parametrize("S", [1, 3, 4, 5, 7])
 @pytest.mark.parametrize("shape", [(128, 64, 32), (300, 130, 777), (129, 65, 3001), (1000, 64, 96)])
 def test_slice_matmul_error_bound(S, shape):
     from paper_2609_00306_b300.cderi import slice_matmul
