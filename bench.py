@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-jk-alone", action="store_true", help="skip the separate J/K timings (FP64 K is slow)")
+    ap.add_argument("--jk-alone-modes", default="all",
+                    help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=8)
     ap.add_argument("--measure-fp64-peak", action="store_true",
                     help="compile and run the FP64 DFMA/DMMA microbenchmark, print its JSON line")
@@ -233,9 +235,12 @@ def run_ours(args, rank, world):
     # the mixed-precision error against the FP64 contraction of the same vectors
     jk = {}
     res = {}
+    sel_modes = None if args.jk_alone_modes == "all" else set(args.jk_alone_modes.split(","))
     for name, mode in modes.items():
         if args.no_jk_alone:
             break
+        if sel_modes is not None and name not in sel_modes:
+            continue
         try:
             torch.cuda.synchronize()
             ev0.record(stream)

@@ -47,7 +47,7 @@ __global__ void row_exp_warp_kernel(const T* __restrict__ X, int64_t ldx, int64_
       const double mx = sizeof(T) == 8 ? __longlong_as_double((long long)m) : (double)__uint_as_float((unsigned)m);
       frexp(mx, &ex);
     }
-    e[r] = max(ex, -900);  // keeps 2^(8S-1-e) a normal double
+    e[r] = ex;
   }
 }
 
@@ -61,11 +61,7 @@ __global__ void slice_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows,
   if (t >= rows * kpitch) return;
   const int64_t r = t / kpitch, c = t % kpitch;
   long long v = 0;
-  if (c < k) {
-    // exact scaling by a power of two (in FP64: the factor may leave the FP32 range)
-    const double scale = __longlong_as_double((long long)(1023 + 8 * S - 1 - e[r]) << 52);
-    v = __double2ll_rn((double)X[r * ldx + c] * scale);
-  }
+  if (c < k) v = scaled_double_to_ll(X[r * ldx + c], 8 * S - 1 - e[r]);  // integer ops only
   float a[S];
   fixed_digits<S>(v, a);
 #pragma unroll

@@ -33,6 +33,20 @@ __device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
   return d;
 }
 
+// An FP32 accumulator value that is an exact integer with |x| <= 2^24, as a
+// 64-bit integer, using only FP32 adds/FMAs and integer adds: x = 4096 h + l
+// with h = round(x / 4096) (|h| <= 4096) and |l| <= 2048, each turned into an
+// int by the 1.5 * 2^23 mantissa trick.  (A direct float -> int64 conversion
+// executes on the FP64 pipe of this GPU, which would bound the drain.)
+__device__ __forceinline__ long long exact_float_to_ll(float x) {
+  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+  const float h = __fadd_rn(__fmaf_rn(x, 1.0f / 4096.0f, kMagic), -kMagic);
+  const float l = __fmaf_rn(-h, 4096.0f, x);
+  const int hi = __float_as_int(__fadd_rn(h, kMagic)) - 0x4B400000;
+  const int lo = __float_as_int(__fadd_rn(l, kMagic)) - 0x4B400000;
+  return ((long long)hi << 12) + (long long)lo;
+}
+
 template <int SA, int SB, int KEEP, int BN, int STAGES>
 struct Cfg {
   static constexpr int G = KEEP - 1;                       // accumulator groups (s+t = 2..KEEP)
@@ -170,7 +184,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             tc::tmem_ld_wait();
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-              const long long iv = (long long)__float2ll_rn(__uint_as_float(v[c]));
+              const long long iv = exact_float_to_ll(__uint_as_float(v[c]));
               long long add;
               if (sh >= 0) add = iv << sh;
               else add = (iv + (1ll << (-sh - 1))) >> (-sh);
@@ -254,10 +268,9 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t src_rs
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * kcount) return;
   const int64_t r = t / kcount, k = t % kcount;
-  // one FP64 multiply by 2^(8S-1-e) and one conversion, then integer digits
-  const double scale = __longlong_as_double((long long)(1023 + 8 * S - 1 - row_exp[r]) << 52);
+  // round(x 2^(8S-1-e)) from the bit pattern, then integer digits
   float a[S];
-  fixed_digits<S>(__double2ll_rn(src[r * src_rs + k * src_ks] * scale), a);
+  fixed_digits<S>(scaled_double_to_ll(src[r * src_rs + k * src_ks], 8 * S - 1 - row_exp[r]), a);
 #pragma unroll
   for (int s = 0; s < S; ++s) dst[((int64_t)s * dst_rows + r) * kpitch + k0 + k] = __float2bfloat16_rn(a[s]);
 }
@@ -327,7 +340,7 @@ __global__ void row_exp_kernel(const double* __restrict__ X, int64_t ldx, int64_
     m = fmax(m, sh[0]);
     int ex = 0;
     if (m > 0.0) frexp(m, &ex);
-    e[r] = max(ex, -900);  // keeps 2^(8S-1-e) a normal double
+    e[r] = ex;
   }
 }
 __global__ void fixed_to_f64_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int64_t m, int64_t n,
@@ -411,7 +424,7 @@ __global__ void row_exp_sqrt_kernel(const double* __restrict__ d, int64_t n, int
   int ex = 0;
   const double v = d[r];
   if (v > 0.0) frexp(sqrt(v), &ex);
-  e[r] = max(ex, -900);
+  e[r] = ex;
 }
 // Bs[s][j][k] = Ls[s][rows[j]][k] for valid[j] <= k < K, else 0 (k < kfill)
 __global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64_t n, int64_t kpitch,

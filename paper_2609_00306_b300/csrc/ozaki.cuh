@@ -33,6 +33,34 @@ __device__ __forceinline__ void fixed_digits(long long v, float (&a)[S]) {
   }
   a[0] = (float)v;
 }
+// round(x * 2^k) for a finite double x with |x * 2^k| < 2^62, by integer
+// operations on the bit pattern (ties away from zero).  A direct double ->
+// int64 conversion would occupy the FP64 pipe, the scarce unit of this GPU.
+__device__ __forceinline__ long long scaled_double_to_ll(double x, int k) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return 0;  // zero or subnormal: below any fixed-point unit used here
+  const long long man = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+  const int sh = ex - 1075 + k;  // value = man * 2^sh
+  long long v;
+  if (sh >= 0) v = man << sh;
+  else if (sh > -63) v = (man + (1ll << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return bits < 0 ? -v : v;
+}
+__device__ __forceinline__ long long scaled_double_to_ll(float x, int k) {
+  const int bits = __float_as_int(x);
+  const int ex = (bits >> 23) & 0xFF;
+  if (ex == 0) return 0;
+  const long long man = (long long)((bits & 0x7FFFFF) | (1 << 23));
+  const int sh = ex - 150 + k;
+  long long v;
+  if (sh >= 0) v = man << sh;
+  else if (sh > -63) v = (man + (1ll << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return bits < 0 ? -v : v;
+}
+
 // largest |a_s * b_t| used for the exactness bound of the FP32 accumulation
 constexpr double kSliceProdMax = 129.0 * 129.0;
 
