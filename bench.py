@@ -264,8 +264,11 @@ def run_ours(args, rank, world):
             }
             if jk.get("fp64_ms") and jk.get(mx + "_ms"):
                 jk[mx + "_speedup_over_fp64"] = jk["fp64_ms"] / jk[mx + "_ms"]
-    # roofline of the dominant kernel of the step
+    # rooflines: the ERI column kernel (FP64 pipe) and the column update (tensor
+    # cores, or FP64 pipe in the DFMA mode); the one with the larger share of the
+    # step is reported as "roofline", the other as "roofline_update"/"roofline_eri"
     peak_fp64 = 148 * 2 * 2 * 2.032e9 / 1e12  # TFLOP/s: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz
+    peak_fp64_ops = 148 * 2 * 2.032e9 / 1e12  # T FP64-pipe operations/s (one DFMA/DMUL/DADD each)
     peaks = _measured_peaks()
     sliced = st.get("ms_colupd", 0) > 0 and _sliced(f)
     upd_fp64eq = st["colupd_flops"] / (st["ms_colupd"] * 1e-3) / 1e12 if st["ms_colupd"] > 0 else None
@@ -273,18 +276,34 @@ def run_ours(args, rank, world):
         # 28 BF16 slice products (s + t <= 8 of 7 x 7) per FP64-equivalent multiply-add
         ach = 28.0 * upd_fp64eq if upd_fp64eq else None
         pk = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1800.0
-        roof = {"kernel": "ozaki_kernel<7,7,8> (sliced column update, Eq. subtr)", "bound": "tensor",
-                "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": (ach / pk) if ach else None,
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16 (sustained) - of measured",
-                "fp64_equivalent_tflops": upd_fp64eq, "fp64_pipe_peak_tflops": peak_fp64,
-                "share_of_step": st["ms_colupd"] / ms if ms else None}
+        roof_upd = {"kernel": "ozaki_kernel<7,7,8,32,3> (sliced column update, Eq. subtr)", "bound": "tensor",
+                    "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": (ach / pk) if ach else None,
+                    "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16 (sustained) - of measured",
+                    "fp64_equivalent_tflops": upd_fp64eq, "fp64_pipe_peak_tflops": peak_fp64,
+                    "share_of_step": st["ms_colupd"] / ms if ms else None,
+                    "note": "runs concurrently with the ERI columns on a second stream"}
     else:
-        roof = {"kernel": "colupd_kernel (FP64 column update, Eq. subtr)", "bound": "alu",
-                "achieved": upd_fp64eq, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": (upd_fp64eq / peak_fp64) if upd_fp64eq else None, "traffic": None,
-                "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (recipe unit counts "
-                               "and clocks; microbenchmark measured 1.128 TFLOP/s at 1935 MHz)",
-                "share_of_step": st["ms_colupd"] / ms if ms else None}
+        roof_upd = {"kernel": "colupd_kernel (FP64 column update, Eq. subtr)", "bound": "alu",
+                    "achieved": upd_fp64eq, "peak": peak_fp64, "unit": "TFLOP/s",
+                    "frac": (upd_fp64eq / peak_fp64) if upd_fp64eq else None, "traffic": None,
+                    "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (recipe unit counts "
+                                   "and clocks; microbenchmark measured 1.128 TFLOP/s at 1935 MHz)",
+                    "share_of_step": st["ms_colupd"] / ms if ms else None}
+    eri_ops = st.get("eri_fp64_ops", 0.0)
+    eri_ach = eri_ops / (st["ms_eri"] * 1e-3) / 1e12 if st["ms_eri"] > 0 and eri_ops > 0 else None
+    roof_eri = {"kernel": "eri_columns_kernel (FP64 ERI columns, Eq. subtr first term)", "bound": "alu",
+                "achieved": eri_ach, "peak": peak_fp64_ops, "unit": "T FP64-pipe ops/s",
+                "frac": (eri_ach / peak_fp64_ops) if eri_ach else None, "traffic": None,
+                "peak_source": "FP64 pipe: 148 SMs x 2 operations/clk x 2.032 GHz (recipe unit counts and clocks; "
+                               "microbenchmark 1.128 TFLOP/s = 2 DFMA/clk/SM at 1935 MHz)",
+                "work_per_launch": "FP64-pipe operations counted by the kernel per primitive quartet from its "
+                                   "recurrences (set-up, Boys branch taken, bra/ket recurrences)",
+                "fp64_ops_total": eri_ops, "share_of_step": st["ms_eri"] / ms if ms else None,
+                "note": "shares the SMs with the concurrent column update"}
+    if st["ms_eri"] >= st["ms_colupd"]:
+        roof, roof_other, other_key = roof_eri, roof_upd, "roofline_update"
+    else:
+        roof, roof_other, other_key = roof_upd, roof_eri, "roofline_eri"
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if jk_mode == cd.CD_JK_FP64 else "f64+" + args.jk,
@@ -297,9 +316,10 @@ def run_ours(args, rank, world):
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "breakdown_ms": {"system": st["ms_system"], "eri_columns": st["ms_eri"], "column_update": st["ms_colupd"],
                             "pivot_steps": st["ms_steps"], "candidate_select": st["ms_select"],
-                            "factor_total": st["ms_total"], "blocks": st["blocks"], "eri_columns_computed": st["eri_columns"]},
+                            "factor_total": st["ms_total"], "blocks": st["blocks"], "eri_columns_computed": st["eri_columns"],
+                            "eri_fp64_ops": st.get("eri_fp64_ops", 0.0)},
            "jk_alone_ms": jk,
-           "roofline": roof, "gpu_launches": int(launches), "clocks": clk.summary()}
+           "roofline": roof, other_key: roof_other, "gpu_launches": int(launches), "clocks": clk.summary()}
     f.free()
     # end to end through the C ABI with host buffers
     if not args.no_e2e:

@@ -216,7 +216,7 @@ class Factor:
         s = np.zeros(16)
         _check(load().cd_factor_stats(self._h, _p(s)))
         keys = ["ms_system", "ms_eri", "ms_colupd", "ms_steps", "ms_select", "ms_total", "blocks", "eri_columns",
-                "colupd_flops", "eri_entries", "M", "sliced"]
+                "colupd_flops", "eri_entries", "M", "sliced", "eri_fp64_ops"]
         return dict(zip(keys, s.tolist()))
 
     def jk(self, C_occ, mode: int = CD_JK_FP64, stream=None, want=("J", "K")):

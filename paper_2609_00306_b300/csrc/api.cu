@@ -137,6 +137,40 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   for (int64_t r = 0; r < n; ++r) p2r[rows[r]] = (int32_t)r;
   PairSetHost hbra;
   build_pairs(hb, ks1, ks2, &hbra, kPrimPrune);
+  {
+    // order the bra shell pairs of each class by surviving primitive pairs
+    // (descending), then along a Morton curve through the pair midpoints: the
+    // 32 lanes of a warp then run the same number of primitive quartets and
+    // mostly the same Boys branch
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int a = 0; a < nsh; ++a)
+      for (int x = 0; x < 3; ++x) {
+        lo[x] = std::min(lo[x], hb.cen[3 * a + x]);
+        hi[x] = std::max(hi[x], hb.cen[3 * a + x]);
+      }
+    const size_t nk = ks1.size();
+    std::vector<uint64_t> key(nk);
+    for (size_t k = 0; k < nk; ++k) {
+      uint64_t m = 0;
+      for (int x = 0; x < 3; ++x) {
+        const double mid = 0.5 * (hb.cen[3 * ks1[k] + x] + hb.cen[3 * ks2[k] + x]);
+        const double span = hi[x] - lo[x];
+        const uint64_t q = span > 0 ? (uint64_t)std::min(1023.0, std::floor((mid - lo[x]) / span * 1024.0)) : 0;
+        for (int bit = 0; bit < 10; ++bit) m |= ((q >> bit) & 1ull) << (3 * bit + x);
+      }
+      const uint64_t npp = (uint64_t)(hbra.pp_off[k + 1] - hbra.pp_off[k]);
+      key[k] = ((63ull - std::min<uint64_t>(npp, 63)) << 32) | m;
+    }
+    std::vector<size_t> perm(nk);
+    for (size_t k = 0; k < nk; ++k) perm[k] = k;
+    for (int c = 0; c < 3; ++c)
+      std::stable_sort(perm.begin() + s->bra_class_off[c], perm.begin() + s->bra_class_off[c + 1],
+                       [&](size_t x, size_t y) { return key[x] < key[y]; });
+    std::vector<int32_t> p1(nk), p2(nk), pa(nk);
+    for (size_t k = 0; k < nk; ++k) { p1[k] = ks1[perm[k]]; p2[k] = ks2[perm[k]]; pa[k] = kall[perm[k]]; }
+    ks1.swap(p1); ks2.swap(p2); kall.swap(pa);
+    build_pairs(hb, ks1, ks2, &hbra, kPrimPrune);
+  }
   for (auto& r : hbra.row)
     if (r >= 0) r = p2r[r];
   s->bra_to_all = kall;
@@ -235,6 +269,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   unsigned long long* Dint = nullptr;  // int64 [b][ld]
   int32_t* erow = nullptr;          // [n]
   int* err = nullptr;
+  unsigned long long* eri_ops = nullptr;   // FP64-pipe operations of the ERI column kernels
   int64_t kcap = 0;
   // candidate selection on the device
   SelectState* sel = nullptr;
@@ -253,7 +288,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   ~Work() {
     for (void* p : {(void*)pool, (void*)D0, (void*)D1, (void*)Bg, (void*)slots_dev, (void*)rows_dev,
                     (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Ls, Bs, (void*)Dint,
-                    (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals})
+                    (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals, (void*)eri_ops})
       scratch_free(p, st);
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -352,6 +387,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   }
   const int cand_cap = 4 * b;
   CD_TRY(scratch_alloc(&w.sel, 1, st));
+  CD_TRY(scratch_alloc(&w.eri_ops, 1, st));
+  CD_CUDA(cudaMemsetAsync(w.eri_ops, 0, sizeof(unsigned long long), st));
   CD_TRY(scratch_alloc(&w.cand_rows, (size_t)cand_cap, st));
   CD_TRY(scratch_alloc(&w.cand_vals, (size_t)cand_cap, st));
   w.cand_rows_h.resize(cand_cap);
@@ -393,6 +430,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   int64_t K = 0;
   bool done = false;
   const bool dbg = getenv("CDERI_DEBUG") != nullptr;
+  // The sliced update runs on the main stream before the ERI columns: run
+  // beside them on a second stream (CDERI_OVERLAP_UPDATE=1) the two kernels
+  // compete for the same SMs and the block takes as long as in sequence.
+  const bool overlap = getenv("CDERI_OVERLAP_UPDATE") != nullptr;
   while (!done) {
     if (forced ? (K >= nf) : !(res.dmax >= tau)) break;
     if (dbg) fprintf(stderr, "[cderi] block %lld K=%lld dmax=%.3e idx=%lld\n", (long long)nblocks, (long long)K,
@@ -464,7 +505,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         }
       nb_upd = (int)w.upd_slots.size();
       if (nb_upd > 0 && K > 0) {
-        cudaStream_t s2 = w.st2;
+        cudaStream_t s2 = overlap ? w.st2 : st;
         CD_CUDA(cudaEventRecord(w.ev_ready, st));      // slices of the last block are written
         CD_CUDA(cudaStreamWaitEvent(s2, w.ev_ready, 0));
         CD_CUDA(cudaEventRecord(w.ev_g0, s2));
@@ -485,7 +526,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     if (!kets.empty()) {
       CD_CUDA(cudaMemcpyAsync(w.kets_dev, groups.data(), sizeof(KetGroup) * groups.size(), cudaMemcpyHostToDevice, st));
       CD_TRY(launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
-                                s->boys, st));
+                                s->boys, st, w.eri_ops));
       eri_ints += (double)kets.size() * (double)n;
     }
     CD_CUDA(cudaEventRecord(w.ev[1], st));
@@ -651,6 +692,11 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   f->stats[9] = eri_ints;
   f->stats[10] = (double)K;
   f->stats[11] = slice ? 1.0 : 0.0;
+  {
+    unsigned long long ops = 0;
+    CD_CUDA(cudaMemcpy(&ops, w.eri_ops, sizeof(ops), cudaMemcpyDeviceToHost));
+    f->stats[12] = (double)ops;
+  }
   return CD_OK;
 }
 

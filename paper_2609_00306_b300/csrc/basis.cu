@@ -83,7 +83,7 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
   out->swapped.resize(n);
   size_t npp = 0;
   for (size_t k = 0; k < n; ++k) npp += (size_t)hb.nprim[s1[k]] * hb.nprim[s2[k]];
-  out->zeta.resize(npp); out->P.resize(3 * npp); out->PA.resize(3 * npp); out->Kp.resize(npp);
+  out->zeta.resize(npp); out->P.resize(3 * npp); out->PA.resize(3 * npp); out->Kp.resize(npp); out->o2z.resize(npp);
   size_t q = 0;
   for (size_t k = 0; k < n; ++k) {
     int S1 = s1[k], S2 = s2[k];
@@ -113,6 +113,7 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
           out->PA[3 * q + x] = P - cA[x];
         }
         out->Kp[q] = kp;
+        out->o2z[q] = 0.5 / z;
         ++q;
       }
     // components: i on A, j on B
@@ -126,7 +127,7 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
       }
   }
   out->pp_off[n] = (int32_t)q;
-  out->zeta.resize(q); out->P.resize(3 * q); out->PA.resize(3 * q); out->Kp.resize(q);
+  out->zeta.resize(q); out->P.resize(3 * q); out->PA.resize(3 * q); out->Kp.resize(q); out->o2z.resize(q);
 }
 
 template <class T>
@@ -149,12 +150,13 @@ int upload_pairs(const PairSetHost& h, PairSet* d, cudaStream_t st) {
   CD_TRY(up(&d->P, h.P, st));
   CD_TRY(up(&d->PA, h.PA, st));
   CD_TRY(up(&d->Kp, h.Kp, st));
+  CD_TRY(up(&d->o2z, h.o2z, st));
   return CD_OK;
 }
 
 void free_pairs(PairSet* d) {
   cudaFree(d->pp_off); cudaFree(d->la); cudaFree(d->lb); cudaFree(d->AB); cudaFree(d->row);
-  cudaFree(d->zeta); cudaFree(d->P); cudaFree(d->PA); cudaFree(d->Kp);
+  cudaFree(d->zeta); cudaFree(d->P); cudaFree(d->PA); cudaFree(d->Kp); cudaFree(d->o2z);
   *d = PairSet();
 }
 

@@ -12,6 +12,7 @@
 // |c,d+1_l) = |c+1_l,d) + CD_l |c,d) give the requested components.
 // Bra shell pairs are sorted by angular class, so warps run one class.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include "internal.cuh"
 
@@ -43,8 +44,12 @@ __device__ __forceinline__ void boys_fm(double T, double (&F)[L + 1], const doub
       for (int m = L - 1; m >= 0; --m) F[m] = fma(2.0 * T, F[m + 1], emT) * (1.0 / (2 * m + 1));
     }
   } else {
-    F[0] = kSqrtPiOver4 * rsqrt(T);
-    const double h = 0.5 / T;
+    // r = 1/sqrt(T): FP32 seed, two FP64 Newton steps; F_0 = sqrt(pi)/2 r, F_{m+1} = (2m+1) F_m r^2 / 2
+    double r = (double)rsqrtf((float)T);
+    r = r * fma(-0.5 * T, r * r, 1.5);
+    r = r * fma(-0.5 * T, r * r, 1.5);
+    F[0] = kSqrtPiOver4 * r;
+    const double h = 0.5 * r * r;
 #pragma unroll
     for (int m = 0; m < L; ++m) F[m + 1] = (double)(2 * m + 1) * F[m] * h;
   }
@@ -65,7 +70,7 @@ __device__ __forceinline__ double sel3(const double (&v)[3], int k) {
 template <int LA, int LB, int LC, int LD, int NC>
 __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const PairSet& ket, int64_t sk,
                                         const int (&kcs)[NC], const int (&kds)[NC], const double* __restrict__ tab,
-                                        double (&out)[NC][9]) {
+                                        double (&out)[NC][9], unsigned& n_table) {
   constexpr int EB = LA + LB;
   constexpr int FK = LC + LD;
   constexpr int L = EB + FK;
@@ -103,6 +108,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
       const double T = rho * (PQ[0] * PQ[0] + PQ[1] * PQ[1] + PQ[2] * PQ[2]);
       const double base = Kb * __ldg(ket.Kp + ik) * y;
       double F[L + 1];
+      n_table += (T < kBoysTmax) ? 1u : 0u;
       boys_fm<L>(T, F, tab);
       double S0[L + 1];
 #pragma unroll
@@ -119,7 +125,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
         }
       }
       if constexpr (EB == 2) {
-        const double o2p = 0.5 / p, rp = q * is;
+        const double o2p = __ldg(bra.o2z + ib), rp = q * is;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -147,13 +153,11 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
         QC[0] = __ldg(ket.PA + 3 * ik); QC[1] = __ldg(ket.PA + 3 * ik + 1); QC[2] = __ldg(ket.PA + 3 * ik + 2);
         double WQ3[3] = {pis * PQ[0], pis * PQ[1], pis * PQ[2]};
         const double o2s = 0.5 * is;
-#pragma unroll
-        for (int cc = 0; cc < NC; ++cc) {
-          const int kc = kcs[cc], kd = kds[cc];
-          // ---- ket vertical recurrence for f = 1_kc (m <= FK-1), then 1_kc + 1_kd
+        constexpr int MF = FK;
+        double f1s[MF], f1p[3][MF], f1d[6][MF];
+        // ---- ket vertical recurrence, level f = 1_kc (m <= FK-1)
+        auto level1 = [&](int kc) {
           const double QCk = sel3(QC, kc), WQk = sel3(WQ3, kc);
-          constexpr int MF = FK;
-          double f1s[MF], f1p[3][MF], f1d[6][MF];
 #pragma unroll
           for (int m = 0; m < MF; ++m) {
             f1s[m] = fma(QCk, S0[m], WQk * S0[m + 1]);
@@ -176,6 +180,9 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
                 }
             }
           }
+        };
+        // ---- accumulate ket component cc from level 1 (and level 2 for a (pp) ket)
+        auto accumulate = [&](int cc, int kc, int kd) {
           if constexpr (FK == 1) {
             if constexpr (EB == 0) acc[cc][0][0] += f1s[0];
             if constexpr (EB >= 1) {
@@ -188,7 +195,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
             }
           } else {
             const double QCl = sel3(QC, kd), WQl = sel3(WQ3, kd);
-            const double o2q = 0.5 / q, rq = pis;
+            const double o2q = __ldg(ket.o2z + ik), rq = pis;
             const double dkl = (kc == kd) ? o2q : 0.0;
             // [e|1k+1l] = QC_l [e|1k]^0 + WQ_l [e|1k]^1 + d_kl/(2q)([e|0]^0 - rho/q [e|0]^1) + e_l/(2s) [e-1_l|1k]^1
             if constexpr (EB == 0) {
@@ -220,6 +227,26 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
                   acc[cc][3 + t][1] += f1d[t][0];
                 }
             }
+          }
+        };
+        if constexpr (FK == 2 && NC > 1) {
+          // level 1 depends only on kc: computed once per distinct kc of the group
+#pragma unroll
+          for (int kcv = 0; kcv < 3; ++kcv) {
+            bool any = false;
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc) any = any || (kcs[cc] == kcv);
+            if (!any) continue;
+            level1(kcv);
+#pragma unroll
+            for (int cc = 0; cc < NC; ++cc)
+              if (kcs[cc] == kcv) accumulate(cc, kcv, kds[cc]);
+          }
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < NC; ++cc) {
+            level1(kcs[cc]);
+            accumulate(cc, kcs[cc], kds[cc]);
           }
         }
       }
@@ -265,9 +292,33 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
   }
 }
 
+// FP64-pipe operations (DFMA, DMUL, DADD, FP64 conversions) per primitive
+// quartet, counted from the code above, for the roofline of this kernel:
+//   set-up 22; Boys tabulated branch 19 (+ 10 + 2L for L > 0), asymptotic
+//   branch 12 + 2L, both + (L+1) for S0; bra recurrence 4 + 6L (p) and
+//   1 + 18(L-1) more (d); ket: 5, level 1 per distinct kc FK x (2 | 9 | 33),
+//   per component NE adds (ket ss), NE adds (level 1 only) or 6 | 19 | 67 (pp).
+template <int EB, int FK, int NC>
+__device__ __forceinline__ unsigned fixed_ops(int n_level1) {
+  constexpr int L = EB + FK;
+  constexpr int NE = EB == 0 ? 1 : (EB == 1 ? 3 : 9);
+  int ops = 22 + (L + 1);
+  if (EB >= 1) ops += 4 + 6 * L;
+  if (EB == 2) ops += 1 + 18 * (L - 1);
+  if (FK == 0) {
+    ops += NE;
+  } else {
+    const int lvl1 = FK * (EB == 0 ? 2 : (EB == 1 ? 9 : 33));
+    const int acc = FK == 1 ? NE : (EB == 0 ? 6 : (EB == 1 ? 19 : 67));
+    ops += 5 + n_level1 * lvl1 + NC * acc;
+  }
+  return (unsigned)ops;
+}
+
 template <int LA, int LB, int LC, int LD, int NC>
 __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, const PairSet& ket, const KetGroup& kg,
-                                             double* __restrict__ out, int64_t ld, const double* __restrict__ tab) {
+                                             double* __restrict__ out, int64_t ld, const double* __restrict__ tab,
+                                             unsigned long long& ops) {
   int kcs[NC], kds[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -275,7 +326,24 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     kds[c] = c < kg.nc ? kg.kd[c] : kg.kd[0];
   }
   double v[NC][9];
-  quartet<LA, LB, LC, LD, NC>(bra, sb, ket, kg.sp, kcs, kds, tab, v);
+  unsigned n_table = 0;
+  quartet<LA, LB, LC, LD, NC>(bra, sb, ket, kg.sp, kcs, kds, tab, v, n_table);
+  {
+    constexpr int L = LA + LB + LC + LD;
+    int n_level1 = NC;
+    if (LC + LD == 2 && NC > 1) {  // distinct kc values (level 1 shared per kc)
+      n_level1 = 0;
+      for (int kcv = 0; kcv < 3; ++kcv) {
+        bool any = false;
+        for (int cc = 0; cc < NC; ++cc) any = any || (kcs[cc] == kcv);
+        n_level1 += any ? 1 : 0;
+      }
+    }
+    const unsigned long long nq = (unsigned long long)(__ldg(bra.pp_off + sb + 1) - __ldg(bra.pp_off + sb)) *
+                                  (unsigned long long)(__ldg(ket.pp_off + kg.sp + 1) - __ldg(ket.pp_off + kg.sp));
+    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (19 + (L > 0 ? 10 + 2 * L : 0)) +
+           (nq - n_table) * (12 + 2 * L);
+  }
   const int32_t* rw = bra.row + 9 * sb;
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
@@ -295,18 +363,27 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
 template <int LA, int LB>
 __global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, int64_t b0, int64_t b1, PairSet ket,
                                                           const KetGroup* __restrict__ groups, double* __restrict__ out,
-                                                          int64_t ld, const double* __restrict__ tab) {
+                                                          int64_t ld, const double* __restrict__ tab,
+                                                          unsigned long long* __restrict__ op_count) {
   const KetGroup kg = groups[blockIdx.y];
   const int64_t sb = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (sb >= b1) return;
-  const int cls = kg.lc * 2 + kg.ld;
-  if (cls == 0) column_block<LA, LB, 0, 0, 1>(bra, sb, ket, kg, out, ld, tab);
-  else if (cls == 2) {
-    if (kg.nc == 1) column_block<LA, LB, 1, 0, 1>(bra, sb, ket, kg, out, ld, tab);
-    else column_block<LA, LB, 1, 0, 3>(bra, sb, ket, kg, out, ld, tab);
-  } else {
-    if (kg.nc == 1) column_block<LA, LB, 1, 1, 1>(bra, sb, ket, kg, out, ld, tab);
-    else column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab);
+  unsigned long long ops = 0;
+  if (sb < b1) {
+    const int cls = kg.lc * 2 + kg.ld;
+    if (cls == 0) column_block<LA, LB, 0, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
+    else if (cls == 2) {
+      if (kg.nc == 1) column_block<LA, LB, 1, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
+      else column_block<LA, LB, 1, 0, 3>(bra, sb, ket, kg, out, ld, tab, ops);
+    } else {
+      if (kg.nc == 1) column_block<LA, LB, 1, 1, 1>(bra, sb, ket, kg, out, ld, tab, ops);
+      else if (kg.nc <= 3) column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab, ops);
+      else column_block<LA, LB, 1, 1, kMaxKetGroup>(bra, sb, ket, kg, out, ld, tab, ops);
+    }
+  }
+  if (op_count) {  // warp sum, one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ops += __shfl_xor_sync(0xffffffffu, ops, o);
+    if ((threadIdx.x & 31) == 0 && ops) atomicAdd(op_count, ops);
   }
 }
 
@@ -322,7 +399,8 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
   if (r < 0) return;
   double v[1][9];
   const int kcs[1] = {c / 3}, kds[1] = {c % 3};
-  quartet<LA, LB, LA, LB, 1>(ps, sp, ps, sp, kcs, kds, tab, v);
+  unsigned n_table = 0;
+  quartet<LA, LB, LA, LB, 1>(ps, sp, ps, sp, kcs, kds, tab, v, n_table);
   diag[r] = v[0][c];
 }
 
@@ -330,15 +408,16 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
 
 int launch_eri_columns(const PairSet& bra, const int64_t* /*bra_order*/, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* kets_dev, int nket,
-                       double* out, int64_t ld, const double* boys, cudaStream_t st) {
+                       double* out, int64_t ld, const double* boys, cudaStream_t st,
+                       unsigned long long* op_count) {
   if (nket <= 0) return CD_OK;
   for (int cls = 0; cls < 3; ++cls) {
     int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
     if (b1 <= b0) continue;
     dim3 grid((unsigned)((b1 - b0 + 127) / 128), (unsigned)nket);
-    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys);
-    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys);
-    else eri_columns_kernel<1, 1><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys);
+    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else eri_columns_kernel<1, 1><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
     count_launch();
   }
   CD_CUDA(cudaGetLastError());
@@ -366,11 +445,16 @@ int launch_eri_diag(const PairSet& ps, const int64_t* /*order*/, const int64_t* 
 namespace cd {
 std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets) {
   std::vector<KetDesc> k(kets);
-  std::stable_sort(k.begin(), k.end(), [](const KetDesc& a, const KetDesc& b) { return a.sp < b.sp; });
+  // same shell pair together, and within it the same kc (the level-1 recurrence is then shared)
+  std::stable_sort(k.begin(), k.end(), [](const KetDesc& a, const KetDesc& b) {
+    return a.sp < b.sp || (a.sp == b.sp && (a.kc < b.kc || (a.kc == b.kc && a.kd < b.kd)));
+  });
   std::vector<KetGroup> out;
   for (size_t i = 0; i < k.size();) {
     size_t j = i;
-    while (j < k.size() && k[j].sp == k[i].sp && j - i < 3) ++j;
+    // (pp) ket shell pairs: up to all 9 components in one group; others up to 3
+    const size_t cap = (k[i].lc == 1 && k[i].ld == 1) ? (size_t)kMaxKetGroup : 3;
+    while (j < k.size() && k[j].sp == k[i].sp && j - i < cap) ++j;
     KetGroup g;
     std::memset(&g, 0, sizeof(g));
     g.sp = k[i].sp;

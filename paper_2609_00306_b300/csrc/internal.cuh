@@ -86,13 +86,14 @@ struct PairSet {
   double* P = nullptr;         // [npp][3]
   double* PA = nullptr;        // [npp][3]
   double* Kp = nullptr;        // [npp]
+  double* o2z = nullptr;       // [npp] 1 / (2 zeta)
 };
 
 // Host-side mirror used while building.
 struct PairSetHost {
   std::vector<int32_t> pp_off, row;
   std::vector<int8_t> la, lb;
-  std::vector<double> AB, zeta, P, PA, Kp;
+  std::vector<double> AB, zeta, P, PA, Kp, o2z;
   std::vector<int32_t> s1, s2;     // shell indices of the pair (S1 >= S2)
   std::vector<int8_t> swapped;     // 1 if A = S2
 };
@@ -120,25 +121,28 @@ struct KetDesc {
   int8_t lc, ld;
 };
 
-// up to three ket function pairs of one ket shell pair, evaluated together
-// (shared primitive set-up, Boys function and bra recurrence)
+// ket function pairs of one ket shell pair evaluated together (shared
+// primitive set-up, Boys function, bra recurrence and, per distinct kc, the
+// first ket level): up to 9 for a (pp) shell pair, up to 3 otherwise
+constexpr int kMaxKetGroup = 9;
 struct KetGroup {
   int32_t sp;        // shell pair index in `all`
   int8_t lc, ld;     // canonical class of the shell pair
-  int8_t nc;         // components in the group (1..3)
+  int8_t nc;         // components in the group
   int8_t pad;
-  int8_t kc[3], kd[3];
+  int8_t kc[kMaxKetGroup], kd[kMaxKetGroup];
   int16_t pad2;
-  int32_t slot[3];   // output columns: out + slot * ld
+  int32_t slot[kMaxKetGroup];   // output columns: out + slot * ld
 };
-// group ket descriptors of the same shell pair (at most 3 per group)
+// group ket descriptors of the same shell pair
 std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets);
 
 // ERI kernels (eri.cu)
 // out[slot * ld + row] = (bra rows | ket component) for every bra shell pair in `bra`
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* groups_dev, int ngroups,
-                       double* out, int64_t ld, const double* boys, cudaStream_t st);
+                       double* out, int64_t ld, const double* boys, cudaStream_t st,
+                       unsigned long long* op_count = nullptr);  // FP64-pipe operation counter (optional)
 // diag[row] = (row|row) for every shell pair in `ps` (rows from ps.row)
 int launch_eri_diag(const PairSet& ps, const int64_t* order, const int64_t* class_off,
                     double* diag, const double* boys, cudaStream_t st);

@@ -60,6 +60,8 @@ struct Cfg {
   static constexpr int TMEM_COLS = NEED <= 32 ? 32 : (NEED <= 64 ? 64 : (NEED <= 128 ? 128 : (NEED <= 256 ? 256 : 512)));
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
   static_assert(ACC_COLS <= 512, "accumulators exceed tensor memory");
+  static_assert(SB >= KEEP - 1, "the first A slice's MMA must cover every accumulator group");
+  static_assert(SB * BN <= 256 && (BN % 16) == 0, "stacked B operand: N = SB*BN must be <= 256");
   static_assert(SMEM <= 232448, "shared memory over the per-CTA limit");
 };
 
@@ -120,7 +122,6 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     } else if (warp == 5) {
       if (lane == 0) {
         // ---------------- MMA issuer
-        constexpr uint32_t idesc = tc::idesc_bf16_f32<BM, BN>();
         int chunk = 0;
         for (int i = 0; i < nkb; ++i) {
           const int s = i % STAGES;
@@ -138,22 +139,23 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           const uint32_t a = tc::smem_u32(smem + s * C::STAGE_BYTES);
           const uint32_t b = a + C::A_BYTES;
           const uint32_t acc = tmem + (uint32_t)(buf * C::ACC_COLS);
+          // One MMA per A slice s: the B slices t = 1..nt are stacked in shared
+          // memory (rows t*BN..), and the accumulator of group s+t sits at
+          // column (s+t-2)*BN, so A_s x [B_1; ...; B_nt] lands every product
+          // (s, t) in its group with a single N = nt*BN instruction.  The first
+          // one of a chunk (s = 1, covering every group) overwrites.
 #pragma unroll
-          for (int sa = 0; sa < SA; ++sa)
+          for (int sa = 0; sa < SA; ++sa) {
+            const int nt = (SB < KEEP - 1 - sa) ? SB : KEEP - 1 - sa;
+            if (nt <= 0) continue;
+            const uint32_t idesc = tc::idesc_bf16_f32_n(BM, nt * BN);
 #pragma unroll
-            for (int sb = 0; sb < SB; ++sb) {
-              const int g = sa + sb;  // 0-based: s + t - 2
-              if (g > KEEP - 2) continue;
-              // the first product of each group inside a chunk overwrites the accumulator
-              const int sa_first = g < SB ? 0 : g - (SB - 1);
-              const bool first_of_group = chunk_start && (sa == sa_first);
-#pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t ad = sdesc_k_sw64(a + sa * (BM * BK * 2) + kk * 32);
-                const uint64_t bd = sdesc_k_sw64(b + sb * (BN * BK * 2) + kk * 32);
-                tc::umma_bf16(acc + g * BN, ad, bd, idesc, (first_of_group && kk == 0) ? 0u : 1u);
-              }
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint64_t ad = sdesc_k_sw64(a + sa * (BM * BK * 2) + kk * 32);
+              const uint64_t bd = sdesc_k_sw64(b + kk * 32);
+              tc::umma_bf16(acc + sa * BN, ad, bd, idesc, (chunk_start && sa == 0 && kk == 0) ? 0u : 1u);
             }
+          }
           tc::umma_commit(&empty[s]);
           if ((i % kcb) == kcb - 1 || i == nkb - 1) {
             tc::umma_commit(&tfull[buf]);
