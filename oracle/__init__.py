@@ -14,6 +14,12 @@ What each function follows (the paper, arXiv 2609.00306, Sec. 2 and 4.1):
   J_{mu nu} = sum_{sigma rho} (mu nu|sigma rho) D_{sigma rho},
   K_{mu nu} = sum_{sigma rho} (mu sigma|nu rho) D_{sigma rho} = sum_P (L^P D L^P)_{mu nu}.
 * ``jk_exact``  -- the same J and K from the exact four-index ERI tensor.
+* ``Oracle.cd_span`` -- partially pivoted selection with a span factor (Sec. 3
+  and its Table of sets; Koch et al. 2003): qualified diagonals >= span * max D,
+  micro iterations inside the qualified set, optional discarding of rows below
+  tau (first step of the two-step scheme).  ``Oracle.cd_from_basis`` -- second
+  step: Cholesky factor of the basis metric and the triangular solve of
+  Eq. (CVsLT).  Both in C (``or_cd_span``, ``or_cd_from_basis``).
 
 Readings taken where the paper is silent (each one is listed with the design
 notes): packed mu >= nu pair indices, strict ``< tau`` stop, ties to the lowest
@@ -71,6 +77,10 @@ def _load():
         lib.or_screen.argtypes = [P, P, D, P]
         lib.or_cd.restype = I
         lib.or_cd.argtypes = [P, P, I64, D, P, I, I, P, P, P, P, P]
+        lib.or_cd_span.restype = I
+        lib.or_cd_span.argtypes = [P, P, I64, D, D, I, I, I, P, P, P, P, P]
+        lib.or_cd_from_basis.restype = I
+        lib.or_cd_from_basis.argtypes = [P, P, I64, P, I, P]
         _lib = lib
     return _lib
 
@@ -129,6 +139,19 @@ class CDResult:
     @property
     def piv_packed(self) -> np.ndarray:
         return self.rows[self.piv]
+
+
+@dataclasses.dataclass
+class SpanResult:
+    rows: np.ndarray         # [npairs] packed pair index of each vector row
+    piv: np.ndarray          # [M] chosen basis (pivot rows), in order
+    L: np.ndarray            # [M, npairs] vectors (dropped rows left at 0 when rows were reduced)
+    D: np.ndarray            # [npairs] residual diagonal (live rows)
+    macro_start: np.ndarray  # [n_macro] vector count at the start of each macro iteration
+
+    @property
+    def M(self) -> int:
+        return int(self.piv.shape[0])
 
 
 class Oracle:
@@ -232,6 +255,48 @@ class Oracle:
             if M < 0:
                 raise RuntimeError(f"oracle CD failed with status {M}")
             return CDResult(rows, piv[:M].copy(), L[:M].copy(), D, gap[:M].copy(), pivD[:M].copy())
+
+    # -- span-factor selection and the two-step scheme --------------------
+    def cd_span(self, rows, tau: float, span: float, qmax: int = 64, reduce: bool = False,
+                mcap: Optional[int] = None) -> SpanResult:
+        """Partially pivoted decomposition with span factor ``span`` (C ``or_cd_span``).
+
+        ``reduce=False``: Koch's one-step algorithm, ``L`` is the factor.
+        ``reduce=True``: first step of the two-step scheme (rows whose residual
+        diagonal drops below tau are discarded); only ``piv`` is meaningful and
+        the vectors come from :meth:`cd_from_basis`.
+        """
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        n = rows.shape[0]
+        mcap = mcap or min(n, max(64, 4 * self.nbf))
+        while True:
+            piv = np.zeros(max(mcap, 1), dtype=np.int64)
+            L = np.zeros((max(mcap, 1), n))
+            D = np.zeros(n)
+            ms = np.zeros(max(mcap, 1) + 1, dtype=np.int32)
+            nm = ctypes.c_int(0)
+            M = self._lib.or_cd_span(self._h, _ptr(rows), n, float(tau), float(span), int(qmax), int(bool(reduce)),
+                                     mcap, _ptr(piv), _ptr(L), _ptr(D), _ptr(ms), ctypes.byref(nm))
+            if M == -1 and mcap < n:
+                mcap = min(n, 2 * mcap)
+                continue
+            if M == -2:
+                raise ArithmeticError("ERI matrix not positive semidefinite within tolerance")
+            if M < 0:
+                raise RuntimeError(f"oracle span CD failed with status {M}")
+            return SpanResult(rows, piv[:M].copy(), L[:M].copy(), D, ms[:nm.value].copy())
+
+    def cd_from_basis(self, rows, piv) -> np.ndarray:
+        """Second step of the two-step scheme: vectors [M, npairs] from the metric
+        Cholesky factor of the basis ``piv`` and a triangular solve (``or_cd_from_basis``)."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        piv = np.ascontiguousarray(piv, dtype=np.int64)
+        M = int(piv.shape[0])
+        L = np.zeros((max(M, 1), rows.shape[0]))
+        st = self._lib.or_cd_from_basis(self._h, _ptr(rows), rows.shape[0], _ptr(piv), M, _ptr(L))
+        if st == -2:
+            raise ArithmeticError("metric of the Cholesky basis is not positive definite")
+        return L[:M].copy()
 
 
 def density(C_occ: np.ndarray) -> np.ndarray:

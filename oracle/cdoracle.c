@@ -21,6 +21,10 @@
  *     Eq. (diag), stop when max D < tau), with a forced-pivot mode.
  *   - The exact ERI matrix over a list of pair indices (for J/K from exact
  *     integrals and for the dense checks in the tests).
+ *   - Span-factor (partially pivoted) basis selection, with or without the
+ *     discarding of rows below tau (Koch's one-step algorithm; the first step
+ *     of the two-step scheme of Sec. 3), and the second step: the metric's
+ *     Cholesky factor and the triangular solve of Eq. (CVsLT).
  *
  * Pair index convention: functions are numbered shell by shell (s; then p as
  * x, y, z); a composite pair (mu, nu) with mu >= nu has packed index
@@ -421,4 +425,183 @@ int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
     }
     free(ri); free(rj);
     return status < 0 ? status : K;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Span-factor (partially pivoted) selection of the Cholesky basis: Koch's    */
+/* partially pivoted decomposition (Koch, Sanchez de Meras, Pedersen, J.      */
+/* Chem. Phys. 118, 9481 (2003), cited in Sec. 3) and the first step of the   */
+/* two-step scheme of Sec. 3 (sets of Table "two-step": B chosen basis, D     */
+/* diagonals >= tau, Q qualified diagonals, C columns already used in the     */
+/* current micro iteration).                                                  */
+/*                                                                           */
+/* One macro iteration:                                                       */
+/*     Dmax = max_{r in D} D_r;  stop when Dmax < tau                         */
+/*     thr  = max(span * Dmax, tau)                                           */
+/*     Q    = rows r in D with D_r >= thr, largest first (ties: lowest row),  */
+/*            at most qmax of them                                            */
+/*     col_q = (r|q) - sum_{J<K} L^J_r L^J_q   for q in Q, r in D  Eq. (subtr)*/
+/*     micro iterations, C = {}:                                              */
+/*         q = argmax_{Q \ C} D_q (ties: lowest row); stop if D_q < thr       */
+/*         L^K_r = col_q,r / sqrt(D_q)                  Eq. (subtr)           */
+/*         col_q',r -= L^K_r L^K_q'   for q' in Q \ C                          */
+/*         D_r -= (L^K_r)^2                              Eq. (diag)            */
+/*         B += q, C += q, K += 1                                             */
+/*     reduce = 1: D = {r in D : D_r >= tau}  (rows below tau are dropped for */
+/*                 good: D_r never increases, Sec. 3)                         */
+/* With reduce = 0 the rows are never dropped and L^K covers every row: that  */
+/* is Koch's one-step algorithm and L is the final factor.  With reduce = 1   */
+/* only the basis B (the pivots) is the result; the vectors then come from    */
+/* or_cd_from_basis (second step).  The paper keeps the integrals of unused   */
+/* qualified columns between macro iterations; this oracle recomputes them,   */
+/* which changes the cost, not the result.  With span = 1 every macro         */
+/* iteration takes exactly the argmax, i.e. full pivoting (or_cd).            */
+/*                                                                           */
+/* L is row-major [mcap][npairs]; entries of dropped rows are left at 0.      */
+/* macro_start[i] = K at the start of macro iteration i (optional).           */
+/* Returns M >= 0, or -1 if M would exceed mcap, -2 if a pivot diagonal is    */
+/* not positive or a residual below -1e-10 max D^1 (matrix not PSD).          */
+/* ------------------------------------------------------------------------- */
+int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double span, int qmax, int reduce,
+               int mcap, int64_t* piv_out, double* L, double* D, int* macro_start, int* n_macro)
+{
+    int* ri = (int*)malloc(sizeof(int) * npairs);
+    int* rj = (int*)malloc(sizeof(int) * npairs);
+    char* live = (char*)malloc(npairs);
+    for (int64_t r = 0; r < npairs; ++r) unpack_pair(rows[r], &ri[r], &rj[r]);
+    #pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t r = 0; r < npairs; ++r) D[r] = or_eri(h, ri[r], rj[r], ri[r], rj[r]);
+    double d1max = 0.0;
+    for (int64_t r = 0; r < npairs; ++r) if (D[r] > d1max) d1max = D[r];
+    for (int64_t r = 0; r < npairs; ++r) live[r] = reduce ? (D[r] >= tau) : 1;
+    if (qmax < 1) qmax = 1;
+    int64_t* Q = (int64_t*)malloc(sizeof(int64_t) * qmax);
+    char* used = (char*)malloc(qmax);
+    double* col = (double*)malloc(sizeof(double) * (size_t)qmax * npairs);
+
+    int K = 0, status = 0, nm = 0;
+    for (;;) {
+        double dmax = -INFINITY;
+        for (int64_t r = 0; r < npairs; ++r)
+            if (live[r] && D[r] > dmax) dmax = D[r];
+        if (!(dmax >= tau)) break;
+        double thr = span * dmax;
+        if (thr < tau) thr = tau;
+        /* Q: the qmax largest D_r >= thr, by repeated selection */
+        int nq = 0;
+        while (nq < qmax) {
+            int64_t best = -1;
+            for (int64_t r = 0; r < npairs; ++r) {
+                if (!live[r] || !(D[r] >= thr)) continue;
+                int taken = 0;
+                for (int i = 0; i < nq; ++i) if (Q[i] == r) { taken = 1; break; }
+                if (taken) continue;
+                if (best < 0 || D[r] > D[best]) best = r;
+            }
+            if (best < 0) break;
+            Q[nq++] = best;
+        }
+        if (macro_start) macro_start[nm] = K;
+        ++nm;
+        /* columns of Q over the live rows, minus all previous vectors */
+        for (int i = 0; i < nq; ++i) {
+            int64_t q = Q[i];
+            double* c = col + (size_t)i * npairs;
+            int k = ri[q], l = rj[q];
+            #pragma omp parallel for schedule(dynamic, 64)
+            for (int64_t r = 0; r < npairs; ++r) {
+                if (!live[r]) { c[r] = 0.0; continue; }
+                double v = or_eri(h, ri[r], rj[r], k, l);
+                for (int J = 0; J < K; ++J)
+                    v -= L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + q];
+                c[r] = v;
+            }
+            used[i] = 0;
+        }
+        /* micro iterations */
+        for (;;) {
+            int bi = -1;
+            for (int i = 0; i < nq; ++i) {
+                if (used[i]) continue;
+                if (bi < 0 || D[Q[i]] > D[Q[bi]] || (D[Q[i]] == D[Q[bi]] && Q[i] < Q[bi])) bi = i;
+            }
+            if (bi < 0 || !(D[Q[bi]] >= thr)) break;
+            int64_t q = Q[bi];
+            if (K >= mcap) { status = -1; break; }
+            if (!(D[q] > 0.0)) { status = -2; break; }
+            double sq = sqrt(D[q]);
+            double* LK = L + (int64_t)K * npairs;
+            const double* cq = col + (size_t)bi * npairs;
+            for (int64_t r = 0; r < npairs; ++r) LK[r] = live[r] ? cq[r] / sq : 0.0;
+            used[bi] = 1;
+            for (int i = 0; i < nq; ++i) {
+                if (used[i]) continue;
+                double* c = col + (size_t)i * npairs;
+                double f = LK[Q[i]];
+                for (int64_t r = 0; r < npairs; ++r) if (live[r]) c[r] -= LK[r] * f;
+            }
+            int bad = 0;
+            for (int64_t r = 0; r < npairs; ++r) {
+                if (!live[r]) continue;
+                D[r] -= LK[r] * LK[r];
+                if (D[r] < -1e-10 * d1max) bad = 1;
+            }
+            piv_out[K] = q;
+            ++K;
+            if (bad) { status = -2; break; }
+        }
+        if (status < 0) break;
+        if (reduce)
+            for (int64_t r = 0; r < npairs; ++r) if (live[r] && !(D[r] >= tau)) live[r] = 0;
+    }
+    if (n_macro) *n_macro = nm;
+    free(ri); free(rj); free(live); free(Q); free(used); free(col);
+    return status < 0 ? status : K;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Second step of the two-step scheme (Sec. 3, Eqs. (DF), (CVsLT)): given the */
+/* Cholesky basis B = piv[0..M), the metric S_{JK} = (B_J|B_K) is factored as */
+/* S = M M^T (plain Cholesky, no pivoting) and the vectors solve              */
+/*     L^K_r = sum_P (r|B_P) (M^{-T})_{PK},                                   */
+/* i.e. row by row, by forward substitution with the lower triangle of M:     */
+/*     L^K_r = ((r|B_K) - sum_{J<K} L^J_r M_{KJ}) / M_{KK}.                    */
+/* L is row-major [M][npairs].  Returns 0, or -2 if the metric is not         */
+/* positive definite.                                                          */
+/* ------------------------------------------------------------------------- */
+int or_cd_from_basis(void* h, const int64_t* rows, int64_t npairs, const int64_t* piv, int M, double* L)
+{
+    int* ri = (int*)malloc(sizeof(int) * npairs);
+    int* rj = (int*)malloc(sizeof(int) * npairs);
+    for (int64_t r = 0; r < npairs; ++r) unpack_pair(rows[r], &ri[r], &rj[r]);
+    double* S = (double*)calloc((size_t)M * M, sizeof(double));
+    for (int J = 0; J < M; ++J)
+        for (int K = 0; K <= J; ++K)
+            S[(size_t)J * M + K] = or_eri(h, ri[piv[J]], rj[piv[J]], ri[piv[K]], rj[piv[K]]);
+    /* S = M M^T, lower triangle in place (Cholesky-Banachiewicz) */
+    int status = 0;
+    for (int J = 0; J < M && status == 0; ++J) {
+        for (int K = 0; K <= J; ++K) {
+            double s = S[(size_t)J * M + K];
+            for (int P = 0; P < K; ++P) s -= S[(size_t)J * M + P] * S[(size_t)K * M + P];
+            if (K == J) {
+                if (!(s > 0.0)) { status = -2; break; }
+                S[(size_t)J * M + J] = sqrt(s);
+            } else {
+                S[(size_t)J * M + K] = s / S[(size_t)K * M + K];
+            }
+        }
+    }
+    if (status == 0) {
+        #pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t r = 0; r < npairs; ++r) {
+            for (int K = 0; K < M; ++K) {
+                double v = or_eri(h, ri[r], rj[r], ri[piv[K]], rj[piv[K]]);
+                for (int J = 0; J < K; ++J) v -= L[(int64_t)J * npairs + r] * S[(size_t)K * M + J];
+                L[(int64_t)K * npairs + r] = v / S[(size_t)K * M + K];
+            }
+        }
+    }
+    free(S); free(ri); free(rj);
+    return status;
 }
