@@ -50,6 +50,11 @@ def _args():
                          "the tensor cores; *_fp32vec = vectors rounded to FP32 first)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--algorithm", choices=["full", "span", "twostep"], default="full",
+                    help="pivot policy of the timed step (full pivoting by default)")
+    ap.add_argument("--span", type=float, default=0.01, help="span factor of the span / two-step policies")
+    ap.add_argument("--no-algorithms", action="store_true",
+                    help="skip the one-off timings of the other pivot policies after the step")
     ap.add_argument("--no-jk-alone", action="store_true", help="skip the separate J/K timings (FP64 K is slow)")
     ap.add_argument("--jk-alone-modes", default="all",
                     help="comma list of J/K modes timed separately after the step (default: all)")
@@ -193,8 +198,11 @@ def run_ours(args, rank, world):
     K_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (126 MB)
 
+    algs = {"full": cd.CD_ALG_FULL, "span": cd.CD_ALG_SPAN, "twostep": cd.CD_ALG_TWOSTEP}
+
     def step():
-        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec)
+        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec, algorithm=algs[args.algorithm],
+                             span=args.span)
         f.jk_device(C_dev, J_dev, K_dev, mode=jk_mode)
         return f
 
@@ -264,6 +272,25 @@ def run_ours(args, rank, world):
             }
             if jk.get("fp64_ms") and jk.get(mx + "_ms"):
                 jk[mx + "_speedup_over_fp64"] = jk["fp64_ms"] / jk[mx + "_ms"]
+    # the other pivot policies, one factorisation each (same system, same tau)
+    other_algs = {}
+    for name, alg in algs.items():
+        if args.no_algorithms or name == args.algorithm:
+            continue
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec, algorithm=alg, span=args.span)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        gs = g.stats()
+        other_algs[name] = {"factor_ms": ev0.elapsed_time(ev1), "M": g.M, "max_resid": g.max_resid,
+                            "span": args.span if alg != cd.CD_ALG_FULL else None,
+                            "eri_columns_computed": gs["eri_columns"], "blocks": gs["blocks"],
+                            "step1_ms": gs["step1_ms"] if alg == cd.CD_ALG_TWOSTEP else None,
+                            "step1_blocks": gs["step1_blocks"] if alg == cd.CD_ALG_TWOSTEP else None,
+                            "step1_eri_columns": gs["step1_eri_columns"] if alg == cd.CD_ALG_TWOSTEP else None}
+        g.free()
+        del g
     # rooflines: the ERI column kernel (FP64 pipe) and the column update (tensor
     # cores, or FP64 pipe in the DFMA mode); the one with the larger share of the
     # step is reported as "roofline", the other as "roofline_update"/"roofline_eri"
@@ -280,8 +307,7 @@ def run_ours(args, rank, world):
                     "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": (ach / pk) if ach else None,
                     "traffic": None, "peak_source": "MEASURED_PEAKS.json bf16 (sustained) - of measured",
                     "fp64_equivalent_tflops": upd_fp64eq, "fp64_pipe_peak_tflops": peak_fp64,
-                    "share_of_step": st["ms_colupd"] / ms if ms else None,
-                    "note": "runs concurrently with the ERI columns on a second stream"}
+                    "share_of_step": st["ms_colupd"] / ms if ms else None}
     else:
         roof_upd = {"kernel": "colupd_kernel (FP64 column update, Eq. subtr)", "bound": "alu",
                     "achieved": upd_fp64eq, "peak": peak_fp64, "unit": "TFLOP/s",
@@ -298,8 +324,7 @@ def run_ours(args, rank, world):
                                "microbenchmark 1.128 TFLOP/s = 2 DFMA/clk/SM at 1935 MHz)",
                 "work_per_launch": "FP64-pipe operations counted by the kernel per primitive quartet from its "
                                    "recurrences (set-up, Boys branch taken, bra/ket recurrences)",
-                "fp64_ops_total": eri_ops, "share_of_step": st["ms_eri"] / ms if ms else None,
-                "note": "shares the SMs with the concurrent column update"}
+                "fp64_ops_total": eri_ops, "share_of_step": st["ms_eri"] / ms if ms else None}
     if st["ms_eri"] >= st["ms_colupd"]:
         roof, roof_other, other_key = roof_eri, roof_upd, "roofline_update"
     else:
@@ -311,6 +336,7 @@ def run_ours(args, rank, world):
            "config": {"workload": f"{args.workload}: N={N} s+p, {s.basis.n_shells} shells, tau={s.tau:g}, "
                                   f"Schwarz {s.schwarz:g}, n_occ={O}",
                       "n_basis": N, "rows": f.n_rows, "M": M, "max_resid": resid, "jk_mode": args.jk,
+                      "algorithm": args.algorithm + ("" if args.algorithm == "full" else f" (span {args.span:g})"),
                       "update": "sliced tensor-core (7 x 8-bit slices)" if sliced else "FP64 DFMA",
                       "l2": "inputs (vectors, 10s of GB) larger than L2; 256 MB flush between steps",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -318,14 +344,15 @@ def run_ours(args, rank, world):
                             "pivot_steps": st["ms_steps"], "candidate_select": st["ms_select"],
                             "factor_total": st["ms_total"], "blocks": st["blocks"], "eri_columns_computed": st["eri_columns"],
                             "eri_fp64_ops": st.get("eri_fp64_ops", 0.0)},
-           "jk_alone_ms": jk,
+           "jk_alone_ms": jk, "pivot_policies": other_algs,
            "roofline": roof, other_key: roof_other, "gpu_launches": int(launches), "clocks": clk.summary()}
     f.free()
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec)
+        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec, algorithm=algs[args.algorithm],
+                             span=args.span)
         J, K = f.jk(s.C_occ, mode=jk_mode)
         torch.cuda.synchronize()
         e2e = time.perf_counter() - t0

@@ -80,8 +80,33 @@ typedef struct {
   const int64_t* forced_pivots; /* test hook: host list of pivot rows to follow (NULL = argmax) */
   int64_t n_forced;
   int32_t update;       /* column update of Eq. (subtr): CD_UPDATE_SLICE (default) or CD_UPDATE_FP64 */
-  int32_t reserved;
+  int32_t algorithm;    /* pivot policy: CD_ALG_FULL (default), CD_ALG_SPAN or CD_ALG_TWOSTEP (below) */
+  double  span;         /* span factor eta in (0, 1] of CD_ALG_SPAN / CD_ALG_TWOSTEP (0 = 0.01) */
 } cd_opts_t;
+
+/* Pivot policies.
+ *  CD_ALG_FULL    fully pivoted recursion of Sec. 2: every step takes the global
+ *                 argmax of the residual diagonal (the block of b columns is
+ *                 speculative and only decides which integrals are computed).
+ *  CD_ALG_SPAN    partially pivoted decomposition with a span factor (Sec. 3,
+ *                 Koch et al. 2003): each macro iteration takes the qualified
+ *                 set Q = the b largest residual diagonals >= max(eta * Dmax,
+ *                 tau), computes their columns, and then takes vectors inside Q
+ *                 (largest residual first, ties to the lowest row) while the
+ *                 largest one left is >= that threshold.  Vectors over all rows.
+ *  CD_ALG_TWOSTEP the two-step scheme of Sec. 3: step 1 is CD_ALG_SPAN on the
+ *                 rows whose residual diagonal is >= tau only (rows that fall
+ *                 below tau are dropped for good, the kept rows compacted), and
+ *                 gives the Cholesky basis B; step 2 computes the vectors of B
+ *                 over all rows, L = (.|B) M^-T with S = M M^T the metric on B
+ *                 (Eq. (CVsLT)), by the blocked recursion over B in order --
+ *                 the same numbers as a forward substitution with the metric's
+ *                 Cholesky factor.  stats[13] = step-1 ms, stats[14] = step-1
+ *                 macro iterations, stats[15] = step-1 ERI columns.
+ * With eta = 1 (or b = 1) both span policies reduce to full pivoting. */
+#define CD_ALG_FULL     0
+#define CD_ALG_SPAN     1
+#define CD_ALG_TWOSTEP  2
 
 #define CD_UPDATE_SLICE  0  /* exact-slice BF16 tensor-core GEMM, 7 slices (56-bit fixed point per row) */
 #define CD_UPDATE_FP64   1  /* register-tiled FP64 DFMA GEMM */

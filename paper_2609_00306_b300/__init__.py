@@ -3,10 +3,10 @@
 The compute path is the CUDA library ``libcderi.so`` (C ABI in
 ``include/cderi.h``); this package is its ctypes binding.
 """
-from .cderi import (CD_FP64, CD_JK_BF16X3, CD_JK_BF16X4, CD_JK_BF16X5, CD_JK_FP64, CD_UPDATE_FP64, CD_UPDATE_SLICE, CD_VEC_FP32, CDError,
+from .cderi import (CD_ALG_FULL, CD_ALG_SPAN, CD_ALG_TWOSTEP, CD_FP64, CD_JK_BF16X3, CD_JK_BF16X4, CD_JK_BF16X5, CD_JK_FP64, CD_UPDATE_FP64, CD_UPDATE_SLICE, CD_VEC_FP32, CDError,
                     Factor, System, batch_run, cd_eri_factor, cd_eri_factor_sys, cd_version, kernel_launches, load,
                     slice_matmul)
 
-__all__ = ["CD_FP64", "CD_JK_BF16X3", "CD_JK_BF16X4", "CD_JK_BF16X5", "CD_JK_FP64", "CD_UPDATE_FP64", "CD_UPDATE_SLICE", "CD_VEC_FP32", "CDError",
+__all__ = ["CD_ALG_FULL", "CD_ALG_SPAN", "CD_ALG_TWOSTEP", "CD_FP64", "CD_JK_BF16X3", "CD_JK_BF16X4", "CD_JK_BF16X5", "CD_JK_FP64", "CD_UPDATE_FP64", "CD_UPDATE_SLICE", "CD_VEC_FP32", "CDError",
            "Factor", "System", "batch_run", "cd_eri_factor", "cd_eri_factor_sys", "cd_version", "kernel_launches", "load",
            "slice_matmul"]

@@ -22,6 +22,7 @@ CD_JK_FP64, CD_JK_BF16X3, CD_JK_BF16X4, CD_JK_BF16X5 = 0, 1, 2, 3
 CD_JK_DEVICE, CD_JK_ONLY_J, CD_JK_ONLY_K, CD_JK_VEC_FP32 = 0x100, 0x200, 0x400, 0x800
 CD_MAX_PRIM = 16
 CD_UPDATE_SLICE, CD_UPDATE_FP64 = 0, 1
+CD_ALG_FULL, CD_ALG_SPAN, CD_ALG_TWOSTEP = 0, 1, 2
 
 _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENOTPSD",
              CD_ETIMEOUT: "CD_ETIMEOUT", CD_ECUDA: "CD_ECUDA"}
@@ -47,7 +48,7 @@ class cd_opts_t(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("schwarz", ctypes.c_double), ("vec_precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("max_vectors", ctypes.c_int64), ("mem_budget_gb", ctypes.c_double),
                 ("forced_pivots", ctypes.c_void_p), ("n_forced", ctypes.c_int64),
-                ("update", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("update", ctypes.c_int32), ("algorithm", ctypes.c_int32), ("span", ctypes.c_double)]
 
 
 _lib = None
@@ -123,9 +124,9 @@ class _BasisArgs:
 
 def make_opts(tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
               max_vectors: int = 0, mem_budget_gb: float = 0.0, forced: Optional[Sequence[int]] = None,
-              update: int = CD_UPDATE_SLICE):
+              update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0):
     o = cd_opts_t(float(tau), float(schwarz), int(vec_precision), int(block), int(max_vectors),
-                  float(mem_budget_gb), None, 0, int(update), 0)
+                  float(mem_budget_gb), None, 0, int(update), int(algorithm), float(span))
     keep = None
     if forced is not None:
         keep = np.ascontiguousarray(forced, dtype=np.int64)
@@ -216,7 +217,8 @@ class Factor:
         s = np.zeros(16)
         _check(load().cd_factor_stats(self._h, _p(s)))
         keys = ["ms_system", "ms_eri", "ms_colupd", "ms_steps", "ms_select", "ms_total", "blocks", "eri_columns",
-                "colupd_flops", "eri_entries", "M", "sliced", "eri_fp64_ops"]
+                "colupd_flops", "eri_entries", "M", "sliced", "eri_fp64_ops", "step1_ms", "step1_blocks",
+                "step1_eri_columns"]
         return dict(zip(keys, s.tolist()))
 
     def jk(self, C_occ, mode: int = CD_JK_FP64, stream=None, want=("J", "K")):
@@ -260,10 +262,11 @@ class Factor:
 
 def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
                   max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
-                  update: int = CD_UPDATE_SLICE) -> Factor:
+                  update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0) -> Factor:
     """Full pipeline from a host basis (C ABI cd_eri_factor)."""
     args = _BasisArgs(basis)
-    o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced, update)
+    o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced, update,
+                        algorithm, span)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor(ctypes.byref(args.s), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep
@@ -272,8 +275,9 @@ def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = 
 
 def cd_eri_factor_sys(system: System, tau: float, vec_precision: int = CD_FP64, block: int = 0,
                       max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
-                      update: int = CD_UPDATE_SLICE) -> Factor:
-    o, keep = make_opts(tau, 0.0, vec_precision, block, max_vectors, mem_budget_gb, forced, update)
+                      update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0) -> Factor:
+    o, keep = make_opts(tau, 0.0, vec_precision, block, max_vectors, mem_budget_gb, forced, update, algorithm,
+                        span)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor_sys(system._h, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep

@@ -174,6 +174,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   for (auto& r : hbra.row)
     if (r >= 0) r = p2r[r];
   s->bra_to_all = kall;
+  s->bra_row_h = hbra.row;
   rc = upload_pairs(hbra, &s->bra, st);
   if (rc != CD_OK) { system_release(s); return rc; }
   // per-row data: diagonal, (mu, nu), ket descriptor pieces
@@ -278,6 +279,13 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   std::vector<int64_t> cand_rows_h;
   std::vector<double> cand_vals_h;
   unsigned cand_count_h[1] = {0};
+  // span policies: residual diagonals of the block's columns
+  int64_t* slot_rows_dev = nullptr;  // [b] working row of each pool slot (-1 = empty)
+  double* slot_vals_dev = nullptr;   // [b]
+  std::vector<double> slot_vals_h;
+  // two-step, first step: compacted rows
+  int32_t* rowmap_dev = nullptr;     // [bra.n][9] working row of each bra component (-1 = dropped)
+  int64_t* order_dev = nullptr;      // live bra shell pairs, grouped by class
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   // sliced update runs on a second stream, concurrently with the ERI columns
   // (tensor cores vs FP64 pipe)
@@ -288,7 +296,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   ~Work() {
     for (void* p : {(void*)pool, (void*)D0, (void*)D1, (void*)Bg, (void*)slots_dev, (void*)rows_dev,
                     (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Ls, Bs, (void*)Dint,
-                    (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals, (void*)eri_ops})
+                    (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals, (void*)eri_ops,
+                    (void*)slot_rows_dev, (void*)slot_vals_dev, (void*)rowmap_dev, (void*)order_dev})
       scratch_free(p, st);
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -326,7 +335,9 @@ static int grow_vectors(cd_factor* f, Work* w, bool slice, int b, int64_t newcap
   return CD_OK;
 }
 
-static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_factor* f) {
+// reduce = true: first step of the two-step scheme (rows below tau dropped and
+// compacted; only f->piv, in system rows, is meaningful afterwards)
+static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_factor* f, bool reduce = false) {
   const double t_start = now_ms();
   const double tau = o->tau;
   if (!(tau > 0.0) || !std::isfinite(tau)) { set_error("tau must be finite and > 0"); return CD_EINVAL; }
@@ -337,7 +348,12 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   const bool slice = o->update == CD_UPDATE_SLICE;
   const bool forced = o->forced_pivots != nullptr;
   const int64_t nf = forced ? o->n_forced : 0;
-  const int64_t n = s->n_rows, ld = s->n_rows_pad, N = s->hb.nbf;
+  const bool span_mode = o->algorithm != CD_ALG_FULL;
+  const double span = o->span > 0.0 ? o->span : 0.01;
+  if (span_mode && !(span > 0.0 && span <= 1.0)) { set_error("span factor must be in (0, 1]"); return CD_EINVAL; }
+  if (span_mode && forced) { set_error("forced pivots need CD_ALG_FULL"); return CD_EINVAL; }
+  int64_t n = s->n_rows, ld = s->n_rows_pad;
+  const int64_t N = s->hb.nbf;
   if (forced) {
     if (nf < 0) { set_error("n_forced < 0"); return CD_EINVAL; }
     for (int64_t k = 0; k < nf; ++k)
@@ -386,6 +402,11 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     CD_TRY(launch_row_exp_sqrt(s->diag_dev, n, w.erow, st));
   }
   const int cand_cap = 4 * b;
+  if (span_mode) {
+    CD_TRY(scratch_alloc(&w.slot_rows_dev, (size_t)b, st));
+    CD_TRY(scratch_alloc(&w.slot_vals_dev, (size_t)b, st));
+    w.slot_vals_h.resize(b);
+  }
   CD_TRY(scratch_alloc(&w.sel, 1, st));
   CD_TRY(scratch_alloc(&w.eri_ops, 1, st));
   CD_CUDA(cudaMemsetAsync(w.eri_ops, 0, sizeof(unsigned long long), st));
@@ -419,15 +440,129 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   } else {
     res.dmax = -1.0; res.idx = -1; res.bad = 0;
   }
+  // ---- working rows.  All rows, or (two-step, first step) the rows whose
+  // residual diagonal is still >= tau: a residual diagonal never increases, so a
+  // row below tau can never be a pivot again and is dropped for good (Sec. 3);
+  // every row-indexed buffer is then compacted to the live rows.
+  std::vector<int64_t> grow;                  // working row -> system row (reduce)
+  PairSet bra_v = s->bra;                     // bra shell pairs with rows mapped to working rows
+  const int64_t* order_v = nullptr;
+  int64_t cls_v[4] = {s->bra_class_off[0], s->bra_class_off[1], s->bra_class_off[2], s->bra_class_off[3]};
+  auto sysrow = [&](int64_t r) -> int64_t { return reduce ? grow[r] : r; };
+  std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
+  std::unordered_map<int64_t, int> row2slot;
+  int64_t K = 0;
+  // compacts when forced, or when fewer than 3/4 of the working rows are live
+  auto compact_rows = [&](bool force) -> int {
+    std::vector<double> dh(n);
+    if (n > 0) CD_CUDA(cudaMemcpyAsync(dh.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> idx;
+    for (int64_t r = 0; r < n; ++r)
+      if (dh[r] >= tau) idx.push_back((int32_t)r);
+    const int64_t m = (int64_t)idx.size();
+    if (!force && 4 * m >= 3 * n) return CD_OK;
+    const int64_t ldm = std::max<int64_t>(32, (m + 31) / 32 * 32);
+    int32_t* idx_dev = nullptr;
+    CD_TRY(scratch_alloc(&idx_dev, (size_t)std::max<int64_t>(m, 1), st));
+    if (m > 0) CD_CUDA(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    double* nL = nullptr;
+    CD_TRY(dalloc(&nL, (size_t)f->Mcap * ldm));
+    CD_TRY(launch_compact_f64(f->L, ld, idx_dev, m, K, nL, ldm, st));
+    double *npool = nullptr, *nD0 = nullptr, *nD1 = nullptr;
+    CD_TRY(scratch_alloc(&npool, (size_t)b * ldm, st));
+    CD_TRY(scratch_alloc(&nD0, (size_t)ldm, st));
+    CD_TRY(scratch_alloc(&nD1, (size_t)ldm, st));
+    CD_CUDA(cudaMemsetAsync(npool, 0, sizeof(double) * b * ldm, st));
+    CD_CUDA(cudaMemsetAsync(nD0, 0, sizeof(double) * ldm, st));
+    CD_CUDA(cudaMemsetAsync(nD1, 0, sizeof(double) * ldm, st));
+    CD_TRY(launch_compact_f64(w.pool, ld, idx_dev, m, b, npool, ldm, st));
+    CD_TRY(launch_compact_f64(Dcur, ld, idx_dev, m, 1, nD0, ldm, st));
+    if (slice) {
+      void* nLs = nullptr;
+      int32_t* nerow = nullptr;
+      CD_TRY(scratch_alloc((uint16_t**)&nLs, (size_t)kSlices * std::max<int64_t>(m, 1) * w.kcap, st));
+      CD_TRY(scratch_alloc(&nerow, (size_t)std::max<int64_t>(m, 1), st));
+      CD_TRY(launch_compact_rows16(w.Ls, n, idx_dev, m, kSlices, w.kcap * 2, nLs, st));
+      CD_TRY(launch_compact_i32(w.erow, idx_dev, m, nerow, st));
+      scratch_free(w.Ls, st);
+      scratch_free(w.erow, st);
+      w.Ls = nLs;
+      w.erow = nerow;
+    }
+    CD_CUDA(cudaStreamSynchronize(st));
+    cudaFree(f->L);
+    f->L = nL;
+    scratch_free(w.pool, st);
+    scratch_free(w.D0, st);
+    scratch_free(w.D1, st);
+    scratch_free(idx_dev, st);
+    w.pool = npool;
+    w.D0 = Dcur = nD0;
+    w.D1 = Dnext = nD1;
+    // working <-> system rows, pool slots
+    std::vector<int64_t> old2new(n, -1);
+    for (int64_t i = 0; i < m; ++i) old2new[idx[i]] = i;
+    std::vector<int64_t> ngrow(m);
+    for (int64_t i = 0; i < m; ++i) ngrow[i] = grow.empty() ? idx[i] : grow[idx[i]];
+    grow.swap(ngrow);
+    row2slot.clear();
+    for (int sl = 0; sl < b; ++sl) {
+      if (slot_row[sl] < 0) continue;
+      slot_row[sl] = old2new[slot_row[sl]];
+      if (slot_row[sl] >= 0) row2slot[slot_row[sl]] = sl;
+    }
+    // bra components mapped to working rows; the shell pairs with a live row
+    std::vector<int32_t> sys2w(s->n_rows, -1);
+    for (int64_t i = 0; i < m; ++i) sys2w[grow[i]] = (int32_t)i;
+    std::vector<int32_t> rmap(s->bra_row_h.size(), -1);
+    std::vector<int64_t> order;
+    int64_t co[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+      co[c] = (int64_t)order.size();
+      for (int64_t k = s->bra_class_off[c]; k < s->bra_class_off[c + 1]; ++k) {
+        bool any = false;
+        for (int x = 0; x < 9; ++x) {
+          const int32_t r = s->bra_row_h[9 * k + x];
+          if (r >= 0 && sys2w[r] >= 0) { rmap[9 * k + x] = sys2w[r]; any = true; }
+        }
+        if (any) order.push_back(k);
+      }
+    }
+    co[3] = (int64_t)order.size();
+    scratch_free(w.rowmap_dev, st);
+    scratch_free(w.order_dev, st);
+    w.rowmap_dev = nullptr;
+    w.order_dev = nullptr;
+    CD_TRY(scratch_alloc(&w.rowmap_dev, std::max<size_t>(rmap.size(), 1), st));
+    CD_TRY(scratch_alloc(&w.order_dev, std::max<size_t>(order.size(), 1), st));
+    if (!rmap.empty())
+      CD_CUDA(cudaMemcpyAsync(w.rowmap_dev, rmap.data(), sizeof(int32_t) * rmap.size(), cudaMemcpyHostToDevice, st));
+    if (!order.empty())
+      CD_CUDA(cudaMemcpyAsync(w.order_dev, order.data(), sizeof(int64_t) * order.size(), cudaMemcpyHostToDevice, st));
+    bra_v.row = w.rowmap_dev;
+    order_v = w.order_dev;
+    for (int c = 0; c < 4; ++c) cls_v[c] = co[c];
+    n = m;
+    ld = ldm;
+    f->n = n;
+    f->ld = ld;
+    if (n > 0) {
+      CD_TRY(launch_argmax(Dcur, n, w.sc, w.res_dev, st));
+      CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
+    }
+    CD_CUDA(cudaStreamSynchronize(st));
+    if (n > 0) res = *w.res_h;
+    else { res.dmax = -1.0; res.idx = -1; res.bad = 0; }
+    return CD_OK;
+  };
+  if (reduce) CD_TRY(compact_rows(true));
   OzakiPlan plan;
   plan.SA = plan.SB = kSlices;
   plan.KEEP = kSlices + 1;
   plan.F = kSliceF;
-  std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
-  std::unordered_map<int64_t, int> row2slot;
   double t_eri = 0, t_upd = 0, t_sel = 0, t_steps = 0, upd_flops = 0, eri_ints = 0;
   int64_t nblocks = 0, ncols = 0;
-  int64_t K = 0;
   bool done = false;
   const bool dbg = getenv("CDERI_DEBUG") != nullptr;
   // The sliced update runs on the main stream before the ERI columns: run
@@ -435,7 +570,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   // compete for the same SMs and the block takes as long as in sequence.
   const bool overlap = getenv("CDERI_OVERLAP_UPDATE") != nullptr;
   while (!done) {
+    if (reduce && K > 0) CD_TRY(compact_rows(false));
     if (forced ? (K >= nf) : !(res.dmax >= tau)) break;
+    // qualified threshold of this macro iteration (span policies)
+    const double thr = span_mode ? std::max(span * res.dmax, tau) : tau;
     if (dbg) fprintf(stderr, "[cderi] block %lld K=%lld dmax=%.3e idx=%lld\n", (long long)nblocks, (long long)K,
                      res.dmax, (long long)res.idx);
     // ---- candidate block
@@ -446,7 +584,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         if (std::find(cand.begin(), cand.end(), o->forced_pivots[k]) == cand.end()) cand.push_back(o->forced_pivots[k]);
     } else {
       // the b largest residual diagonals >= tau (radix select on the device)
-      CD_TRY(launch_select(Dcur, n, tau, b, w.sel, w.cand_rows, w.cand_vals, cand_cap, st));
+      CD_TRY(launch_select(Dcur, n, thr, b, w.sel, w.cand_rows, w.cand_vals, cand_cap, st));
       CD_CUDA(cudaMemcpyAsync(w.cand_count_h, &w.sel->count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
       CD_CUDA(cudaMemcpyAsync(w.cand_rows_h.data(), w.cand_rows, sizeof(int64_t) * cand_cap, cudaMemcpyDeviceToHost, st));
       CD_CUDA(cudaMemcpyAsync(w.cand_vals_h.data(), w.cand_vals, sizeof(double) * cand_cap, cudaMemcpyDeviceToHost, st));
@@ -460,7 +598,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         CD_CUDA(cudaMemcpyAsync(w.dh.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         CD_CUDA(cudaStreamSynchronize(st));
         for (int64_t r = 0; r < n; ++r)
-          if (w.dh[r] >= tau) c.emplace_back(w.dh[r], r);
+          if (w.dh[r] >= thr) c.emplace_back(w.dh[r], r);
       }
       auto cmp = [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
         return x.first > y.first || (x.first == y.first && x.second < y.second);
@@ -489,7 +627,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       slot_row[free_sl] = r;
       slot_valid[free_sl] = 0;
       row2slot[r] = free_sl;
-      kets.push_back(ket_of_row(s, r, free_sl));
+      kets.push_back(ket_of_row(s, sysrow(r), free_sl));
     }
     ++nblocks;
     ncols += (int64_t)kets.size();
@@ -525,7 +663,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     std::vector<KetGroup> groups = group_kets(kets);
     if (!kets.empty()) {
       CD_CUDA(cudaMemcpyAsync(w.kets_dev, groups.data(), sizeof(KetGroup) * groups.size(), cudaMemcpyHostToDevice, st));
-      CD_TRY(launch_eri_columns(s->bra, nullptr, s->bra_class_off, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
+      CD_TRY(launch_eri_columns(bra_v, order_v, cls_v, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
                                 s->boys, st, w.eri_ops));
       eri_ints += (double)kets.size() * (double)n;
     }
@@ -559,6 +697,11 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       if (slot_row[sl] >= 0) slot_valid[sl] = K;
     const int64_t Kb = K;
     bool first = true;
+    if (span_mode) {  // residual diagonals of the block's columns
+      CD_CUDA(cudaMemcpyAsync(w.slot_rows_dev, slot_row.data(), sizeof(int64_t) * b, cudaMemcpyHostToDevice, st));
+      CD_TRY(launch_gather_vals(Dcur, w.slot_rows_dev, b, w.slot_vals_dev, st));
+      CD_CUDA(cudaMemcpyAsync(w.slot_vals_h.data(), w.slot_vals_dev, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+    }
     CD_CUDA(cudaStreamSynchronize(st));  // columns of this block are complete
     const double t_blk = now_ms();
     // ---- serial pivot steps inside the block
@@ -568,6 +711,19 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       if (forced) {
         if (K >= nf) { done = true; break; }
         p = o->forced_pivots[K];
+      } else if (span_mode) {
+        if (!(res.dmax >= tau)) { done = true; break; }
+        // the largest residual diagonal among the block's unused columns (ties:
+        // lowest row); the macro iteration ends when it is below the threshold
+        int best = -1;
+        for (int x = 0; x < b; ++x) {
+          if (slot_row[x] < 0) continue;
+          const double v = w.slot_vals_h[x];
+          if (best < 0 || v > w.slot_vals_h[best] || (v == w.slot_vals_h[best] && slot_row[x] < slot_row[best]))
+            best = x;
+        }
+        if (best < 0 || !(w.slot_vals_h[best] >= thr)) break;
+        p = slot_row[best];
       } else {
         if (!(res.dmax >= tau)) { done = true; break; }
         p = res.idx;
@@ -579,6 +735,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         CD_CUDA(cudaMemcpyAsync(w.dp_h, Dcur + p, sizeof(double), cudaMemcpyDeviceToHost, st));
         CD_CUDA(cudaStreamSynchronize(st));
         dp = *w.dp_h;
+      } else if (span_mode) {
+        dp = w.slot_vals_h[sl];
       } else {
         dp = res.dmax;
       }
@@ -600,6 +758,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       CD_TRY(launch_finalize(w.pool + (int64_t)sl * ld, f->L, ld, Kb, K, p, Dcur, Dnext, f->L + K * ld, n, neg_tol,
                              w.sc, w.res_dev, st));
       CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
+      if (span_mode) {
+        CD_TRY(launch_gather_vals(Dnext, w.slot_rows_dev, b, w.slot_vals_dev, st));
+        CD_CUDA(cudaMemcpyAsync(w.slot_vals_h.data(), w.slot_vals_dev, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+      }
       CD_CUDA(cudaStreamSynchronize(st));
       if (first) {
         float a = 0, c = 0;
@@ -615,7 +777,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       }
       res = *w.res_h;
       std::swap(Dcur, Dnext);
-      f->piv.push_back(p);
+      f->piv.push_back(sysrow(p));
       f->gaps.push_back(gap);
       ++K;
       row2slot.erase(it);
@@ -758,8 +920,40 @@ int cd_eri_factor_sys(cd_system_t* sys, const cd_opts_t* opts, void* stream, cd_
   if (!out) { set_error("out is NULL"); return CD_EINVAL; }
   *out = nullptr;
   if (!sys || !opts) { set_error("system or opts is NULL"); return CD_EINVAL; }
+  if (opts->algorithm < CD_ALG_FULL || opts->algorithm > CD_ALG_TWOSTEP) { set_error("bad algorithm"); return CD_EINVAL; }
   cd_factor* f = new cd_factor();
-  int rc = factor_impl(sys, opts, (cudaStream_t)stream, f);
+  int rc = CD_OK;
+  if (opts->algorithm == CD_ALG_TWOSTEP) {
+    // step 1: the Cholesky basis, by the span policy on the rows still >= tau
+    const double t0 = now_ms();
+    if (opts->forced_pivots) { set_error("forced pivots need CD_ALG_FULL"); delete f; return CD_EINVAL; }
+    cd_factor* f1 = new cd_factor();
+    cd_opts_t o1 = *opts;
+    o1.algorithm = CD_ALG_SPAN;
+    o1.vec_precision = CD_FP64;
+    rc = factor_impl(sys, &o1, (cudaStream_t)stream, f1, true);
+    std::vector<int64_t> basis = f1->piv;
+    const double s1_blocks = f1->stats[6], s1_cols = f1->stats[7];
+    cudaStreamSynchronize((cudaStream_t)stream);
+    factor_release(f1);
+    const double t1 = now_ms() - t0;
+    // step 2: the vectors of that basis over every row, Eq. (CVsLT)
+    if (rc == CD_OK) {
+      cd_opts_t o2 = *opts;
+      o2.algorithm = CD_ALG_FULL;
+      o2.forced_pivots = basis.data();
+      o2.n_forced = (int64_t)basis.size();
+      rc = factor_impl(sys, &o2, (cudaStream_t)stream, f);
+    }
+    if (rc == CD_OK) {
+      f->stats[5] += t1;
+      f->stats[13] = t1;
+      f->stats[14] = s1_blocks;
+      f->stats[15] = s1_cols;
+    }
+  } else {
+    rc = factor_impl(sys, opts, (cudaStream_t)stream, f);
+  }
   if (rc != CD_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     factor_release(f);

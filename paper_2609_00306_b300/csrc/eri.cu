@@ -361,14 +361,17 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
 
 // grid: x = tiles of bra shell pairs of one class, y = ket groups
 template <int LA, int LB>
-__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, int64_t b0, int64_t b1, PairSet ket,
+__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, const int64_t* __restrict__ order, int64_t b0,
+                                                          int64_t b1, PairSet ket,
                                                           const KetGroup* __restrict__ groups, double* __restrict__ out,
                                                           int64_t ld, const double* __restrict__ tab,
                                                           unsigned long long* __restrict__ op_count) {
   const KetGroup kg = groups[blockIdx.y];
-  const int64_t sb = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t ib = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long ops = 0;
-  if (sb < b1) {
+  if (ib < b1) {
+    // bra shell pair: the ib-th of the class range, or the ib-th entry of a subset list
+    const int64_t sb = order ? __ldg(order + ib) : ib;
     const int cls = kg.lc * 2 + kg.ld;
     if (cls == 0) column_block<LA, LB, 0, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
     else if (cls == 2) {
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
 
 }  // namespace
 
-int launch_eri_columns(const PairSet& bra, const int64_t* /*bra_order*/, const int64_t* class_off,
+int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* kets_dev, int nket,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,
                        unsigned long long* op_count) {
@@ -415,9 +418,9 @@ int launch_eri_columns(const PairSet& bra, const int64_t* /*bra_order*/, const i
     int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
     if (b1 <= b0) continue;
     dim3 grid((unsigned)((b1 - b0 + 127) / 128), (unsigned)nket);
-    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else eri_columns_kernel<1, 1><<<grid, 128, 0, st>>>(bra, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else eri_columns_kernel<1, 1><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
     count_launch();
   }
   CD_CUDA(cudaGetLastError());

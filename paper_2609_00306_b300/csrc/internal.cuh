@@ -139,6 +139,9 @@ std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets);
 
 // ERI kernels (eri.cu)
 // out[slot * ld + row] = (bra rows | ket component) for every bra shell pair in `bra`
+// bra_order: NULL (every bra shell pair; class c is [class_off[c], class_off[c+1]))
+// or a device list of bra shell pairs grouped by class, class c being entries
+// [class_off[c], class_off[c+1]) of the list.  Rows come from bra.row.
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* groups_dev, int ngroups,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,
@@ -157,6 +160,7 @@ struct cd_system {
   int64_t* bra_order = nullptr;  // unused (bra already sorted); kept for symmetry
   int64_t bra_class_off[4] = {0, 0, 0, 0};
   std::vector<int32_t> bra_to_all;          // bra shell pair -> index in `all`
+  std::vector<int32_t> bra_row_h;           // host copy of bra.row ([n][9] row of each component, -1 = none)
   std::vector<int64_t> all_class_off_h;     // class offsets of `all` (sorted by class)
   int64_t all_class_off[4] = {0, 0, 0, 0};
   int64_t n_rows = 0, n_rows_pad = 0;

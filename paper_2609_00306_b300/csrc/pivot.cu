@@ -9,6 +9,7 @@
 // buffered (read D, write D') so that D_p stays readable by every CTA.
 // The argmax is reduced warp -> CTA (shuffles) -> grid (last CTA to finish).
 #include <float.h>
+#include <math.h>
 #include "internal.cuh"
 #include "pivot.cuh"
 
@@ -137,7 +138,80 @@ __global__ void gather_kernel(const double* __restrict__ L, int64_t ld, const in
   Bg[t] = L[(k0 + k) * ld + rows[j]];
 }
 
+// dst[c * ldd + i] = src[c * lds + idx[i]] for c < ncol, i < m (row compaction of
+// column-stored vectors: idx increasing, so reads stay mostly coalesced)
+__global__ void compact_f64_kernel(const double* __restrict__ src, int64_t lds, const int32_t* __restrict__ idx,
+                                   int64_t m, int64_t ncol, double* __restrict__ dst, int64_t ldd) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * ncol) return;
+  const int64_t c = t / m, i = t % m;
+  dst[c * ldd + i] = src[c * lds + __ldg(idx + i)];
+}
+
+// rows of 16-byte words: dst[(g * m + i) * w + x] = src[(g * n_old + idx[i]) * w + x]
+// for g < groups (slices), i < m, x < w
+__global__ void compact_rows16_kernel(const uint4* __restrict__ src, int64_t n_old, const int32_t* __restrict__ idx,
+                                      int64_t m, int groups, int64_t w, uint4* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = m * w;
+  if (t >= per * groups) return;
+  const int64_t g = t / per, r = t % per;
+  const int64_t i = r / w, x = r % w;
+  dst[(g * m + i) * w + x] = src[(g * n_old + __ldg(idx + i)) * w + x];
+}
+
+__global__ void compact_i32_kernel(const int32_t* __restrict__ src, const int32_t* __restrict__ idx, int64_t m,
+                                   int32_t* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) dst[i] = src[__ldg(idx + i)];
+}
+
+// out[j] = D[rows[j]] (or -inf for rows[j] < 0), j < nb
+__global__ void gather_vals_kernel(const double* __restrict__ D, const int64_t* __restrict__ rows, int nb,
+                                   double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) out[j] = rows[j] >= 0 ? D[rows[j]] : -INFINITY;
+}
+
 }  // namespace
+
+int launch_compact_f64(const double* src, int64_t lds, const int32_t* idx, int64_t m, int64_t ncol, double* dst,
+                       int64_t ldd, cudaStream_t st) {
+  const int64_t tot = m * ncol;
+  if (tot <= 0) return CD_OK;
+  compact_f64_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(src, lds, idx, m, ncol, dst, ldd);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_compact_rows16(const void* src, int64_t n_old, const int32_t* idx, int64_t m, int groups, int64_t row_bytes,
+                          void* dst, cudaStream_t st) {
+  if (row_bytes % 16) { set_error("compact_rows16: row not a multiple of 16 bytes"); return CD_EINVAL; }
+  const int64_t w = row_bytes / 16, tot = m * w * groups;
+  if (tot <= 0) return CD_OK;
+  compact_rows16_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((const uint4*)src, n_old, idx, m, groups, w,
+                                                                       (uint4*)dst);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_compact_i32(const int32_t* src, const int32_t* idx, int64_t m, int32_t* dst, cudaStream_t st) {
+  if (m <= 0) return CD_OK;
+  compact_i32_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(src, idx, m, dst);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_gather_vals(const double* D, const int64_t* rows, int nb, double* out, cudaStream_t st) {
+  if (nb <= 0) return CD_OK;
+  gather_vals_kernel<<<(nb + 255) / 256, 256, 0, st>>>(D, rows, nb, out);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
 
 int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st) {
   argmax_kernel<<<kStepGrid, kStepThreads, 0, st>>>(D, n, sc, res);

@@ -42,6 +42,15 @@ int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, 
 int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
                   double* Bg, cudaStream_t st);
 
+// row compaction (first step of the two-step scheme): keep rows idx[0..m) (increasing)
+int launch_compact_f64(const double* src, int64_t lds, const int32_t* idx, int64_t m, int64_t ncol, double* dst,
+                       int64_t ldd, cudaStream_t st);
+int launch_compact_rows16(const void* src, int64_t n_old, const int32_t* idx, int64_t m, int groups, int64_t row_bytes,
+                          void* dst, cudaStream_t st);
+int launch_compact_i32(const int32_t* src, const int32_t* idx, int64_t m, int32_t* dst, cudaStream_t st);
+// out[j] = D[rows[j]] (-inf where rows[j] < 0)
+int launch_gather_vals(const double* D, const int64_t* rows, int nb, double* out, cudaStream_t st);
+
 // column update (colupd.cu): cols[slot[j]] -= L[k0:k1]^T Bg  (Bg row-major [k1-k0][nb])
 int launch_colupd(double* cols, int64_t ld, const int32_t* slots_dev, int nb, const double* L,
                   int64_t k0, int64_t k1, const double* Bg, int64_t n, cudaStream_t st);

@@ -1,0 +1,127 @@
+"""Span-factor policies on the GPU (CD_ALG_SPAN: Koch's partially pivoted
+decomposition; CD_ALG_TWOSTEP: the two-step scheme of Sec. 3) against the
+oracle's ``cd_span`` / ``cd_from_basis``, through the C ABI.
+
+Tolerances as for the full-pivoting parity tests: identical basis (pivot
+sequence) and vector count, except at a near-tie (the oracle's own residual
+diagonals of the two choices within 1e-12); vectors to 1e-10 x max |L|;
+every residual diagonal < tau.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_00306_b300 import build
+    build.build()
+    import paper_2609_00306_b300 as cd
+    cd.load()
+
+
+_cache = {}
+
+
+def _setup(name):
+    if name not in _cache:
+        s = synth.make_workload(name)
+        o = oracle.Oracle(s.basis)
+        rows = o.screen(s.schwarz)
+        _cache[name] = (s, o, rows)
+    return _cache[name]
+
+
+CASES = [("s40", 0.05, 16), ("sp8", 0.1, 8), ("sp18", 0.02, 32), ("sp27", 0.01, 64), ("sp27", 1.0, 64),
+         ("sp18", 0.3, 1)]
+
+
+def _check_sequence(o, rows, s, got, ref_piv):
+    diverge = np.nonzero(got[: ref_piv.shape[0]] != ref_piv[: got.shape[0]])[0]
+    if diverge.size:
+        k = int(diverge[0])
+        Dk = o.cd(rows, s.tau, forced=ref_piv[:k]).D
+        assert abs(Dk[got[k]] - Dk[ref_piv[k]]) < 1e-12, (k, Dk[got[k]], Dk[ref_piv[k]])
+        return False
+    assert got.shape[0] == ref_piv.shape[0]
+    return True
+
+
+@pytest.mark.parametrize("update", [0, 1])
+@pytest.mark.parametrize("name,span,b", CASES)
+def test_span_policy_matches_oracle(name, span, b, update):
+    import paper_2609_00306_b300 as cd
+    s, o, rows = _setup(name)
+    ref = o.cd_span(rows, s.tau, span, qmax=b, reduce=False)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=b, algorithm=cd.CD_ALG_SPAN, span=span, update=update)
+    prow, ppk, gaps, resid = f.pivots()
+    assert f.max_resid < s.tau and np.max(resid) < s.tau
+    if _check_sequence(o, rows, s, prow, ref.piv):
+        assert f.stats()["blocks"] == ref.macro_start.shape[0]
+        L = f.vectors_host()
+        assert np.max(np.abs(L - ref.L)) <= 1e-10 * np.max(np.abs(ref.L))
+
+
+@pytest.mark.parametrize("name,span,b", CASES)
+def test_two_step_matches_oracle(name, span, b):
+    import paper_2609_00306_b300 as cd
+    s, o, rows = _setup(name)
+    ref = o.cd_span(rows, s.tau, span, qmax=b, reduce=True)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=b, algorithm=cd.CD_ALG_TWOSTEP, span=span)
+    prow, ppk, gaps, resid = f.pivots()
+    assert np.array_equal(ppk, rows[prow])
+    assert f.max_resid < s.tau and np.max(resid) < s.tau
+    if _check_sequence(o, rows, s, prow, ref.piv):
+        st = f.stats()
+        assert st["step1_blocks"] == ref.macro_start.shape[0]
+        Lref = o.cd_from_basis(rows, ref.piv)
+        L = f.vectors_host()
+        assert np.max(np.abs(L - Lref)) <= 1e-10 * np.max(np.abs(Lref))
+
+
+def test_span_one_is_full_pivoting_on_gpu():
+    import paper_2609_00306_b300 as cd
+    s, o, rows = _setup("sp27")
+    full = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=32)
+    for alg in (cd.CD_ALG_SPAN, cd.CD_ALG_TWOSTEP):
+        f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=32, algorithm=alg, span=1.0)
+        assert np.array_equal(f.pivots()[0], full.pivots()[0])
+
+
+def test_two_step_and_koch_choose_the_same_basis_sp400():
+    """Discarding rows below tau cannot change the basis (a residual diagonal
+    never increases); at N = 400 the first step runs on a compacted row set."""
+    import paper_2609_00306_b300 as cd
+    s = synth.make_workload("sp400")
+    koch = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=64, algorithm=cd.CD_ALG_SPAN, span=0.01)
+    two = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, block=64, algorithm=cd.CD_ALG_TWOSTEP, span=0.01)
+    pk, pt = koch.pivots()[0], two.pivots()[0]
+    n = min(pk.shape[0], pt.shape[0])
+    same = np.array_equal(pk, pt)
+    if not same:  # only a near-tie may split them; the rest must agree before it
+        k = int(np.nonzero(pk[:n] != pt[:n])[0][0])
+        assert k > 0.9 * n, k
+    else:
+        Lk = koch.vectors_host()
+        Lt = two.vectors_host()
+        assert np.max(np.abs(Lk - Lt)) <= 1e-10 * np.max(np.abs(Lk))
+    assert koch.max_resid < s.tau and two.max_resid < s.tau
+    st = two.stats()
+    assert st["step1_eri_columns"] >= two.M and st["step1_blocks"] >= 1
+
+
+def test_span_rejects_bad_factor():
+    import paper_2609_00306_b300 as cd
+    s, o, rows = _setup("sp8")
+    with pytest.raises(cd.CDError):
+        cd.cd_eri_factor(s.basis, s.tau, s.schwarz, algorithm=cd.CD_ALG_SPAN, span=1.5)
+    with pytest.raises(cd.CDError):
+        cd.cd_eri_factor(s.basis, s.tau, s.schwarz, algorithm=7)
