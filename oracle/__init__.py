@@ -20,6 +20,8 @@ What each function follows (the paper, arXiv 2609.00306, Sec. 2 and 4.1):
   tau (first step of the two-step scheme).  ``Oracle.cd_from_basis`` -- second
   step: Cholesky factor of the basis metric and the triangular solve of
   Eq. (CVsLT).  Both in C (``or_cd_span``, ``or_cd_from_basis``).
+* ``mo_vectors`` -- the vectors in the MO basis used by CASSCF and CC (Sec.
+  4.1), C^T L^P C for every P; ``mo_eri`` the MO integrals from the exact tensor.
 
 Readings taken where the paper is silent (each one is listed with the design
 notes): packed mu >= nu pair indices, strict ``< tau`` stop, ties to the lowest
@@ -337,3 +339,17 @@ def jk_exact(tensor: np.ndarray, C_occ: np.ndarray):
     J = np.einsum("mnsr,sr->mn", tensor, Dm)
     K = np.einsum("msnr,sr->mn", tensor, Dm)
     return J, K
+
+
+def mo_vectors(L: np.ndarray, rows: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Cholesky vectors in the MO basis (Sec. 4.1, CASSCF / CC): for every vector P,
+    L^P_{pq} = sum_{mu nu} C_{mu p} L^P_{mu nu} C_{nu q}, L^P the symmetric N x N
+    unpacking of the packed vector.  Returns [M, n_mo, n_mo]."""
+    N = C.shape[0]
+    U = unpack_vectors(L, rows, N)             # [M, N, N]
+    return np.einsum("mp,Pmn,nq->Ppq", C, U, C, optimize=True)
+
+
+def mo_eri(tensor: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """(pq|rs) = sum C_{mu p} C_{nu q} C_{sigma r} C_{rho s} (mu nu|sigma rho), from the exact tensor."""
+    return np.einsum("ap,bq,cr,ds,abcd->pqrs", C, C, C, C, tensor, optimize=True)
