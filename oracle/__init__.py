@@ -78,9 +78,9 @@ def _load():
         lib.or_screen.restype = I64
         lib.or_screen.argtypes = [P, P, D, P]
         lib.or_cd.restype = I
-        lib.or_cd.argtypes = [P, P, I64, D, P, I, I, P, P, P, P, P]
+        lib.or_cd.argtypes = [P, P, I64, D, P, I, I, P, P, P, P, P, P]
         lib.or_cd_span.restype = I
-        lib.or_cd_span.argtypes = [P, P, I64, D, D, I, I, I, P, P, P, P, P]
+        lib.or_cd_span.argtypes = [P, P, I64, D, D, I, I, I, P, P, P, P, P, P]
         lib.or_cd_from_basis.restype = I
         lib.or_cd_from_basis.argtypes = [P, P, I64, P, I, P]
         _lib = lib
@@ -225,10 +225,13 @@ class Oracle:
 
     # -- Cholesky decomposition -------------------------------------------
     def cd(self, rows, tau: float, forced=None, mcap: Optional[int] = None,
-           max_steps: Optional[int] = None) -> CDResult:
+           max_steps: Optional[int] = None, candidates=None) -> CDResult:
         """Run the decomposition; ``max_steps`` stops after that many vectors
-        (a bounded sample of a large run; the result is then partial)."""
+        (a bounded sample of a large run; the result is then partial).
+        ``candidates``: boolean mask over ``rows`` of the rows that may be pivots
+        (None = all); the stop test then runs over those rows only."""
         rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cand = None if candidates is None else np.ascontiguousarray(candidates, dtype=np.uint8)
         if max_steps is not None:
             mcap = int(max_steps)
         n = rows.shape[0]
@@ -246,7 +249,8 @@ class Oracle:
             pivD = np.zeros(max(mcap, 1))
             M = self._lib.or_cd(self._h, _ptr(rows), n, float(tau),
                                 _ptr(forced) if forced is not None else None, nf, mcap,
-                                _ptr(piv), _ptr(L), _ptr(D), _ptr(gap), _ptr(pivD))
+                                _ptr(piv), _ptr(L), _ptr(D), _ptr(gap), _ptr(pivD),
+                                _ptr(cand) if cand is not None else None)
             if M == -1 and max_steps is not None:
                 M = int(max_steps)
             elif M == -1 and mcap < n:
@@ -260,7 +264,7 @@ class Oracle:
 
     # -- span-factor selection and the two-step scheme --------------------
     def cd_span(self, rows, tau: float, span: float, qmax: int = 64, reduce: bool = False,
-                mcap: Optional[int] = None) -> SpanResult:
+                mcap: Optional[int] = None, candidates=None) -> SpanResult:
         """Partially pivoted decomposition with span factor ``span`` (C ``or_cd_span``).
 
         ``reduce=False``: Koch's one-step algorithm, ``L`` is the factor.
@@ -269,6 +273,7 @@ class Oracle:
         the vectors come from :meth:`cd_from_basis`.
         """
         rows = np.ascontiguousarray(rows, dtype=np.int64)
+        cand = None if candidates is None else np.ascontiguousarray(candidates, dtype=np.uint8)
         n = rows.shape[0]
         mcap = mcap or min(n, max(64, 4 * self.nbf))
         while True:
@@ -278,7 +283,8 @@ class Oracle:
             ms = np.zeros(max(mcap, 1) + 1, dtype=np.int32)
             nm = ctypes.c_int(0)
             M = self._lib.or_cd_span(self._h, _ptr(rows), n, float(tau), float(span), int(qmax), int(bool(reduce)),
-                                     mcap, _ptr(piv), _ptr(L), _ptr(D), _ptr(ms), ctypes.byref(nm))
+                                     mcap, _ptr(piv), _ptr(L), _ptr(D), _ptr(ms), ctypes.byref(nm),
+                                     _ptr(cand) if cand is not None else None)
             if M == -1 and mcap < n:
                 mcap = min(n, 2 * mcap)
                 continue

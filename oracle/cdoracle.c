@@ -370,13 +370,19 @@ int64_t or_screen(void* h, const double* diag, double thr, int64_t* rows_out)
 /* Forced mode (nforced >= 0): the pivot of step K is forced[K] instead of    */
 /* the argmax, for K < nforced, and the run stops after nforced steps; gap[K] */
 /* records Dmax - D_forced at each step.                                      */
+/* Candidate mask (cand != NULL): only rows with cand[r] != 0 may be pivots,  */
+/* and Dmax, the argmax and the stop test run over those rows; the vectors    */
+/* still cover every row.  This is the restriction of the Cholesky basis to  */
+/* one block of the matrix (the (LL|LL) diagonals in the spin-free            */
+/* relativistic case of Sec. 5, where no (SS|SS) diagonals are then needed).  */
 /* L is row-major [mcap][npairs].  Returns M >= 0, or                         */
 /*   -1 if M would exceed mcap, -2 if a pivot diagonal is not positive or a   */
 /*   residual diagonal is below -1e-10 * max D^1 (matrix not PSD).            */
 /* ------------------------------------------------------------------------- */
 int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
           const int64_t* forced, int nforced, int mcap,
-          int64_t* piv_out, double* L, double* D, double* gap, double* pivD)
+          int64_t* piv_out, double* L, double* D, double* gap, double* pivD,
+          const unsigned char* cand)
 {
     int* ri = (int*)malloc(sizeof(int) * npairs);
     int* rj = (int*)malloc(sizeof(int) * npairs);
@@ -390,7 +396,7 @@ int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
     for (;;) {
         double dmax = -INFINITY; int64_t am = -1;
         for (int64_t r = 0; r < npairs; ++r)
-            if (D[r] > dmax) { dmax = D[r]; am = r; }
+            if ((!cand || cand[r]) && D[r] > dmax) { dmax = D[r]; am = r; }
         int64_t p;
         if (nforced >= 0) {
             if (K >= nforced) break;
@@ -459,11 +465,14 @@ int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
 /*                                                                           */
 /* L is row-major [mcap][npairs]; entries of dropped rows are left at 0.      */
 /* macro_start[i] = K at the start of macro iteration i (optional).           */
+/* cand: candidate mask as for or_cd (NULL = every row); with reduce = 1 the  */
+/* rows outside it are not carried through the first step at all.            */
 /* Returns M >= 0, or -1 if M would exceed mcap, -2 if a pivot diagonal is    */
 /* not positive or a residual below -1e-10 max D^1 (matrix not PSD).          */
 /* ------------------------------------------------------------------------- */
 int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double span, int qmax, int reduce,
-               int mcap, int64_t* piv_out, double* L, double* D, int* macro_start, int* n_macro)
+               int mcap, int64_t* piv_out, double* L, double* D, int* macro_start, int* n_macro,
+               const unsigned char* cand)
 {
     int* ri = (int*)malloc(sizeof(int) * npairs);
     int* rj = (int*)malloc(sizeof(int) * npairs);
@@ -473,7 +482,9 @@ int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double 
     for (int64_t r = 0; r < npairs; ++r) D[r] = or_eri(h, ri[r], rj[r], ri[r], rj[r]);
     double d1max = 0.0;
     for (int64_t r = 0; r < npairs; ++r) if (D[r] > d1max) d1max = D[r];
-    for (int64_t r = 0; r < npairs; ++r) live[r] = reduce ? (D[r] >= tau) : 1;
+    /* with a candidate mask and reduce = 1 the other rows are not needed at all */
+    for (int64_t r = 0; r < npairs; ++r)
+        live[r] = reduce ? (D[r] >= tau && (!cand || cand[r])) : 1;
     if (qmax < 1) qmax = 1;
     int64_t* Q = (int64_t*)malloc(sizeof(int64_t) * qmax);
     char* used = (char*)malloc(qmax);
@@ -483,7 +494,7 @@ int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double 
     for (;;) {
         double dmax = -INFINITY;
         for (int64_t r = 0; r < npairs; ++r)
-            if (live[r] && D[r] > dmax) dmax = D[r];
+            if (live[r] && (!cand || cand[r]) && D[r] > dmax) dmax = D[r];
         if (!(dmax >= tau)) break;
         double thr = span * dmax;
         if (thr < tau) thr = tau;
@@ -492,7 +503,7 @@ int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double 
         while (nq < qmax) {
             int64_t best = -1;
             for (int64_t r = 0; r < npairs; ++r) {
-                if (!live[r] || !(D[r] >= thr)) continue;
+                if (!live[r] || (cand && !cand[r]) || !(D[r] >= thr)) continue;
                 int taken = 0;
                 for (int i = 0; i < nq; ++i) if (Q[i] == r) { taken = 1; break; }
                 if (taken) continue;
