@@ -82,6 +82,13 @@ typedef struct {
   int32_t update;       /* column update of Eq. (subtr): CD_UPDATE_SLICE (default) or CD_UPDATE_FP64 */
   int32_t algorithm;    /* pivot policy: CD_ALG_FULL (default), CD_ALG_SPAN or CD_ALG_TWOSTEP (below) */
   double  span;         /* span factor eta in (0, 1] of CD_ALG_SPAN / CD_ALG_TWOSTEP (0 = 0.01) */
+  const uint8_t* candidates; /* host [n_rows] (system row order), nonzero = the row may be a pivot;
+                              * NULL = every row.  The Cholesky basis is then chosen from that
+                              * block of the matrix only (Sec. 5: the (LL|LL) diagonals of the
+                              * spin-free relativistic matrix); the stop test max D < tau runs over
+                              * the candidate rows, the vectors still cover every row, and rows
+                              * outside the block carry no tau guarantee.  With CD_ALG_TWOSTEP the
+                              * first step never touches the other rows. */
 } cd_opts_t;
 
 /* Pivot policies.
@@ -162,8 +169,8 @@ int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, 
 int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, double* out);
 /* Statistics of the factorisation, 16 doubles: [0] system set-up ms (host
  * clock), [1] ERI-column kernels ms, [2] column-update kernels ms (CUDA
- * events; the sliced update runs concurrently with the ERI columns, so [1]
- * and [2] overlap), [3] pivot steps ms (host clock), [4] candidate selection
+ * events; the update runs on the calling stream before the ERI columns of each
+ * block), [3] pivot steps ms (host clock), [4] candidate selection
  * ms, [5] total ms;
  * [6] blocks, [7] ERI columns computed, [8] column-update flops (2 x rows x
  * columns x vectors applied), [9] ERI column entries computed, [10] M;
@@ -185,6 +192,19 @@ long long cd_kernel_launches(void);
  * over the vectors.  K (kernel e): B^P = L^P C_occ, K = 2 sum_P B^P B^P^T. */
 int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ,
           double* J, double* K, int32_t mode, void* stream);
+
+/* ---- Cholesky vectors in the MO basis (Sec. 4.1: CASSCF, CC) --------------- */
+/* out[P - P0][i][j] = sum_{mu nu} C[mu][i] L^P_{mu nu} C[nu][j] for
+ * P0 <= P < P0 + nP and i, j < n_mo, with L^P the symmetric N x N unpacking of
+ * vector P (zero on screened-out pairs).  C [N][n_mo] row-major; out
+ * [nP][n_mo][n_mo] row-major, caller-owned; host pointers unless flags has
+ * CD_JK_DEVICE.  slices: 0 = FP64 GEMMs (FP64 pipe), 3 / 4 / 5 / 7 = exact
+ * 8-bit-slice GEMMs on the BF16 tensor cores, B^P = L^P C then C^T B^P
+ * (7 slices: 56-bit fixed point per row, FP64-equivalent).  The work is done in
+ * chunks of vectors; O(N^3) per vector.  Errors: CD_EINVAL (bad range or
+ * slices), CD_ECUDA, CD_ETIMEOUT (bounded tensor-core pipeline wait). */
+int cd_mo_vectors(const cd_factor_t* f, const double* C, int32_t n_mo, int64_t P0, int64_t nP, int32_t slices,
+                  double* out, int32_t flags, void* stream);
 
 /* ---- batches of independent systems ---------------------------------------- */
 /* For i < n_sys: cd_system_create(bases[i], opts[i].schwarz), the

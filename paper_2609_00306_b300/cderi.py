@@ -30,7 +30,7 @@ _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENO
 # every symbol declared in include/cderi.h
 EXPORTS = ["cd_system_create", "cd_system_free", "cd_system_info", "cd_system_rows", "cd_eri_columns",
            "cd_eri_factor", "cd_eri_factor_sys", "cd_factor_free", "cd_factor_info", "cd_factor_pivots",
-           "cd_factor_vectors", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_batch_run", "cd_slice_matmul", "cd_last_error", "cd_version"]
+           "cd_factor_vectors", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_last_error", "cd_version"]
 
 
 class CDError(RuntimeError):
@@ -48,7 +48,8 @@ class cd_opts_t(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("schwarz", ctypes.c_double), ("vec_precision", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("max_vectors", ctypes.c_int64), ("mem_budget_gb", ctypes.c_double),
                 ("forced_pivots", ctypes.c_void_p), ("n_forced", ctypes.c_int64),
-                ("update", ctypes.c_int32), ("algorithm", ctypes.c_int32), ("span", ctypes.c_double)]
+                ("update", ctypes.c_int32), ("algorithm", ctypes.c_int32), ("span", ctypes.c_double),
+                ("candidates", ctypes.c_void_p)]
 
 
 _lib = None
@@ -79,6 +80,7 @@ def load(path: Optional[str] = None):
         "cd_factor_stats": (ctypes.c_int, [P, P]),
         "cd_factor_gather": (ctypes.c_int, [P, P, I32, P]),
         "cd_jk": (ctypes.c_int, [P, P, I32, P, P, I32, P]),
+        "cd_mo_vectors": (ctypes.c_int, [P, P, I32, I64, I64, I32, P, I32, P]),
         "cd_kernel_launches": (ctypes.c_longlong, []),
         "cd_batch_run": (ctypes.c_int, [I32, P, P, P, P, P, P, I32, I32, P]),
         "cd_slice_matmul": (ctypes.c_int, [P, I64, I64, P, I64, I64, I64, I32, P, I64, P]),
@@ -124,14 +126,20 @@ class _BasisArgs:
 
 def make_opts(tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
               max_vectors: int = 0, mem_budget_gb: float = 0.0, forced: Optional[Sequence[int]] = None,
-              update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0):
+              update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0,
+              candidates=None):
     o = cd_opts_t(float(tau), float(schwarz), int(vec_precision), int(block), int(max_vectors),
-                  float(mem_budget_gb), None, 0, int(update), int(algorithm), float(span))
-    keep = None
+                  float(mem_budget_gb), None, 0, int(update), int(algorithm), float(span), None)
+    keep = []
     if forced is not None:
-        keep = np.ascontiguousarray(forced, dtype=np.int64)
-        o.forced_pivots = keep.ctypes.data
-        o.n_forced = int(keep.shape[0])
+        f = np.ascontiguousarray(forced, dtype=np.int64)
+        o.forced_pivots = f.ctypes.data
+        o.n_forced = int(f.shape[0])
+        keep.append(f)
+    if candidates is not None:
+        c = np.ascontiguousarray(candidates, dtype=np.uint8)
+        o.candidates = c.ctypes.data
+        keep.append(c)
     return o, keep
 
 
@@ -236,6 +244,23 @@ class Factor:
                             _p(K) if K is not None else None, int(flags), _stream(stream)))
         return J, K
 
+    def mo_vectors(self, C, P0: int = 0, nP: Optional[int] = None, slices: int = 7, stream=None) -> np.ndarray:
+        """[nP, n_mo, n_mo] Cholesky vectors in the MO basis C [N, n_mo] (C ABI cd_mo_vectors)."""
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        nP = self.M - P0 if nP is None else int(nP)
+        out = np.zeros((max(nP, 0), C.shape[1], C.shape[1]))
+        _check(load().cd_mo_vectors(self._h, _p(C), int(C.shape[1]), int(P0), int(nP), int(slices), _p(out), 0,
+                                    _stream(stream)))
+        return out
+
+    def mo_vectors_device(self, C_dev, out_dev, P0: int = 0, slices: int = 7, stream=None):
+        """Same, with torch CUDA tensors C [N, n_mo] and out [nP, n_mo, n_mo] (float64)."""
+        assert C_dev.is_cuda and out_dev.is_cuda and C_dev.dtype == out_dev.dtype
+        n_mo = C_dev.shape[1]
+        _check(load().cd_mo_vectors(self._h, ctypes.c_void_p(C_dev.data_ptr()), int(n_mo), int(P0),
+                                    int(out_dev.shape[0]), int(slices), ctypes.c_void_p(out_dev.data_ptr()),
+                                    CD_JK_DEVICE, _stream(stream)))
+
     def jk_device(self, C_dev, J_dev, K_dev, mode: int = CD_JK_FP64, stream=None):
         """J, K into torch CUDA tensors (no host copies)."""
         flags = mode | CD_JK_DEVICE
@@ -262,11 +287,13 @@ class Factor:
 
 def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
                   max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
-                  update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0) -> Factor:
-    """Full pipeline from a host basis (C ABI cd_eri_factor)."""
+                  update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0,
+                  candidates=None) -> Factor:
+    """Full pipeline from a host basis (C ABI cd_eri_factor).  ``candidates``: mask
+    over the screened rows (``System.rows()`` order) of the rows that may be pivots."""
     args = _BasisArgs(basis)
     o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced, update,
-                        algorithm, span)
+                        algorithm, span, candidates)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor(ctypes.byref(args.s), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep
@@ -275,9 +302,12 @@ def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = 
 
 def cd_eri_factor_sys(system: System, tau: float, vec_precision: int = CD_FP64, block: int = 0,
                       max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
-                      update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0) -> Factor:
+                      update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0,
+                      candidates=None) -> Factor:
+    if candidates is not None and len(candidates) != system.n_rows:
+        raise ValueError("candidates must have one entry per screened row")
     o, keep = make_opts(tau, 0.0, vec_precision, block, max_vectors, mem_budget_gb, forced, update, algorithm,
-                        span)
+                        span, candidates)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor_sys(system._h, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep

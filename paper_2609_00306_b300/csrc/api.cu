@@ -22,6 +22,9 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_counter() { return g_launches.load(); }
 int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st);
+int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N, int n_mo,
+                      const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
+                      cudaStream_t st);
 int jk_mixed(const float* L32, const double* L64, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
              const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
              int S, cudaStream_t st);
@@ -286,6 +289,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   // two-step, first step: compacted rows
   int32_t* rowmap_dev = nullptr;     // [bra.n][9] working row of each bra component (-1 = dropped)
   int64_t* order_dev = nullptr;      // live bra shell pairs, grouped by class
+  uint8_t* cand_dev = nullptr;       // [n] candidate mask (working rows)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   // sliced update runs on a second stream, concurrently with the ERI columns
   // (tensor cores vs FP64 pipe)
@@ -297,7 +301,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
     for (void* p : {(void*)pool, (void*)D0, (void*)D1, (void*)Bg, (void*)slots_dev, (void*)rows_dev,
                     (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Ls, Bs, (void*)Dint,
                     (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals, (void*)eri_ops,
-                    (void*)slot_rows_dev, (void*)slot_vals_dev, (void*)rowmap_dev, (void*)order_dev})
+                    (void*)slot_rows_dev, (void*)slot_vals_dev, (void*)rowmap_dev, (void*)order_dev,
+                    (void*)cand_dev})
       scratch_free(p, st);
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
@@ -402,6 +407,15 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     CD_TRY(launch_row_exp_sqrt(s->diag_dev, n, w.erow, st));
   }
   const int cand_cap = 4 * b;
+  // candidate mask (system rows).  The first step of the two-step scheme drops
+  // the other rows at its first compaction and needs no mask afterwards.
+  const uint8_t* cmask_h = o->candidates;
+  const uint8_t* cmask = nullptr;
+  if (cmask_h && n > 0) {
+    CD_TRY(scratch_alloc(&w.cand_dev, (size_t)n, st));
+    CD_CUDA(cudaMemcpyAsync(w.cand_dev, cmask_h, (size_t)n, cudaMemcpyHostToDevice, st));
+    cmask = w.cand_dev;
+  }
   if (span_mode) {
     CD_TRY(scratch_alloc(&w.slot_rows_dev, (size_t)b, st));
     CD_TRY(scratch_alloc(&w.slot_vals_dev, (size_t)b, st));
@@ -433,7 +447,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   double* Dnext = w.D1;
   StepResult res;
   if (n > 0) {
-    CD_TRY(launch_argmax(Dcur, n, w.sc, w.res_dev, st));
+    CD_TRY(launch_argmax(Dcur, n, w.sc, w.res_dev, st, cmask));
     CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
     CD_CUDA(cudaStreamSynchronize(st));
     res = *w.res_h;
@@ -459,7 +473,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     CD_CUDA(cudaStreamSynchronize(st));
     std::vector<int32_t> idx;
     for (int64_t r = 0; r < n; ++r)
-      if (dh[r] >= tau) idx.push_back((int32_t)r);
+      if (dh[r] >= tau && (!cmask_h || cmask_h[r])) idx.push_back((int32_t)r);
     const int64_t m = (int64_t)idx.size();
     if (!force && 4 * m >= 3 * n) return CD_OK;
     const int64_t ldm = std::max<int64_t>(32, (m + 31) / 32 * 32);
@@ -547,6 +561,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     ld = ldm;
     f->n = n;
     f->ld = ld;
+    cmask_h = nullptr;  // every working row is a candidate now
+    cmask = nullptr;
     if (n > 0) {
       CD_TRY(launch_argmax(Dcur, n, w.sc, w.res_dev, st));
       CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
@@ -584,7 +600,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         if (std::find(cand.begin(), cand.end(), o->forced_pivots[k]) == cand.end()) cand.push_back(o->forced_pivots[k]);
     } else {
       // the b largest residual diagonals >= tau (radix select on the device)
-      CD_TRY(launch_select(Dcur, n, thr, b, w.sel, w.cand_rows, w.cand_vals, cand_cap, st));
+      CD_TRY(launch_select(Dcur, n, thr, b, w.sel, w.cand_rows, w.cand_vals, cand_cap, st, cmask));
       CD_CUDA(cudaMemcpyAsync(w.cand_count_h, &w.sel->count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
       CD_CUDA(cudaMemcpyAsync(w.cand_rows_h.data(), w.cand_rows, sizeof(int64_t) * cand_cap, cudaMemcpyDeviceToHost, st));
       CD_CUDA(cudaMemcpyAsync(w.cand_vals_h.data(), w.cand_vals, sizeof(double) * cand_cap, cudaMemcpyDeviceToHost, st));
@@ -598,7 +614,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         CD_CUDA(cudaMemcpyAsync(w.dh.data(), Dcur, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         CD_CUDA(cudaStreamSynchronize(st));
         for (int64_t r = 0; r < n; ++r)
-          if (w.dh[r] >= thr) c.emplace_back(w.dh[r], r);
+          if (w.dh[r] >= thr && (!cmask_h || cmask_h[r])) c.emplace_back(w.dh[r], r);
       }
       auto cmp = [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
         return x.first > y.first || (x.first == y.first && x.second < y.second);
@@ -756,7 +772,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       }
       const double gap = forced ? res.dmax - dp : 0.0;
       CD_TRY(launch_finalize(w.pool + (int64_t)sl * ld, f->L, ld, Kb, K, p, Dcur, Dnext, f->L + K * ld, n, neg_tol,
-                             w.sc, w.res_dev, st));
+                             w.sc, w.res_dev, st, cmask));
       CD_CUDA(cudaMemcpyAsync(w.res_h, w.res_dev, sizeof(StepResult), cudaMemcpyDeviceToHost, st));
       if (span_mode) {
         CD_TRY(launch_gather_vals(Dnext, w.slot_rows_dev, b, w.slot_vals_dev, st));
@@ -1131,6 +1147,70 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
   return fail(CD_OK);
 }
 
+
+int cd_mo_vectors(const cd_factor_t* f, const double* C, int32_t n_mo, int64_t P0, int64_t nP, int32_t slices,
+                  double* out, int32_t flags, void* stream) {
+  if (!f || !C || !out || n_mo <= 0 || P0 < 0 || nP < 0 || P0 + nP > f->M) {
+    set_error("cd_mo_vectors: bad argument");
+    return CD_EINVAL;
+  }
+  if (slices != 0 && slices != 3 && slices != 4 && slices != 5 && slices != 7) {
+    set_error("cd_mo_vectors: slices must be 0 (FP64), 3, 4, 5 or 7");
+    return CD_EINVAL;
+  }
+  if (nP == 0) return CD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = f->sys->hb.nbf;
+  const int64_t n = f->n, ld = f->ld;
+  const bool dev = (flags & CD_JK_DEVICE) != 0;
+  const size_t out_elems = (size_t)nP * n_mo * n_mo;
+  double *dC = nullptr, *dOut = nullptr, *U = nullptr, *B = nullptr;
+  auto done = [&](int code) {
+    if (!dev) { scratch_free(dC, st); scratch_free(dOut, st); }
+    scratch_free(U, st);
+    scratch_free(B, st);
+    cudaStreamSynchronize(st);
+    return code;
+  };
+  int rc = CD_OK;
+  if (dev) {
+    dC = const_cast<double*>(C);
+    dOut = out;
+  } else {
+    if ((rc = scratch_alloc(&dC, (size_t)N * n_mo, st)) != CD_OK) return done(rc);
+    if ((rc = scratch_alloc(&dOut, out_elems, st)) != CD_OK) return done(rc);
+    if (cudaMemcpyAsync(dC, C, sizeof(double) * N * n_mo, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_error("cd_mo_vectors: copy of C failed");
+      return done(CD_ECUDA);
+    }
+  }
+  if (slices > 0) {
+    rc = mo_vectors_sliced(f->L, ld, P0, nP, n, N, n_mo, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, slices, dOut, st);
+    if (rc != CD_OK) return done(rc);
+  } else {
+    // FP64: per chunk of vectors, U^P = unpack(L^P), B^P = U^P C, out^P = C^T B^P
+    const double perP = 8.0 * ((double)N * N + (double)N * n_mo);
+    const int Pc = (int)std::max<double>(1.0, std::min<double>((double)nP, 1.5e9 / perP));
+    if ((rc = scratch_alloc(&U, (size_t)Pc * N * N, st)) != CD_OK) return done(rc);
+    if ((rc = scratch_alloc(&B, (size_t)Pc * N * n_mo, st)) != CD_OK) return done(rc);
+    for (int64_t Q0 = P0; Q0 < P0 + nP; Q0 += Pc) {
+      const int pc = (int)std::min<int64_t>(Pc, P0 + nP - Q0);
+      if ((rc = launch_unpack_vectors<double>(f->L, ld, Q0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, U, st)) != CD_OK)
+        return done(rc);
+      if ((rc = launch_dgemm(N, n_mo, N, pc, 1.0, U, N, 1, (int64_t)N * N, dC, n_mo, 1, 0, B, n_mo,
+                             (int64_t)N * n_mo, false, st)) != CD_OK)
+        return done(rc);
+      double* o = dOut + (Q0 - P0) * (int64_t)n_mo * n_mo;
+      if ((rc = launch_dgemm(n_mo, n_mo, N, pc, 1.0, dC, 1, n_mo, 0, B, n_mo, 1, (int64_t)N * n_mo, o, n_mo,
+                             (int64_t)n_mo * n_mo, false, st)) != CD_OK)
+        return done(rc);
+    }
+  }
+  if (!dev && cudaMemcpyAsync(out, dOut, sizeof(double) * out_elems, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return done(CD_ECUDA);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { set_error("cd_mo_vectors: CUDA failure"); return done(CD_ECUDA); }
+  return done(CD_OK);
+}
 
 // ---------------------------------------------------------------- batch ----
 // Many independent systems: a pool of host workers, each driving its own

@@ -110,7 +110,8 @@ int launch_slice3(const T* X, int64_t ldx, int64_t rows, int64_t k, const int32_
   const unsigned grid = (unsigned)((tot + 255) / 256);
   if (S == 3) slice_kernel<T, 3><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
   else if (S == 4) slice_kernel<T, 4><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
-  else slice_kernel<T, 5><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
+  else if (S == 5) slice_kernel<T, 5><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
+  else slice_kernel<T, 7><<<grid, 256, 0, st>>>(X, ldx, rows, k, e, (__nv_bfloat16*)dst, kpitch);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -281,6 +282,106 @@ int jk_mixed_t(const TL* L32, int64_t ld, int64_t M, int64_t n, int N, int O, co
     if (herr) { set_error("mixed K: a bounded tensor-core pipeline wait timed out"); return CD_ETIMEOUT; }
   }
   CD_CUDA(cudaStreamSynchronize(st));
+  return CD_OK;
+}
+
+namespace {
+// Bt[(p*n_mo + i)*Np + mu] = B^P[mu][i] from the fixed-point product D[i][p*N + mu]
+__global__ void mo_half_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int Pc, int N, int n_mo,
+                               int64_t Np, const int32_t* __restrict__ eL, const int32_t* __restrict__ eC, int F,
+                               double* __restrict__ Bt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)Pc * N * n_mo) return;
+  const int i = (int)(t % n_mo);
+  const int64_t row = t / n_mo;  // p*N + mu
+  const int p = (int)(row / N), mu = (int)(row % N);
+  Bt[((int64_t)p * n_mo + i) * Np + mu] = ldexp((double)(long long)D[(int64_t)i * ldd + row], eL[row] + eC[i] - F);
+}
+// out[p][i][j] = 2^(eB[p*n_mo+i] + eC[j] - F) * D[(p*n_mo + i)][j]
+__global__ void mo_out_kernel(const unsigned long long* __restrict__ D, int Pc, int n_mo,
+                              const int32_t* __restrict__ eB, const int32_t* __restrict__ eC, int F,
+                              double* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)Pc * n_mo * n_mo) return;
+  const int j = (int)(t % n_mo);
+  const int64_t row = t / n_mo;  // p*n_mo + i
+  out[t] = ldexp((double)(long long)D[t], eB[row] + eC[j] - F);
+}
+}  // namespace
+
+// CV -> MO transformation (Sec. 4.1: the vectors transformed to the MO basis
+// for CASSCF / CC), out[P - P0][i][j] = sum_{mu nu} C[mu][i] L^P_{mu nu} C[nu][j],
+// as two exact-slice products per chunk of vectors: B^P = L^P C, then C^T B^P.
+int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N, int n_mo,
+                      const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
+                      cudaStream_t st) {
+  if (nP <= 0) return CD_OK;
+  const int64_t Np = (N + 7) / 8 * 8;
+  int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(nP, (int64_t)(1.5e9 / ((8.0 + 2.0 * S) * N * (double)N))));
+  Pc = std::min(Pc, 64);
+  MixedBufs b;
+  b.st = st;
+  unsigned long long* D3 = nullptr;
+  int32_t* eBt = nullptr;
+  struct Extra {
+    cudaStream_t st;
+    unsigned long long** d3;
+    int32_t** e;
+    ~Extra() { scratch_free(*d3, st); scratch_free(*e, st); }
+  } extra{st, &D3, &eBt};
+  CD_TRY(scratch_alloc((double**)&b.Lfull, (size_t)Pc * N * N, st));
+  CD_TRY(scratch_alloc((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np, st));
+  CD_TRY(scratch_alloc((uint16_t**)&b.Cs, (size_t)S * n_mo * Np, st));
+  CD_TRY(scratch_alloc(&b.Ct, (size_t)n_mo * N, st));
+  CD_TRY(scratch_alloc(&b.eL, (size_t)Pc * N, st));
+  CD_TRY(scratch_alloc(&b.eC, (size_t)n_mo, st));
+  CD_TRY(scratch_alloc(&eBt, (size_t)Pc * n_mo, st));
+  CD_TRY(scratch_alloc(&b.D1, (size_t)n_mo * Pc * N, st));
+  CD_TRY(scratch_alloc(&D3, (size_t)Pc * n_mo * n_mo, st));
+  CD_TRY(scratch_alloc(&b.Bm, (size_t)Pc * n_mo * Np, st));
+  CD_TRY(scratch_alloc((uint16_t**)&b.Bs, (size_t)S * Pc * n_mo * Np, st));
+  CD_TRY(scratch_alloc(&b.err, 1, st));
+  CD_CUDA(cudaMemsetAsync(b.err, 0, sizeof(int), st));
+  transpose_kernel<<<(unsigned)(((int64_t)N * n_mo + 255) / 256), 256, 0, st>>>(C_dev, N, n_mo, b.Ct);
+  count_launch();
+  CD_TRY(launch_row_exp_warp<double>(b.Ct, N, n_mo, N, b.eC, st));
+  CD_TRY(launch_slice3<double>(b.Ct, N, n_mo, N, b.eC, b.Cs, Np, S, st));
+  OzakiPlan pl;
+  pl.SA = pl.SB = S;
+  pl.KEEP = S + 1;
+  pl.F = 61 - ilog2_ceil(N);
+  for (int64_t Q0 = P0; Q0 < P0 + nP; Q0 += Pc) {
+    const int pc = (int)std::min<int64_t>(Pc, P0 + nP - Q0);
+    double* Lf = (double*)b.Lfull;
+    CD_TRY(launch_unpack_vectors<double>(L, ld, Q0, pc, mu, nu, n, N, Lf, st));
+    CD_TRY(launch_row_exp_warp<double>(Lf, N, (int64_t)pc * N, N, b.eL, st));
+    CD_TRY(launch_slice3<double>(Lf, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+    // B^P[mu][i]: D1[i][p*N + mu]
+    CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * n_mo * pc * N, st));
+    CD_TRY(ozaki_gemm(pl, b.Ls, (int64_t)pc * N, Np, b.Cs, n_mo, Np, N, b.D1, (int64_t)pc * N, 1, b.err, st));
+    CD_CUDA(cudaMemsetAsync(b.Bm, 0, sizeof(double) * pc * n_mo * Np, st));
+    {
+      const int64_t tot = (int64_t)pc * N * n_mo;
+      mo_half_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(b.D1, (int64_t)pc * N, pc, N, n_mo, Np, b.eL,
+                                                                    b.eC, pl.F, b.Bm);
+      count_launch();
+    }
+    // (C^T B^P)[i][j] = sum_mu B^P[mu][i] C[mu][j]: rows (p, i) of Bt against rows j of C^T
+    CD_TRY(launch_row_exp_warp<double>(b.Bm, Np, (int64_t)pc * n_mo, N, eBt, st));
+    CD_TRY(launch_slice3<double>(b.Bm, Np, (int64_t)pc * n_mo, N, eBt, b.Bs, Np, S, st));
+    CD_CUDA(cudaMemsetAsync(D3, 0, sizeof(unsigned long long) * pc * n_mo * n_mo, st));
+    CD_TRY(ozaki_gemm(pl, b.Cs, n_mo, Np, b.Bs, (int64_t)pc * n_mo, Np, N, D3, n_mo, 1, b.err, st));
+    {
+      const int64_t tot = (int64_t)pc * n_mo * n_mo;
+      mo_out_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(D3, pc, n_mo, eBt, b.eC, pl.F,
+                                                                   out_dev + (Q0 - P0) * (int64_t)n_mo * n_mo);
+      count_launch();
+    }
+  }
+  int herr = 0;
+  CD_CUDA(cudaMemcpyAsync(&herr, b.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CD_CUDA(cudaStreamSynchronize(st));
+  if (herr) { set_error("MO transform: a bounded tensor-core pipeline wait timed out"); return CD_ETIMEOUT; }
   return CD_OK;
 }
 

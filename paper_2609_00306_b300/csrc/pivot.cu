@@ -79,12 +79,13 @@ __device__ void grid_finish(double v, int64_t i, int bad, StepScratch* sc, StepR
 }
 
 __global__ void __launch_bounds__(kStepThreads) argmax_kernel(const double* __restrict__ D, int64_t n,
+                                                              const uint8_t* __restrict__ cand,
                                                               StepScratch* sc, StepResult* res) {
   double bv = -DBL_MAX;
   int64_t bi = INT64_MAX;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     double d = D[r];
-    if (better(d, r, bv, bi)) { bv = d; bi = r; }
+    if ((!cand || cand[r]) && better(d, r, bv, bi)) { bv = d; bi = r; }
   }
   block_argmax(bv, bi);
   grid_finish(bv, bi, 0, sc, res);
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(kStepThreads) argmax_kernel(const double* __re
 __global__ void __launch_bounds__(kStepThreads) finalize_kernel(
     const double* __restrict__ col, const double* __restrict__ L, int64_t ld, int64_t Kb, int64_t K,
     int64_t prow, const double* __restrict__ Din, double* __restrict__ Dout, double* __restrict__ Lout,
-    int64_t n, double neg_tol, StepScratch* sc, StepResult* res) {
+    int64_t n, double neg_tol, const uint8_t* __restrict__ cand, StepScratch* sc, StepResult* res) {
   __shared__ double g[kMaxBlock];
   const int nk = (int)(K - Kb);
   for (int k = threadIdx.x; k < nk; k += blockDim.x) g[k] = L[(Kb + k) * ld + prow];
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(kStepThreads) finalize_kernel(
     const double d = fma(-v, v, Din[r]);
     Dout[r] = d;
     if (d < neg_tol) bad = 1;
-    if (better(d, r, bv, bi)) { bv = d; bi = r; }
+    if ((!cand || cand[r]) && better(d, r, bv, bi)) { bv = d; bi = r; }
   }
   block_argmax(bv, bi);
   grid_finish(bv, bi, bad, sc, res);
@@ -213,8 +214,8 @@ int launch_gather_vals(const double* D, const int64_t* rows, int nb, double* out
   return CD_OK;
 }
 
-int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st) {
-  argmax_kernel<<<kStepGrid, kStepThreads, 0, st>>>(D, n, sc, res);
+int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st, const uint8_t* cand) {
+  argmax_kernel<<<kStepGrid, kStepThreads, 0, st>>>(D, n, cand, sc, res);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -222,9 +223,10 @@ int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, 
 
 int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, int64_t K, int64_t prow,
                     const double* Din, double* Dout, double* Lout, int64_t n, double neg_tol,
-                    StepScratch* sc, StepResult* res, cudaStream_t st) {
+                    StepScratch* sc, StepResult* res, cudaStream_t st, const uint8_t* cand) {
   if (K - Kb > kMaxBlock) { set_error("finalize: block too large"); return CD_EINVAL; }
-  finalize_kernel<<<kStepGrid, kStepThreads, 0, st>>>(col, L, ld, Kb, K, prow, Din, Dout, Lout, n, neg_tol, sc, res);
+  finalize_kernel<<<kStepGrid, kStepThreads, 0, st>>>(col, L, ld, Kb, K, prow, Din, Dout, Lout, n, neg_tol, cand, sc,
+                                                      res);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -255,7 +257,7 @@ __device__ __forceinline__ unsigned long long dkey(double d, double tau) {
 }
 
 __global__ void __launch_bounds__(256) select_pass_kernel(const double* __restrict__ D, int64_t n, double tau, int pass,
-                                                          int b, SelectState* stt) {
+                                                          int b, SelectState* stt, const uint8_t* __restrict__ cand) {
   __shared__ unsigned sh[256];
   __shared__ bool last;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) sh[i] = 0;
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const double* __restri
   const unsigned long long prefix = stt->prefix, mask = stt->mask;
   const int shift = 56 - 8 * pass;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long k = dkey(D[r], tau);
+    const unsigned long long k = (cand && !cand[r]) ? 0ull : dkey(D[r], tau);
     if (k != 0ull && (k & mask) == prefix) atomicAdd(&sh[(k >> shift) & 255ull], 1u);
   }
   __syncthreads();
@@ -306,12 +308,13 @@ __global__ void __launch_bounds__(256) select_pass_kernel(const double* __restri
 
 __global__ void __launch_bounds__(256) select_compact_kernel(const double* __restrict__ D, int64_t n, double tau,
                                                              SelectState* stt, int64_t* __restrict__ rows_out,
-                                                             double* __restrict__ vals_out, int cap) {
+                                                             double* __restrict__ vals_out, int cap,
+                                                             const uint8_t* __restrict__ cand) {
   const unsigned long long thr = stt->all ? (stt->prefix & stt->mask) : stt->prefix;
   const bool all = stt->all != 0;
   const unsigned long long mask = stt->mask, prefix = stt->prefix;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long k = dkey(D[r], tau);
+    const unsigned long long k = (cand && !cand[r]) ? 0ull : dkey(D[r], tau);
     if (k == 0ull) continue;
     const bool take = all ? ((k & mask) >= prefix) : (k >= thr);
     if (take) {
@@ -324,13 +327,13 @@ __global__ void __launch_bounds__(256) select_compact_kernel(const double* __res
 }  // namespace
 
 int launch_select(const double* D, int64_t n, double tau, int b, SelectState* stt, int64_t* rows_out,
-                  double* vals_out, int cap, cudaStream_t st) {
+                  double* vals_out, int cap, cudaStream_t st, const uint8_t* cand) {
   CD_CUDA(cudaMemsetAsync(stt, 0, sizeof(SelectState), st));
   for (int pass = 0; pass < 8; ++pass) {
-    select_pass_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, pass, b, stt);
+    select_pass_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, pass, b, stt, cand);
     count_launch();
   }
-  select_compact_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, stt, rows_out, vals_out, cap);
+  select_compact_kernel<<<kStepGrid, 256, 0, st>>>(D, n, tau, stt, rows_out, vals_out, cap, cand);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;

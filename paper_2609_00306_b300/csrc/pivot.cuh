@@ -22,7 +22,9 @@ struct StepScratch {       // device scratch of the grid-wide argmax
   int bad;
 };
 
-int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st);
+// cand (optional, [n]): rows with cand[r] == 0 are not candidates for the argmax / the selection
+int launch_argmax(const double* D, int64_t n, StepScratch* sc, StepResult* res, cudaStream_t st,
+                  const uint8_t* cand = nullptr);
 
 // radix select of the b largest D >= tau (see pivot.cu)
 struct SelectState {
@@ -35,10 +37,10 @@ struct SelectState {
   unsigned hist[8][256];
 };
 int launch_select(const double* D, int64_t n, double tau, int b, SelectState* stt, int64_t* rows_out,
-                  double* vals_out, int cap, cudaStream_t st);
+                  double* vals_out, int cap, cudaStream_t st, const uint8_t* cand = nullptr);
 int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, int64_t K, int64_t prow,
                     const double* Din, double* Dout, double* Lout, int64_t n, double neg_tol,
-                    StepScratch* sc, StepResult* res, cudaStream_t st);
+                    StepScratch* sc, StepResult* res, cudaStream_t st, const uint8_t* cand = nullptr);
 int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
                   double* Bg, cudaStream_t st);
 
