@@ -58,7 +58,7 @@ def _args():
     ap.add_argument("--no-jk-alone", action="store_true", help="skip the separate J/K timings (FP64 K is slow)")
     ap.add_argument("--jk-alone-modes", default="all",
                     help="comma list of J/K modes timed separately after the step (default: all)")
-    ap.add_argument("--cpu-sample-steps", type=int, default=8)
+    ap.add_argument("--cpu-sample-steps", type=int, default=48)
     ap.add_argument("--measure-fp64-peak", action="store_true",
                     help="compile and run the FP64 DFMA/DMMA microbenchmark, print its JSON line")
     return ap.parse_args()
@@ -175,6 +175,17 @@ def _sliced(f) -> bool:
 
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest per-step time over the ranks of the process group (replicas: one
+    independent system per GPU, the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_2609_00306_b300 as cd
@@ -233,11 +244,7 @@ def run_ours(args, rank, world):
                 f.free()
                 del f
     launches = cd.kernel_launches() - launches0
-    ms = tot_ms / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(tot_ms / args.steps, world, dev)
     st = {k: float(np.mean([x[k] for x in stats])) for k in stats[0]}
     # J and K alone, both modes, on the last step's factor (device buffers), and
     # the mixed-precision error against the FP64 contraction of the same vectors
@@ -272,6 +279,13 @@ def run_ours(args, rank, world):
             }
             if jk.get("fp64_ms") and jk.get(mx + "_ms"):
                 jk[mx + "_speedup_over_fp64"] = jk["fp64_ms"] / jk[mx + "_ms"]
+    # what the report needs from the step's factor; then free it before the
+    # other factorisations (its vectors are tens of GB)
+    n_rows = f.n_rows
+    sliced = st.get("ms_colupd", 0) > 0 and _sliced(f)
+    f.free()
+    del f
+    torch.cuda.synchronize()
     # the other pivot policies, one factorisation each (same system, same tau)
     other_algs = {}
     for name, alg in algs.items():
@@ -297,7 +311,6 @@ def run_ours(args, rank, world):
     peak_fp64 = 148 * 2 * 2 * 2.032e9 / 1e12  # TFLOP/s: 148 SMs x 2 DFMA/clk x 2 flop x 2032 MHz
     peak_fp64_ops = 148 * 2 * 2.032e9 / 1e12  # T FP64-pipe operations/s (one DFMA/DMUL/DADD each)
     peaks = _measured_peaks()
-    sliced = st.get("ms_colupd", 0) > 0 and _sliced(f)
     upd_fp64eq = st["colupd_flops"] / (st["ms_colupd"] * 1e-3) / 1e12 if st["ms_colupd"] > 0 else None
     if sliced:
         # 28 BF16 slice products (s + t <= 8 of 7 x 7) per FP64-equivalent multiply-add
@@ -335,7 +348,7 @@ def run_ours(args, rank, world):
            "data": "synthetic (seeded lattice s+p system; no public dataset)",
            "config": {"workload": f"{args.workload}: N={N} s+p, {s.basis.n_shells} shells, tau={s.tau:g}, "
                                   f"Schwarz {s.schwarz:g}, n_occ={O}",
-                      "n_basis": N, "rows": f.n_rows, "M": M, "max_resid": resid, "jk_mode": args.jk,
+                      "n_basis": N, "rows": n_rows, "M": M, "max_resid": resid, "jk_mode": args.jk,
                       "algorithm": args.algorithm + ("" if args.algorithm == "full" else f" (span {args.span:g})"),
                       "update": "sliced tensor-core (7 x 8-bit slices)" if sliced else "FP64 DFMA",
                       "l2": "inputs (vectors, 10s of GB) larger than L2; 256 MB flush between steps",
@@ -346,7 +359,6 @@ def run_ours(args, rank, world):
                             "eri_fp64_ops": st.get("eri_fp64_ops", 0.0)},
            "jk_alone_ms": jk, "pivot_policies": other_algs,
            "roofline": roof, other_key: roof_other, "gpu_launches": int(launches), "clocks": clk.summary()}
-    f.free()
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         torch.cuda.synchronize()
