@@ -176,7 +176,8 @@ int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, d
  * columns x vectors applied), [9] ERI column entries computed, [10] M;
  * [11] 1 if the sliced tensor-core update ran; [12] FP64-pipe operations of
  * the ERI column kernels (counted by the kernels from per-primitive-quartet
- * operation counts of their recurrences); [13..15] reserved (0). */
+ * operation counts of their recurrences); [13] first-step ms, [14] first-step
+ * macro iterations, [15] first-step ERI columns of CD_ALG_TWOSTEP (0 otherwise). */
 int cd_factor_stats(const cd_factor_t* f, double* stats16);
 /* Number of CUDA kernel launches issued by this library in this process. */
 long long cd_kernel_launches(void);

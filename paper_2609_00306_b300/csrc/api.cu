@@ -291,8 +291,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   int64_t* order_dev = nullptr;      // live bra shell pairs, grouped by class
   uint8_t* cand_dev = nullptr;       // [n] candidate mask (working rows)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-  // sliced update runs on a second stream, concurrently with the ERI columns
-  // (tensor cores vs FP64 pipe)
+  // second stream for the sliced update, used only with CDERI_OVERLAP_UPDATE=1
+  // (by default the update runs on the main stream before the ERI columns)
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_ready = nullptr, ev_gemm = nullptr, ev_g0 = nullptr, ev_g1 = nullptr;
   std::vector<int32_t> upd_slots;
