@@ -112,16 +112,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle ---
-def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 16384, sub_steps: int = 240):
+def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 4096, sub_steps: int = 600):
     """Time the CPU oracle on a bounded sample of the workload and project it.
 
     Sample (all on the same N=2000 system, oracle as it stands):
       1. the Schwarz screening pass (diagonal of every pair);
       2. the first k pivot steps over all rows: per-step cost a (one ERI
          column over all rows, the update is negligible at small K);
-      3. the first k1 and k2 steps of the decomposition restricted to the first
-         `sub_rows` rows: per-step cost a' + b' K, giving the update cost b'
-         per vector per step, scaled by rows / sub_rows;
+      3. the decomposition restricted to the first `sub_rows` rows, up to
+         `sub_steps` steps (K of them), timed whole, minus the time of the same
+         K ERI columns alone: the remainder is the update, sum_k b' k =
+         b' K^2 / 2, giving the update cost b' per vector per step, scaled by
+         rows / sub_rows;
       4. the J/K contraction of 2 vectors (per-vector cost c).
     Projection to one full step: t_screen + M a + b M^2 / 2 + M c, with M the
     vector count of the full decomposition.
@@ -138,14 +140,14 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 16384, sub_
     r = o.cd(rows, system.tau, max_steps=k_steps)
     a = (time.perf_counter() - t) / k_steps
     sub = rows[:min(sub_rows, n)]
-    k1, k2 = sub_steps // 3, sub_steps
     t = time.perf_counter()
-    o.cd(sub, system.tau, max_steps=k1)
-    T1 = time.perf_counter() - t
+    rs = o.cd(sub, system.tau, max_steps=sub_steps)
+    T_cd = time.perf_counter() - t
+    K_sub = max(rs.M, 1)
     t = time.perf_counter()
-    o.cd(sub, system.tau, max_steps=k2)
-    T2 = time.perf_counter() - t
-    b_sub = max(0.0, 2.0 * (T2 / k2 - T1 / k1) / (k2 - k1))
+    o.eri_matrix(sub, sub[rs.piv])            # the same K_sub ERI columns alone
+    T_eri = time.perf_counter() - t
+    b_sub = max(0.0, 2.0 * (T_cd - T_eri) / K_sub ** 2)
     b = b_sub * n / sub.shape[0]
     t = time.perf_counter()
     oracle.jk_from_vectors(r.L[:2], rows, system.C_occ)
@@ -155,8 +157,9 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 16384, sub_
     return {
         "value": proj, "unit": "s", "cores": cores, "kind": "oracle",
         "sample": (f"oracle on the N=2000 system: screening ({t_screen:.2f}s), first {k_steps} pivot steps over "
-                   f"all {n} rows (a={a:.3g}s/step), first {k1}/{k2} steps on the first {sub.shape[0]} rows "
-                   f"(update b={b:.3g}s per vector per step after scaling), J/K of 2 vectors (c={c:.3g}s each); "
+                   f"all {n} rows (a={a:.3g}s/step), {K_sub} steps on the first {sub.shape[0]} rows "
+                   f"({T_cd:.2f}s, of which its ERI columns alone {T_eri:.2f}s: update b={b:.3g}s per vector "
+                   f"per step after scaling), J/K of 2 vectors (c={c:.3g}s each); "
                    f"projected to M={M_full}: t_screen + M a + b M^2/2 + M c; sample wall {sample_s:.1f}s"),
         "sample_wall_s": sample_s, "model": {"t_screen": t_screen, "a": a, "b": b, "c": c},
     }
