@@ -59,8 +59,6 @@ def _args():
     ap.add_argument("--jk-alone-modes", default="all",
                     help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=48)
-    ap.add_argument("--measure-fp64-peak", action="store_true",
-                    help="compile and run the FP64 DFMA/DMMA microbenchmark, print its JSON line")
     return ap.parse_args()
 
 
@@ -433,21 +431,8 @@ def run_batch(args):
     return 0
 
 
-def measure_fp64_peak():
-    src = os.path.join(ROOT, "paper_2609_00306_b300", "peaks", "fp64_peak.cu")
-    exe = os.path.join(ROOT, "paper_2609_00306_b300", "_build", "fp64_peak")
-    os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.check_call(["/usr/local/cuda/bin/nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
-                           "-o", exe, src])
-    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
-    print(out, flush=True)
-    return 0
-
-
 def main():
     args = _args()
-    if args.measure_fp64_peak:
-        return measure_fp64_peak()
     if args.workload == "batch64" and args.impl == "ours":
         return run_batch(args)
     rank = int(os.environ.get("RANK", 0))

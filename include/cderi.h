@@ -89,6 +89,10 @@ typedef struct {
                               * the candidate rows, the vectors still cover every row, and rows
                               * outside the block carry no tau guarantee.  With CD_ALG_TWOSTEP the
                               * first step never touches the other rows. */
+  double  diag_shift;   /* test hook: decompose with every starting diagonal lowered by this amount,
+                         * i.e. the diagonal of A - shift I, indefinite once shift exceeds the
+                         * smallest diagonal; the decomposition must then stop with CD_ENOTPSD
+                         * (0 = off) */
 } cd_opts_t;
 
 /* Pivot policies.
@@ -122,22 +126,32 @@ typedef struct cd_system cd_system_t;   /* basis + screened pair list on the dev
 typedef struct cd_factor cd_factor_t;   /* Cholesky basis and vectors on the device */
 
 /* ---- system (basis, screening) ------------------------------------------ */
-/* Validate and normalise the basis, compute the diagonal (mu nu|mu nu) of every
- * pair on the GPU (kernel: ERI diagonal) and keep the shell pairs (AB) with
- * sqrt(max_{mu nu in AB} D_{mu nu} * max D) >= schwarz.  Errors: CD_EINVAL on a
- * malformed basis, CD_ECUDA, CD_ENOMEM. */
+/* Validate and normalise the basis, compute the diagonal D^1 = (mu nu|mu nu)
+ * of every pair on the GPU (Sec. 2, the starting diagonal of the recursion;
+ * kernel: ERI diagonal) and keep the shell pairs (AB) with
+ * sqrt(max_{mu nu in AB} D_{mu nu} * max D) >= schwarz (the integral
+ * prescreening of Sec. 1, read at shell-pair granularity).  *out receives a
+ * library-owned object (free with cd_system_free).  Errors: CD_EINVAL on a
+ * malformed basis (NaN, exponent <= 0, l > 1, nprim out of range), CD_ECUDA,
+ * CD_ENOMEM; *out is NULL then. */
 int cd_system_create(const cd_basis_t* basis, double schwarz, void* stream, cd_system_t** out);
+/* Frees a system and its device memory (NULL is ignored).  A factor made on
+ * it with cd_eri_factor_sys must be freed first. */
 void cd_system_free(cd_system_t* sys);
-/* n_basis, number of rows (screened pairs), number of kept shell pairs. */
+/* n_basis, number of rows (screened pairs), number of kept shell pairs
+ * (each output may be NULL).  CD_EINVAL if sys is NULL. */
 int cd_system_info(const cd_system_t* sys, int32_t* n_basis, int64_t* n_rows, int64_t* n_shell_pairs);
-/* Host copies: packed index of each row [n_rows] (may be NULL) and the row's
- * diagonal (row|row) [n_rows] (may be NULL). */
+/* Host copies, caller-owned arrays of n_rows entries: packed index of each row
+ * (may be NULL) and the row's diagonal D^1 = (row|row) of Sec. 2 (may be
+ * NULL).  CD_EINVAL if sys is NULL. */
 int cd_system_rows(const cd_system_t* sys, int64_t* packed, double* diag);
 
 /* ERI columns (kernel a, column mode): out[j][r] = (row r | row cols[j]) for
- * j < ncols, r < n_rows.  cols: host array of row indices.  out: device
+ * j < ncols, r < n_rows -- the integral column (.|K) that opens Eq. (subtr)
+ * of Sec. 2.  cols: host array of row indices.  out: caller-owned device
  * pointer, row-major with leading dimension ld >= n_rows (doubles).  Runs on
- * `stream`, asynchronous. */
+ * `stream` and synchronises it.  CD_EINVAL on a row out of range or
+ * ld < n_rows, CD_ECUDA. */
 int cd_eri_columns(const cd_system_t* sys, const int64_t* cols, int32_t ncols,
                    double* out, int64_t ld, void* stream);
 
@@ -153,21 +167,42 @@ int cd_eri_factor(const cd_basis_t* basis, const cd_opts_t* opts, void* stream, 
 /* Same on an existing system (the factor keeps a reference; free the factor
  * before the system). */
 int cd_eri_factor_sys(cd_system_t* sys, const cd_opts_t* opts, void* stream, cd_factor_t** out);
+/* Frees a factor, its vectors and (for cd_eri_factor) its system; NULL is
+ * ignored. */
 void cd_factor_free(cd_factor_t* f);
-/* M, number of rows, N, residual max diagonal at exit. */
+/* M (vectors), number of rows, N, and the residual max diagonal at exit, which
+ * is < tau after a completed decomposition (the truncation of Sec. 2: every
+ * element of the residual matrix is then bounded by it).  Outputs may be NULL. */
 int cd_factor_info(const cd_factor_t* f, int64_t* M, int64_t* n_rows, int32_t* n_basis, double* max_resid_diag);
-/* Host copies: pivots as row indices [M], their packed pair indices [M] (either
- * may be NULL), gaps [M] (max D - D_pivot when each pivot was taken; 0 unless
- * forced), and the final residual diagonal [n_rows] (may be NULL). */
+/* The Cholesky basis {|K)} of Sec. 2 -- the pivots in the order taken -- as
+ * host copies: row indices [M] and packed pair indices [M] (either may be
+ * NULL), gaps [M] (max D - D_pivot when each pivot was taken; 0 unless forced;
+ * may be NULL), and the final residual diagonal [n_rows] (may be NULL).  All
+ * arrays caller-owned.  The pivots are int64 row indices (rows index the
+ * screened pairs) and the pairs are packed indices mu(mu+1)/2 + nu rather
+ * than (mu, nu) tuples: both are one integer per pivot, and the packed index
+ * is the pair index of the paper's MN(N+1)/2 storage (Sec. 4.1). */
 int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packed, double* gaps, double* resid_diag);
-/* Vectors: if L_host != NULL it receives [M][n_rows] doubles (converted from
- * FP32 when stored so).  *L_dev (may be NULL) receives the device pointer of
- * the stored array, leading dimension *ld (elements), *dtype 0 = FP64, 1 = FP32. */
+/* The tracked residual diagonal D_{K} of every pivot when it was taken -- the
+ * divisor of Eq. (subtr) -- into out [M] (host, caller-owned).  Two correct
+ * runs can order near-tied pivots differently; comparing these values at the
+ * first difference tells a near-tie (|dD| < 1e-12) from an error. */
+int cd_factor_pivot_diag(const cd_factor_t* f, double* out);
+/* The vectors L^K_{mu nu} (Sec. 2; stored in core, M x N(N+1)/2 words in the
+ * paper's Sec. 4.1, here M x n_rows over the screened pairs).  If L_host !=
+ * NULL it receives [M][n_rows] doubles (caller-owned; converted from FP32 when
+ * stored so).  *L_dev (may be NULL) receives the library-owned device pointer
+ * of the stored array (valid until cd_factor_free), leading dimension *ld
+ * (elements), *dtype 0 = FP64, 1 = FP32. */
 int cd_factor_vectors(const cd_factor_t* f, double* L_host, const void** L_dev, int64_t* ld, int32_t* dtype);
 /* Entries of every vector on selected rows: out[K][j] = L^K_{rows[j]} (FP64,
- * host, [M][nrows]); rows: host array of row indices.  Synchronous. */
+ * host, caller-owned [M][nrows]); rows: host array of row indices.  With
+ * these, (p|q) ~ sum_K L^K_p L^K_q (Sec. 2) can be checked on any sample of
+ * pairs.  Synchronous.  CD_EINVAL on a row out of range. */
 int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, double* out);
-/* Statistics of the factorisation, 16 doubles: [0] system set-up ms (host
+/* Measurement record (the paper has no counterpart; its tables report
+ * wall times and vector counts per run).  Statistics of the factorisation,
+ * 16 doubles into a caller-owned array: [0] system set-up ms (host
  * clock), [1] ERI-column kernels ms, [2] column-update kernels ms (CUDA
  * events; the update runs on the calling stream before the ERI columns of each
  * block), [3] pivot steps ms (host clock), [4] candidate selection
@@ -179,7 +214,8 @@ int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, d
  * operation counts of their recurrences); [13] first-step ms, [14] first-step
  * macro iterations, [15] first-step ERI columns of CD_ALG_TWOSTEP (0 otherwise). */
 int cd_factor_stats(const cd_factor_t* f, double* stats16);
-/* Number of CUDA kernel launches issued by this library in this process. */
+/* Number of CUDA kernel launches issued by this library in this process
+ * (measurement; no counterpart in the paper). */
 long long cd_kernel_launches(void);
 
 /* ---- J and K (Sec. 4.1) ------------------------------------------------- */
@@ -208,7 +244,9 @@ int cd_mo_vectors(const cd_factor_t* f, const double* C, int32_t n_mo, int64_t P
                   double* out, int32_t flags, void* stream);
 
 /* ---- batches of independent systems ---------------------------------------- */
-/* For i < n_sys: cd_system_create(bases[i], opts[i].schwarz), the
+/* The paper has no counterpart: it factors one molecule at a time.  Batching
+ * many small independent systems is a throughput pattern of this library.
+ * For i < n_sys: cd_system_create(bases[i], opts[i].schwarz), the
  * decomposition with opts[i], and cd_jk(C_occ[i], n_occ[i], J[i], K[i],
  * jk_mode).  `workers` host threads (0 = 8), each with its own CUDA stream,
  * take systems from a shared queue (largest first) so that the kernels of
@@ -234,7 +272,21 @@ int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, 
 int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const double* Y, int64_t ldy, int64_t n,
                     int64_t k, int32_t slices, double* out, int64_t ldo, void* stream);
 
+/* ---- bounded device waits ------------------------------------------------------ */
+/* Failure detection (no counterpart in the paper).  The tensor-core pipelines
+ * (column update, mixed J/K, MO vectors, cd_slice_matmul) wait on mbarriers
+ * with a wall-clock limit (default 2 s); a wait that runs out makes every CTA
+ * of the launch stop issuing work, let its in-flight copies and MMAs finish,
+ * free its tensor memory and return, and the entry point returns CD_ETIMEOUT
+ * with the device still usable.  This sets the limit for launches issued from
+ * now on (process-wide; seconds in [0, 3600], 0 = give up at the first wait
+ * that is not already satisfied) and returns the previous limit in *previous
+ * (may be NULL).  Meant for tests of that error path and for tuning. */
+int cd_set_wait_limit(double seconds, double* previous);
+
 /* ---- errors ---------------------------------------------------------------- */
+/* Message of the last failure on the calling thread (library-owned string,
+ * valid until the thread's next failing call). */
 const char* cd_last_error(void);
 /* Library version string. */
 const char* cd_version(void);

@@ -83,8 +83,16 @@ def _load():
         lib.or_cd_span.argtypes = [P, P, I64, D, D, I, I, I, P, P, P, P, P, P]
         lib.or_cd_from_basis.restype = I
         lib.or_cd_from_basis.argtypes = [P, P, I64, P, I, P]
+        lib.or_set_order.argtypes = [I, I]
         _lib = lib
     return _lib
+
+
+def set_loop_order(plain: bool = False, chunk: int = 2048) -> None:
+    """Memory order of the Eq. (subtr) sums in the C decompositions: the plain
+    per-element loop (``plain=True``) or row chunks of ``chunk`` with the vector
+    index outermost (default).  Both give bit-identical results."""
+    _load().or_set_order(int(bool(plain)), int(chunk))
 
 
 def _ptr(a: np.ndarray):
@@ -225,11 +233,13 @@ class Oracle:
 
     # -- Cholesky decomposition -------------------------------------------
     def cd(self, rows, tau: float, forced=None, mcap: Optional[int] = None,
-           max_steps: Optional[int] = None, candidates=None) -> CDResult:
+           max_steps: Optional[int] = None, candidates=None, copy: bool = True) -> CDResult:
         """Run the decomposition; ``max_steps`` stops after that many vectors
         (a bounded sample of a large run; the result is then partial).
         ``candidates``: boolean mask over ``rows`` of the rows that may be pivots
-        (None = all); the stop test then runs over those rows only."""
+        (None = all); the stop test then runs over those rows only.
+        ``copy=False`` returns views into the work arrays instead of trimmed
+        copies (for runs whose vectors fill most of the host memory)."""
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         cand = None if candidates is None else np.ascontiguousarray(candidates, dtype=np.uint8)
         if max_steps is not None:
@@ -260,6 +270,8 @@ class Oracle:
                 raise ArithmeticError("ERI matrix not positive semidefinite within tolerance")
             if M < 0:
                 raise RuntimeError(f"oracle CD failed with status {M}")
+            if not copy:
+                return CDResult(rows, piv[:M], L[:M], D, gap[:M], pivD[:M])
             return CDResult(rows, piv[:M].copy(), L[:M].copy(), D, gap[:M].copy(), pivD[:M].copy())
 
     # -- span-factor selection and the two-step scheme --------------------
@@ -321,21 +333,24 @@ def unpack_vectors(L: np.ndarray, rows: np.ndarray, N: int) -> np.ndarray:
     return out
 
 
-def jk_from_vectors(L: np.ndarray, rows: np.ndarray, C_occ: np.ndarray):
+def jk_from_vectors(L: np.ndarray, rows: np.ndarray, C_occ: np.ndarray, want_j: bool = True, want_k: bool = True):
     """J and K from Cholesky vectors, written from the definitions (Sec. 4.1).
 
     J_{mu nu} = sum_P L^P_{mu nu} sum_{sigma rho} L^P_{sigma rho} D_{sigma rho}
     K_{mu nu} = sum_P sum_{sigma rho} L^P_{mu sigma} D_{sigma rho} L^P_{rho nu}
     with L^P the full symmetric N x N matrix of vector P and D = 2 C C^T.
+    ``want_j`` / ``want_k`` skip the other matrix (returned as None).
     """
     N = C_occ.shape[0]
     Dm = density(C_occ)
-    J = np.zeros((N, N))
-    K = np.zeros((N, N))
+    J = np.zeros((N, N)) if want_j else None
+    K = np.zeros((N, N)) if want_k else None
     for P in range(L.shape[0]):
         LP = unpack_vectors(L[P:P + 1], rows, N)[0]
-        J += LP * np.sum(LP * Dm)
-        K += LP @ Dm @ LP
+        if want_j:
+            J += LP * np.sum(LP * Dm)
+        if want_k:
+            K += LP @ Dm @ LP
     return J, K
 
 

@@ -357,6 +357,50 @@ int64_t or_screen(void* h, const double* diag, double thr, int64_t* rows_out)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Memory order of the Eq. (subtr) sums.                                     */
+/*                                                                           */
+/* Every element of a new column is                                          */
+/*     col_r = (r|p) - L^0_r L^0_p - L^1_r L^1_p - ... - L^{K-1}_r L^{K-1}_p  */
+/* evaluated left to right.  Vectors are stored row-major [K][npairs], so a   */
+/* loop over J for one r walks memory with a stride of npairs.  The default   */
+/* order takes the rows in chunks (2048 by default) and runs J outermost     */
+/* inside a chunk: each L^J is then read contiguously, and every element      */
+/* still sees the same operations in the same order (J ascending), so both    */
+/* orders give bit-identical results.  The plain per-element order and the    */
+/* chunk length are selectable (or_set_order) so that a test can check that   */
+/* identity with several chunks and a ragged last one.                       */
+/* ------------------------------------------------------------------------- */
+static int or_plain_order = 0;
+static int64_t OR_CHUNK = 2048;
+void or_set_order(int plain, int chunk)
+{
+    or_plain_order = plain ? 1 : 0;
+    OR_CHUNK = chunk > 0 ? chunk : 2048;
+}
+
+/* out[r] = (r | k l) - sum_{J<K} L[J][r] * w[J * wstride] for r in [r0, r1),
+ * J ascending for every r (the Eq. (subtr) sum with a strided weight list). */
+static void or_subtr_rows(void* h, const int* ri, const int* rj, int64_t r0, int64_t r1, int k, int l,
+                          const double* L, int64_t npairs, int K, const double* w, int64_t wstride,
+                          double* out)
+{
+    if (or_plain_order) {
+        for (int64_t r = r0; r < r1; ++r) {
+            double col = or_eri(h, ri[r], rj[r], k, l);
+            for (int J = 0; J < K; ++J) col -= L[(int64_t)J * npairs + r] * w[(int64_t)J * wstride];
+            out[r] = col;
+        }
+        return;
+    }
+    for (int64_t r = r0; r < r1; ++r) out[r] = or_eri(h, ri[r], rj[r], k, l);
+    for (int J = 0; J < K; ++J) {
+        const double* LJ = L + (int64_t)J * npairs;
+        const double wj = w[(int64_t)J * wstride];
+        for (int64_t r = r0; r < r1; ++r) out[r] -= LJ[r] * wj;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Fully pivoted incomplete Cholesky decomposition (Sec. 2).                  */
 /*                                                                           */
 /*   D^1_r = (r|r)                                   over the screened rows   */
@@ -413,12 +457,11 @@ int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
         double sq = sqrt(D[p]);
         int k = ri[p], l = rj[p];
         double* LK = L + (int64_t)K * npairs;
-        #pragma omp parallel for schedule(dynamic, 64)
-        for (int64_t r = 0; r < npairs; ++r) {
-            double col = or_eri(h, ri[r], rj[r], k, l);
-            for (int J = 0; J < K; ++J)
-                col -= L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + p];
-            LK[r] = col / sq;
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
+            int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
+            or_subtr_rows(h, ri, rj, r0, r1, k, l, L, npairs, K, L + p, npairs, LK);
+            for (int64_t r = r0; r < r1; ++r) LK[r] = LK[r] / sq;
         }
         int bad = 0;
         for (int64_t r = 0; r < npairs; ++r) {
@@ -519,13 +562,17 @@ int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double 
             int64_t q = Q[i];
             double* c = col + (size_t)i * npairs;
             int k = ri[q], l = rj[q];
-            #pragma omp parallel for schedule(dynamic, 64)
-            for (int64_t r = 0; r < npairs; ++r) {
-                if (!live[r]) { c[r] = 0.0; continue; }
-                double v = or_eri(h, ri[r], rj[r], k, l);
-                for (int J = 0; J < K; ++J)
-                    v -= L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + q];
-                c[r] = v;
+            /* live rows only; a dropped row keeps 0 in every vector */
+            #pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
+                int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
+                for (int64_t a = r0; a < r1;) {
+                    if (!live[a]) { c[a++] = 0.0; continue; }
+                    int64_t e = a;
+                    while (e < r1 && live[e]) ++e;
+                    or_subtr_rows(h, ri, rj, a, e, k, l, L, npairs, K, L + q, npairs, c);
+                    a = e;
+                }
             }
             used[i] = 0;
         }
@@ -604,12 +651,13 @@ int or_cd_from_basis(void* h, const int64_t* rows, int64_t npairs, const int64_t
         }
     }
     if (status == 0) {
-        #pragma omp parallel for schedule(dynamic, 64)
-        for (int64_t r = 0; r < npairs; ++r) {
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
+            int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
             for (int K = 0; K < M; ++K) {
-                double v = or_eri(h, ri[r], rj[r], ri[piv[K]], rj[piv[K]]);
-                for (int J = 0; J < K; ++J) v -= L[(int64_t)J * npairs + r] * S[(size_t)K * M + J];
-                L[(int64_t)K * npairs + r] = v / S[(size_t)K * M + K];
+                double* LK = L + (int64_t)K * npairs;
+                or_subtr_rows(h, ri, rj, r0, r1, ri[piv[K]], rj[piv[K]], L, npairs, K, S + (size_t)K * M, 1, LK);
+                for (int64_t r = r0; r < r1; ++r) LK[r] = LK[r] / S[(size_t)K * M + K];
             }
         }
     }

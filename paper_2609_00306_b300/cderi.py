@@ -30,7 +30,7 @@ _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENO
 # every symbol declared in include/cderi.h
 EXPORTS = ["cd_system_create", "cd_system_free", "cd_system_info", "cd_system_rows", "cd_eri_columns",
            "cd_eri_factor", "cd_eri_factor_sys", "cd_factor_free", "cd_factor_info", "cd_factor_pivots",
-           "cd_factor_vectors", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_last_error", "cd_version"]
+           "cd_factor_vectors", "cd_factor_pivot_diag", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_set_wait_limit", "cd_last_error", "cd_version"]
 
 
 class CDError(RuntimeError):
@@ -49,7 +49,7 @@ class cd_opts_t(ctypes.Structure):
                 ("block", ctypes.c_int32), ("max_vectors", ctypes.c_int64), ("mem_budget_gb", ctypes.c_double),
                 ("forced_pivots", ctypes.c_void_p), ("n_forced", ctypes.c_int64),
                 ("update", ctypes.c_int32), ("algorithm", ctypes.c_int32), ("span", ctypes.c_double),
-                ("candidates", ctypes.c_void_p)]
+                ("candidates", ctypes.c_void_p), ("diag_shift", ctypes.c_double)]
 
 
 _lib = None
@@ -77,6 +77,8 @@ def load(path: Optional[str] = None):
         "cd_factor_info": (ctypes.c_int, [P, P, P, P, P]),
         "cd_factor_pivots": (ctypes.c_int, [P, P, P, P, P]),
         "cd_factor_vectors": (ctypes.c_int, [P, P, P, P, P]),
+        "cd_factor_pivot_diag": (ctypes.c_int, [P, P]),
+        "cd_set_wait_limit": (ctypes.c_int, [D, P]),
         "cd_factor_stats": (ctypes.c_int, [P, P]),
         "cd_factor_gather": (ctypes.c_int, [P, P, I32, P]),
         "cd_jk": (ctypes.c_int, [P, P, I32, P, P, I32, P]),
@@ -127,9 +129,10 @@ class _BasisArgs:
 def make_opts(tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
               max_vectors: int = 0, mem_budget_gb: float = 0.0, forced: Optional[Sequence[int]] = None,
               update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0,
-              candidates=None):
+              candidates=None, diag_shift: float = 0.0):
     o = cd_opts_t(float(tau), float(schwarz), int(vec_precision), int(block), int(max_vectors),
-                  float(mem_budget_gb), None, 0, int(update), int(algorithm), float(span), None)
+                  float(mem_budget_gb), None, 0, int(update), int(algorithm), float(span), None,
+                  float(diag_shift))
     keep = []
     if forced is not None:
         f = np.ascontiguousarray(forced, dtype=np.int64)
@@ -203,6 +206,12 @@ class Factor:
         resid = np.zeros(self.n_rows)
         _check(load().cd_factor_pivots(self._h, _p(rows), _p(packed), _p(gaps), _p(resid)))
         return rows, packed, gaps, resid
+
+    def pivot_diag(self) -> np.ndarray:
+        """Tracked residual diagonal of each pivot when it was taken [M]."""
+        out = np.zeros(self.M)
+        _check(load().cd_factor_pivot_diag(self._h, _p(out)))
+        return out
 
     def vectors_host(self) -> np.ndarray:
         L = np.zeros((self.M, self.n_rows))
@@ -288,12 +297,13 @@ class Factor:
 def cd_eri_factor(basis, tau: float, schwarz: float = 0.0, vec_precision: int = CD_FP64, block: int = 0,
                   max_vectors: int = 0, mem_budget_gb: float = 0.0, forced=None, stream=None,
                   update: int = CD_UPDATE_SLICE, algorithm: int = CD_ALG_FULL, span: float = 0.0,
-                  candidates=None) -> Factor:
+                  candidates=None, diag_shift: float = 0.0) -> Factor:
     """Full pipeline from a host basis (C ABI cd_eri_factor).  ``candidates``: mask
-    over the screened rows (``System.rows()`` order) of the rows that may be pivots."""
+    over the screened rows (``System.rows()`` order) of the rows that may be pivots.
+    ``diag_shift``: test hook (lowers every starting diagonal; see cd_opts_t)."""
     args = _BasisArgs(basis)
     o, keep = make_opts(tau, schwarz, vec_precision, block, max_vectors, mem_budget_gb, forced, update,
-                        algorithm, span, candidates)
+                        algorithm, span, candidates, diag_shift)
     h = ctypes.c_void_p()
     _check(load().cd_eri_factor(ctypes.byref(args.s), ctypes.byref(o), _stream(stream), ctypes.byref(h)))
     del keep
@@ -356,6 +366,14 @@ def batch_run(systems, jk_mode: int = CD_JK_FP64, workers: int = 0, blocks=None,
                                PArr(*[j.ctypes.data for j in Js]), PArr(*[k.ctypes.data for k in Ks]),
                                int(jk_mode), int(workers), _stream(stream)))
     return Js, Ks
+
+
+def set_wait_limit(seconds: float) -> float:
+    """Wall-clock limit of the bounded device waits (C ABI cd_set_wait_limit);
+    returns the previous limit in seconds."""
+    prev = ctypes.c_double()
+    _check(load().cd_set_wait_limit(float(seconds), ctypes.byref(prev)))
+    return prev.value
 
 
 def kernel_launches() -> int:

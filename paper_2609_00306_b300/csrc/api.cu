@@ -439,7 +439,16 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   CD_CUDA(cudaMemsetAsync(w.sc, 0, sizeof(StepScratch), st));
   CD_CUDA(cudaMemsetAsync(w.pool, 0, sizeof(double) * b * ld, st));
   CD_CUDA(cudaMemsetAsync(w.D1, 0, sizeof(double) * ld, st));
-  CD_CUDA(cudaMemcpyAsync(w.D0, s->diag_dev, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+  if (o->diag_shift != 0.0) {
+    // test hook: the diagonal of A - shift I (host-made indefinite input)
+    if (!std::isfinite(o->diag_shift)) { set_error("diag_shift must be finite"); return CD_EINVAL; }
+    w.dh.assign(ld, 0.0);
+    for (int64_t r = 0; r < n; ++r) w.dh[r] = s->row_diag[r] - o->diag_shift;
+    CD_CUDA(cudaMemcpyAsync(w.D0, w.dh.data(), sizeof(double) * ld, cudaMemcpyHostToDevice, st));
+    CD_CUDA(cudaStreamSynchronize(st));
+  } else {
+    CD_CUDA(cudaMemcpyAsync(w.D0, s->diag_dev, sizeof(double) * ld, cudaMemcpyDeviceToDevice, st));
+  }
   double d1max = 0.0;
   for (double v : s->row_diag) d1max = std::max(d1max, v);
   const double neg_tol = -1e-10 * d1max;
@@ -688,7 +697,13 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       if (gemm_issued) {
         CD_CUDA(cudaStreamWaitEvent(st, w.ev_gemm, 0));
         CD_TRY(launch_colupd_finalize(w.Dint, ld, n, nb_upd, w.erow, w.rows_dev, w.slots_dev, plan.F, w.pool, ld, st));
+        int herr_blk = 0;
+        CD_CUDA(cudaMemcpyAsync(&herr_blk, w.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         CD_CUDA(cudaStreamSynchronize(st));  // host copies of the group vectors are complete
+        if (herr_blk) {  // an incomplete update must not feed the pivot steps
+          set_error("tensor-core update: a bounded pipeline wait timed out (wait bits " + std::to_string(herr_blk) + ")");
+          return CD_ETIMEOUT;
+        }
       }
     } else {
       std::unordered_map<int64_t, std::vector<int>> groups;
@@ -795,6 +810,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       std::swap(Dcur, Dnext);
       f->piv.push_back(sysrow(p));
       f->gaps.push_back(gap);
+      f->pivd.push_back(dp);
       ++K;
       row2slot.erase(it);
       slot_row[sl] = -1;
@@ -1012,6 +1028,12 @@ int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packe
     if (gaps) gaps[k] = f->gaps[k];
   }
   if (resid_diag && f->n > 0) std::memcpy(resid_diag, f->resid.data(), sizeof(double) * f->n);
+  return CD_OK;
+}
+
+int cd_factor_pivot_diag(const cd_factor_t* f, double* out) {
+  if (!f || (f->M > 0 && !out)) { set_error("cd_factor_pivot_diag: bad argument"); return CD_EINVAL; }
+  if (f->M > 0) std::memcpy(out, f->pivd.data(), sizeof(double) * f->M);
   return CD_OK;
 }
 

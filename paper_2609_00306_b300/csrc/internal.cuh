@@ -185,6 +185,7 @@ struct cd_factor {
   int vec_precision = CD_FP64;
   std::vector<int64_t> piv;
   std::vector<double> gaps;
+  std::vector<double> pivd;     // tracked residual diagonal of each pivot when it was taken
   std::vector<double> resid;
   double resid_max = 0.0;
   double stats[16] = {0};

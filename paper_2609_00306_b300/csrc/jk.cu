@@ -103,8 +103,11 @@ int launch_gemv_rows(const T* L, int64_t ld, int64_t M, int64_t n, const double*
 
 template <class T>
 int launch_gemv_cols(const T* L, int64_t ld, int64_t M, int64_t n, const double* v, double* y, cudaStream_t st) {
-  if (M <= 0 || n <= 0) return CD_OK;
+  if (n <= 0) return CD_OK;
+  // y accumulates with atomics: clear it first, also when there is no vector
+  // (M = 0 gives y = 0)
   CD_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
+  if (M <= 0) return CD_OK;
   const int64_t tiles = (n + 255) / 256;
   int64_t splits = (148 * 8 + tiles - 1) / tiles;
   if (splits < 1) splits = 1;

@@ -11,6 +11,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include "internal.cuh"
 #include "ozaki.cuh"
@@ -70,7 +71,7 @@ template <int SA, int SB, int KEEP, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, BN == 32 ? 2 : 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              int64_t m_rows, int64_t n_rows, int nkb_total, int kb_per_split, int kcb, int F,
-             unsigned long long* __restrict__ D, int64_t ldd, int* err, int sym) {
+             unsigned long long* __restrict__ D, int64_t ldd, int* err, int sym, unsigned long long wait_ns) {
   using C = Cfg<SA, SB, KEEP, BN, STAGES>;
   // symmetric product (A == B): tiles entirely below the diagonal are skipped
   if (sym && (int64_t)blockIdx.x * BN + BN <= (int64_t)blockIdx.y * BM) return;
@@ -80,7 +81,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;      // [2] accumulator set ready for the drain
   uint64_t* tempty = tfull + 2;          // [2] accumulator set drained
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* mma_done = tempty + 2;       // MMAs of an aborted CTA completed
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -93,6 +95,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
     for (int b = 0; b < 2; ++b) { tc::mbar_init(&tfull[b], 1); tc::mbar_init(&tempty[b], 4); }
+    tc::mbar_init(mma_done, 1);
     *abort_flag = 0;
     tc::fence_mbar_init();
   }
@@ -107,16 +110,25 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     if (warp == 4) {
       if (lane == 0) {
         // ---------------- TMA producer
+        int issued = 0;
         for (int i = 0; i < nkb; ++i) {
           const int s = i % STAGES;
           const uint32_t ph = (uint32_t)((i / STAGES) & 1);
-          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 2)) break;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, err, 2, wait_ns)) break;
           uint8_t* a = smem + s * C::STAGE_BYTES;
           uint8_t* b = a + C::A_BYTES;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
           const int kx = (kb0 + i) * BK;
           tc::tma_load_3d(a, &tmA, kx, (int32_t)m0, 0, &full[s]);
           tc::tma_load_3d(b, &tmB, kx, (int32_t)n0, 0, &full[s]);
+          issued = i + 1;
+        }
+        if (*abort_flag) {
+          // the MMA warp may have stopped before consuming the last loads: let
+          // every copy still in flight land before the CTA's shared memory is
+          // released (each of the last STAGES loads completes its stage's phase)
+          for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+            tc::mbar_settle(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
         }
       }
     } else if (warp == 5) {
@@ -131,10 +143,10 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           if (chunk_start && chunk >= C::NBUF) {
             // the set about to be overwritten was filled by chunk - NBUF: wait for its drain
             const int prev = chunk - C::NBUF;
-            if (!tc::mbar_wait(&tempty[buf], (uint32_t)((prev / C::NBUF) & 1), abort_flag, err, 8)) break;
+            if (!tc::mbar_wait(&tempty[buf], (uint32_t)((prev / C::NBUF) & 1), abort_flag, err, 8, wait_ns)) break;
             tc::tc_fence_after();
           }
-          if (!tc::mbar_wait(&full[s], ph, abort_flag, err, 1)) break;
+          if (!tc::mbar_wait(&full[s], ph, abort_flag, err, 1, wait_ns)) break;
           tc::tc_fence_after();
           const uint32_t a = tc::smem_u32(smem + s * C::STAGE_BYTES);
           const uint32_t b = a + C::A_BYTES;
@@ -162,6 +174,11 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             ++chunk;
           }
         }
+        if (*abort_flag) {
+          // MMAs issued before the abort must finish before tensor memory is freed
+          tc::umma_commit(mma_done);
+          tc::mbar_settle(mma_done, 0u);
+        }
       }
     } else {
       // ---------------- drain (warps 0-3): thread = TMEM lane = tile row
@@ -173,7 +190,7 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
       bool ok = true;
       for (int ch = 0; ch < nchunks; ++ch) {
         const int buf = C::NBUF == 2 ? (ch & 1) : 0;
-        if (!tc::mbar_wait(&tfull[buf], (uint32_t)((ch / C::NBUF) & 1), abort_flag, err, 4)) { ok = false; break; }
+        if (!tc::mbar_wait(&tfull[buf], (uint32_t)((ch / C::NBUF) & 1), abort_flag, err, 4, wait_ns)) { ok = false; break; }
         tc::tc_fence_after();
         const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * C::ACC_COLS);
 #pragma unroll
@@ -217,6 +234,9 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 }
 
 // ------------------------------------------------------------------ host ----
+std::atomic<unsigned long long> g_wait_ns{tc::kWaitNsDefault};
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -257,7 +277,7 @@ int run(const CUtensorMap& ta, const CUtensorMap& tb, int64_t a_rows, int64_t b_
   const int64_t row_tiles = (a_rows + BM - 1) / BM;
   if (row_tiles > 65535) { set_error("ozaki_gemm: too many row tiles"); return CD_EINVAL; }
   dim3 grid((unsigned)((b_rows + BN - 1) / BN), (unsigned)row_tiles, (unsigned)nsplit);
-  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err, sym);
+  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err, sym, wait_limit_ns());
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -412,6 +432,18 @@ extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const do
   }
   if (herr) { set_error("cd_slice_matmul: tensor-core pipeline wait timed out"); return fin(CD_ETIMEOUT); }
   return fin(CD_OK);
+}
+
+extern "C" int cd_set_wait_limit(double seconds, double* previous) {
+  using namespace cd;
+  if (previous) *previous = (double)g_wait_ns.load() * 1e-9;
+  if (!(seconds >= 0.0) || !(seconds <= 3600.0)) {
+    set_error("cd_set_wait_limit: seconds must be in [0, 3600]");
+    return CD_EINVAL;
+  }
+  const double ns = seconds * 1e9;
+  g_wait_ns.store(ns < 1.0 ? 1ull : (unsigned long long)ns);
+  return CD_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -13,10 +13,13 @@ namespace tc {
 // ---- error flag written by kernels whose bounded waits give up ------------
 // *err (global) collects bits: 1 = smem-stage "full" wait, 2 = "empty" wait,
 // 4 = accumulator "full" wait, 8 = accumulator "empty" wait.  A wait gives up
-// after kWaitNs of wall time (globaltimer) or as soon as any CTA has set *err;
-// the CTA then stops issuing work, frees its tensor memory and returns, and the
-// host reports CD_ETIMEOUT.
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+// after limit_ns of wall time (globaltimer; the kernel's argument, 2 s unless
+// the host changed it with cd_set_wait_limit) or as soon as any CTA has set
+// *err.  The CTA then stops issuing work, waits (bounded by kSettleNs) for the
+// copies and MMAs it already issued, frees its tensor memory and returns, and
+// the host reports CD_ETIMEOUT.
+constexpr unsigned long long kWaitNsDefault = 2000000000ull;   // 2 s
+constexpr unsigned long long kSettleNs = 1000000000ull;        // 1 s for in-flight work after an abort
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -54,19 +57,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // bounded wait: false when it gave up (time limit, or another CTA/role gave up)
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int which = 1) {
+                                          int which, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0u) {
       if (*abort_flag || (err && *(volatile int*)err)) { *abort_flag = 1; return false; }
-      if (globaltimer_ns() - t0 > kWaitNs) {
+      if (globaltimer_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         if (err) atomicOr(err, which);
         return false;
       }
     }
+  }
+}
+// wait for work this CTA already issued (a TMA copy or an MMA commit) after an
+// abort: ignores the abort flag, gives up after kSettleNs
+__device__ __forceinline__ bool mbar_settle(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u && globaltimer_ns() - t0 > kSettleNs) return false;
   }
 }
 

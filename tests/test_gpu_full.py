@@ -40,7 +40,9 @@ def test_sp400_full_parity():
     r = o.cd(rows, s.tau)
     f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
     prow, ppk, gaps, resid = f.pivots()
-    assert np.array_equal(ppk[:0], rows[:0])
+    packed, _ = cd.System(s.basis, s.schwarz).rows()
+    assert np.array_equal(packed, rows)          # same screened rows, same order
+    assert np.array_equal(ppk, rows[prow])       # pivots reported as rows and packed pairs consistently
     assert f.n_rows == rows.shape[0]
     assert f.M == r.M
     assert f.max_resid < s.tau

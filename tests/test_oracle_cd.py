@@ -53,8 +53,12 @@ def test_cd_matches_lapack_dpstrf(s40):
     # same pivot sequence, except where two candidate diagonals are within 1e-12
     same = piv[:rank] == r.piv
     if not np.all(same):
+        # a divergence is allowed only at a near-tie: the residual diagonal after
+        # the first k vectors (recomputed from A, not from the oracle's tracked D)
+        # must be within 1e-12 at the two pivots
         k = int(np.argmin(same))
-        assert r.gap[k] < 1e-12 or abs(r.D.max()) < 1e-12
+        Dk = np.diag(A) - np.sum(r.L[:k] ** 2, axis=0)
+        assert abs(Dk[r.piv[k]] - Dk[piv[k]]) < 1e-12
     else:
         Lo = r.L[:, piv].T  # rows in dpstrf order
         assert np.max(np.abs(Lo - Lf)) < 1e-10 * np.max(np.abs(Lf))
@@ -167,3 +171,30 @@ def test_jk_exact_closed_form_single_s():
     a = 0.8
     ssss = 2 * np.pi ** 2.5 / (2 * a * 2 * a * np.sqrt(4 * a)) * (2 * a / np.pi) ** 3.0
     assert abs(J[0, 0] - 2 * ssss) < 1e-13 and abs(K[0, 0] - 2 * ssss) < 1e-13
+
+
+@pytest.mark.parametrize("name,chunk", [("s40", 97), ("sp8", 50), ("sp18", 700)])
+def test_loop_order_is_bit_identical(name, chunk):
+    """The chunked, vector-outer memory order of the Eq. (subtr) sums gives the
+    same bits as the plain per-element loop: free and forced decompositions, the
+    span-factor selection with and without dropped rows, and the second step."""
+    s = synth.make_workload(name)
+    o = oracle.Oracle(s.basis)
+    rows = o.screen(s.schwarz)
+    assert rows.shape[0] % chunk != 0  # several chunks and a ragged last one
+    out = {}
+    try:
+        for plain in (True, False):
+            oracle.set_loop_order(plain=plain, chunk=chunk)
+            r = o.cd(rows, s.tau)
+            sp = o.cd_span(rows, s.tau, span=0.05, qmax=16, reduce=False)
+            sr = o.cd_span(rows, s.tau, span=0.05, qmax=16, reduce=True)
+            fb = o.cd_from_basis(rows, sr.piv)
+            out[plain] = (r, sp, sr, fb)
+    finally:
+        oracle.set_loop_order()
+    (r0, sp0, sr0, fb0), (r1, sp1, sr1, fb1) = out[True], out[False]
+    assert np.array_equal(r0.piv, r1.piv) and np.array_equal(r0.L, r1.L) and np.array_equal(r0.D, r1.D)
+    assert np.array_equal(sp0.piv, sp1.piv) and np.array_equal(sp0.L, sp1.L)
+    assert np.array_equal(sr0.piv, sr1.piv) and np.array_equal(sr0.L, sr1.L)
+    assert np.array_equal(fb0, fb1)

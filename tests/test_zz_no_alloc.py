@@ -46,3 +46,33 @@ def test_coulomb_static_matches_cd_jk_twice(name):
         got = J.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref)) <= tol
+
+
+def test_coulomb_static_clears_after_a_factor_without_vectors():
+    """A factor with no vector (tau above every diagonal) right after a normal
+    one: J must be exactly zero, not the previous call's J left in the shared
+    static scratch.  The device's free memory is unchanged by the calls."""
+    import paper_2609_00306_b300 as cd
+    from paper_2609_00306_b300.static_jk import coulomb_static
+    s = synth.make_workload("sp18")
+    N = s.n_basis
+    C = torch.tensor(s.C_occ, device="cuda")
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
+    sysm = cd.System(s.basis, s.schwarz)
+    tau0 = 2.0 * float(np.max(sysm.rows()[1]))
+    f0 = cd.cd_eri_factor(s.basis, tau0, s.schwarz)
+    assert f0.M == 0
+    J = torch.zeros((N, N), dtype=torch.float64, device="cuda")
+    coulomb_static(f, C, J)          # warm: symbol address looked up, kernels loaded
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(J).item() > 0
+    free0 = torch.cuda.mem_get_info()[0]
+    coulomb_static(f, C, J)
+    J0 = torch.full((N, N), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    coulomb_static(f0, C, J0)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free1
+    assert free1 <= free0  # only the NaN-filled output tensor was added
+    assert torch.count_nonzero(J0).item() == 0
