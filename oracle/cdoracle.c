@@ -363,7 +363,7 @@ int64_t or_screen(void* h, const double* diag, double thr, int64_t* rows_out)
 /*     col_r = (r|p) - L^0_r L^0_p - L^1_r L^1_p - ... - L^{K-1}_r L^{K-1}_p  */
 /* evaluated left to right.  Vectors are stored row-major [K][npairs], so a   */
 /* loop over J for one r walks memory with a stride of npairs.  The default   */
-/* order takes the rows in chunks (2048 by default) and runs J outermost     */
+/* order takes the rows in chunks (or_chunk_len) and runs J outermost        */
 /* inside a chunk: each L^J is then read contiguously, and every element      */
 /* still sees the same operations in the same order (J ascending), so both    */
 /* orders give bit-identical results.  The plain per-element order and the    */
@@ -371,11 +371,26 @@ int64_t or_screen(void* h, const double* diag, double thr, int64_t* rows_out)
 /* identity with several chunks and a ragged last one.                       */
 /* ------------------------------------------------------------------------- */
 static int or_plain_order = 0;
-static int64_t OR_CHUNK = 2048;
+static int64_t or_chunk_set = 0;   /* 0 = automatic */
 void or_set_order(int plain, int chunk)
 {
     or_plain_order = plain ? 1 : 0;
-    OR_CHUNK = chunk > 0 ? chunk : 2048;
+    or_chunk_set = chunk > 0 ? chunk : 0;
+}
+/* chunk length for npairs rows: at most 2048 (the working set of a chunk stays
+ * in cache), and small enough to give every thread several chunks */
+static int64_t or_chunk_len(int64_t npairs)
+{
+    if (or_chunk_set > 0) return or_chunk_set;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    int64_t c = (npairs + 4 * (int64_t)nt - 1) / (4 * (int64_t)nt);
+    c = (c + 7) / 8 * 8;
+    if (c > 2048) c = 2048;
+    if (c < 64) c = 64;
+    return c;
 }
 
 /* out[r] = (r | k l) - sum_{J<K} L[J][r] * w[J * wstride] for r in [r0, r1),
@@ -457,9 +472,10 @@ int or_cd(void* h, const int64_t* rows, int64_t npairs, double tau,
         double sq = sqrt(D[p]);
         int k = ri[p], l = rj[p];
         double* LK = L + (int64_t)K * npairs;
+        const int64_t CH = or_chunk_len(npairs);
         #pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
-            int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
+        for (int64_t r0 = 0; r0 < npairs; r0 += CH) {
+            int64_t r1 = r0 + CH < npairs ? r0 + CH : npairs;
             or_subtr_rows(h, ri, rj, r0, r1, k, l, L, npairs, K, L + p, npairs, LK);
             for (int64_t r = r0; r < r1; ++r) LK[r] = LK[r] / sq;
         }
@@ -563,9 +579,10 @@ int or_cd_span(void* h, const int64_t* rows, int64_t npairs, double tau, double 
             double* c = col + (size_t)i * npairs;
             int k = ri[q], l = rj[q];
             /* live rows only; a dropped row keeps 0 in every vector */
+            const int64_t CH = or_chunk_len(npairs);
             #pragma omp parallel for schedule(dynamic, 1)
-            for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
-                int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
+            for (int64_t r0 = 0; r0 < npairs; r0 += CH) {
+                int64_t r1 = r0 + CH < npairs ? r0 + CH : npairs;
                 for (int64_t a = r0; a < r1;) {
                     if (!live[a]) { c[a++] = 0.0; continue; }
                     int64_t e = a;
@@ -651,9 +668,10 @@ int or_cd_from_basis(void* h, const int64_t* rows, int64_t npairs, const int64_t
         }
     }
     if (status == 0) {
+        const int64_t CH = or_chunk_len(npairs);
         #pragma omp parallel for schedule(dynamic, 1)
-        for (int64_t r0 = 0; r0 < npairs; r0 += OR_CHUNK) {
-            int64_t r1 = r0 + OR_CHUNK < npairs ? r0 + OR_CHUNK : npairs;
+        for (int64_t r0 = 0; r0 < npairs; r0 += CH) {
+            int64_t r1 = r0 + CH < npairs ? r0 + CH : npairs;
             for (int K = 0; K < M; ++K) {
                 double* LK = L + (int64_t)K * npairs;
                 or_subtr_rows(h, ri, rj, r0, r1, ri[piv[K]], rj[piv[K]], L, npairs, K, S + (size_t)K * M, 1, LK);

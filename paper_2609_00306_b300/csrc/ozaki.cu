@@ -106,11 +106,11 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  int issued = 0;   // TMA stages issued (producer thread)
   if (nkb > 0) {
     if (warp == 4) {
       if (lane == 0) {
         // ---------------- TMA producer
-        int issued = 0;
         for (int i = 0; i < nkb; ++i) {
           const int s = i % STAGES;
           const uint32_t ph = (uint32_t)((i / STAGES) & 1);
@@ -122,13 +122,6 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           tc::tma_load_3d(a, &tmA, kx, (int32_t)m0, 0, &full[s]);
           tc::tma_load_3d(b, &tmB, kx, (int32_t)n0, 0, &full[s]);
           issued = i + 1;
-        }
-        if (*abort_flag) {
-          // the MMA warp may have stopped before consuming the last loads: let
-          // every copy still in flight land before the CTA's shared memory is
-          // released (each of the last STAGES loads completes its stage's phase)
-          for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
-            tc::mbar_settle(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
         }
       }
     } else if (warp == 5) {
@@ -173,11 +166,6 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             tc::umma_commit(&tfull[buf]);
             ++chunk;
           }
-        }
-        if (*abort_flag) {
-          // MMAs issued before the abort must finish before tensor memory is freed
-          tc::umma_commit(mma_done);
-          tc::mbar_settle(mma_done, 0u);
         }
       }
     } else {
@@ -227,6 +215,22 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
   }
   tc::tc_fence_before();
   __syncthreads();
+  // Every role has left its loop, so the abort flag is final here.  After an
+  // abort some issued work may still be in flight: the last STAGES TMA loads
+  // (the MMA warp may have stopped before consuming them; each completes its
+  // stage's phase) and MMAs the drain never waited for.  Both are waited for
+  // (bounded) before the shared and tensor memory of the CTA are released.
+  if (*abort_flag) {
+    if (warp == 4 && lane == 0) {
+      for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+        tc::mbar_settle(&full[i % STAGES], (uint32_t)((i / STAGES) & 1));
+    } else if (warp == 5 && lane == 0) {
+      tc::umma_commit(mma_done);   // arrives once every MMA this thread issued has completed
+      tc::mbar_settle(mma_done, 0u);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+  }
   if (warp == 5) {
     tc::tc_fence_after();
     tc::tmem_dealloc<C::TMEM_COLS>(tmem);
