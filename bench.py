@@ -59,6 +59,8 @@ def _args():
     ap.add_argument("--jk-alone-modes", default="all",
                     help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=48)
+    ap.add_argument("--no-fp64-update", action="store_true",
+                    help="skip the factorisation with the FP64 DFMA column update (its roofline entry)")
     return ap.parse_args()
 
 
@@ -68,7 +70,7 @@ class ClockSampler:
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_power_cap,memory.used")
 
     def __init__(self, index: int = 0):
         self.index = index
@@ -107,6 +109,11 @@ class ClockSampler:
         reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.samples)}
+
+    def peak_memory_mib(self):
+        """Largest device memory in use (MiB) over the samples, or None."""
+        used = [float(s[7]) for s in self.samples if len(s) > 7 and s[7].replace(".", "").isdigit()]
+        return max(used) if used else None
 
 
 # ------------------------------------------------------------- CPU oracle ---
@@ -148,18 +155,26 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 4096, sub_s
     b_sub = max(0.0, 2.0 * (T_cd - T_eri) / K_sub ** 2)
     b = b_sub * n / sub.shape[0]
     t = time.perf_counter()
-    oracle.jk_from_vectors(r.L[:2], rows, system.C_occ)
-    c = (time.perf_counter() - t) / 2.0
-    proj = t_screen + M_full * a + b * M_full ** 2 / 2.0 + M_full * c
+    oracle.jk_from_vectors(r.L[:2], rows, system.C_occ, want_k=False)
+    cJ = (time.perf_counter() - t) / 2.0
+    t = time.perf_counter()
+    oracle.jk_from_vectors(r.L[:2], rows, system.C_occ, want_j=False)
+    cK = (time.perf_counter() - t) / 2.0
+    cd_s = t_screen + M_full * a + b * M_full ** 2 / 2.0
+    proj = cd_s + M_full * (cJ + cK)
     sample_s = time.perf_counter() - t0
+    name = getattr(system, "name", "the workload")
     return {
         "value": proj, "unit": "s", "cores": cores, "kind": "oracle",
-        "sample": (f"oracle on the N=2000 system: screening ({t_screen:.2f}s), first {k_steps} pivot steps over "
+        "cd_s": cd_s, "j_ms": M_full * cJ * 1e3, "k_ms": M_full * cK * 1e3, "projected": True,
+        "sample": (f"oracle on {name}: screening ({t_screen:.2f}s), first {k_steps} pivot steps over "
                    f"all {n} rows (a={a:.3g}s/step), {K_sub} steps on the first {sub.shape[0]} rows "
                    f"({T_cd:.2f}s, of which its ERI columns alone {T_eri:.2f}s: update b={b:.3g}s per vector "
-                   f"per step after scaling), J/K of 2 vectors (c={c:.3g}s each); "
-                   f"projected to M={M_full}: t_screen + M a + b M^2/2 + M c; sample wall {sample_s:.1f}s"),
-        "sample_wall_s": sample_s, "model": {"t_screen": t_screen, "a": a, "b": b, "c": c},
+                   f"per step after scaling), J and K of 2 vectors (cJ={cJ:.3g}s, cK={cK:.3g}s each); "
+                   f"projected to M={M_full}: CD = t_screen + M a + b M^2/2, J = M cJ, K = M cK; "
+                   f"sample wall {sample_s:.1f}s"),
+        "sample_wall_s": sample_s,
+        "model": {"t_screen": t_screen, "a": a, "b": b, "cJ": cJ, "cK": cK},
     }
 
 
@@ -229,6 +244,8 @@ def run_ours(args, rank, world):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     tot_ms = 0.0
     stats = []
+    free0, total0 = torch.cuda.mem_get_info(dev)
+    used0_mib = (total0 - free0) / 2 ** 20   # device memory in use before the timed steps
     with ClockSampler(dev.index) as clk:
         for i in range(args.steps):
             flush.zero_()
@@ -268,6 +285,23 @@ def run_ours(args, rank, world):
         except cd.CDError as e:
             jk[name + "_ms"] = None
             jk[name + "_error"] = str(e)
+    # J alone (FP64 vectors: two streamed passes over L) and the mixed K alone,
+    # for their own rooflines; best of 3 after a warm call
+    def timed(fn, reps=3):
+        fn()
+        best = None
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t = ev0.elapsed_time(ev1)
+            best = t if best is None else min(best, t)
+        return best
+    j_only_ms = timed(lambda: f.jk_device(C_dev, J_dev, None, mode=cd.CD_JK_FP64))
+    k_mixed_ms = timed(lambda: f.jk_device(C_dev, None, K_dev, mode=jk_mode)) if jk_mode != cd.CD_JK_FP64 else None
     Dm = 2.0 * s.C_occ @ s.C_occ.T
     for mx in ("bf16x3", "bf16x4", "bf16x5", "bf16x3_fp32vec", "bf16x4_fp32vec"):
         if "fp64" in res and mx in res:
@@ -287,6 +321,20 @@ def run_ours(args, rank, world):
     f.free()
     del f
     torch.cuda.synchronize()
+    # the FP64 column update (DFMA, CD_UPDATE_FP64): one factorisation, for its
+    # own roofline on the FP64 pipe at this size
+    upd64 = None
+    if not args.no_fp64_update:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec, update=cd.CD_UPDATE_FP64)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        gs = g.stats()
+        upd64 = {"factor_ms": ev0.elapsed_time(ev1), "M": g.M, "ms_colupd": gs["ms_colupd"],
+                 "colupd_flops": gs["colupd_flops"], "same_pivots_as_step": None}
+        g.free()
+        del g
     # the other pivot policies, one factorisation each (same system, same tau)
     other_algs = {}
     for name, alg in algs.items():
@@ -343,6 +391,48 @@ def run_ours(args, rank, world):
         roof, roof_other, other_key = roof_eri, roof_upd, "roofline_update"
     else:
         roof, roof_other, other_key = roof_upd, roof_eri, "roofline_eri"
+    hbm = peaks.get("hbm_gbs") or 6400.0
+    bf16_burst = peaks.get("bf16_tflops") or 1800.0
+    bf16_sust = peaks.get("bf16_tflops_sustained") or bf16_burst
+    # J: two streamed passes over the FP64 vectors, 2 M rows 8 bytes (the
+    # density, v and the packed J are rows-sized or smaller)
+    j_bytes = 2.0 * M * n_rows * 8.0
+    roof_j = {"kernel": "j_pass1_kernel + j_pass2_kernel (J = L^T (L d), Sec. 4.1)", "bound": "hbm",
+              "achieved": j_bytes / (j_only_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+              "frac": j_bytes / (j_only_ms * 1e-3) / 1e9 / hbm, "traffic": None, "ms": j_only_ms,
+              "algorithmic_bytes": j_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst; timed alone) - of measured"}
+    # K: 4 N^2 O M algorithmic flops (B^P = L^P C and K = 2 sum B B^T); the
+    # mixed form issues S(S+1)/2 BF16 slice products per FP64-equivalent flop
+    k_flops = 4.0 * N * N * O * M
+    roof_k = None
+    if k_mixed_ms:
+        S_sl = {"bf16x3": 3, "bf16x4": 4, "bf16x5": 5}.get(args.jk.split("_")[0], 3)
+        prods = S_sl * (S_sl + 1) // 2
+        ach = prods * k_flops / (k_mixed_ms * 1e-3) / 1e12
+        roof_k = {"kernel": f"mixed K ({args.jk}: unpack_slice_kernel + ozaki_kernel<{S_sl},{S_sl},{S_sl + 1}> x2)",
+                  "bound": "tensor", "achieved": ach, "peak": bf16_burst, "unit": "TFLOP/s", "frac": ach / bf16_burst,
+                  "frac_of_sustained": ach / bf16_sust, "traffic": None, "ms": k_mixed_ms,
+                  "algorithmic_flops": k_flops, "slice_products": prods,
+                  "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; timed alone) - of measured"}
+    roof_k64 = None
+    if jk.get("fp64_ms"):
+        k64_ms = jk["fp64_ms"] - j_only_ms
+        ach = k_flops / (k64_ms * 1e-3) / 1e12
+        roof_k64 = {"kernel": "dgemm_kernel (FP64 K, DFMA)", "bound": "alu", "achieved": ach, "peak": peak_fp64,
+                    "unit": "TFLOP/s", "frac": ach / peak_fp64, "traffic": None, "ms": k64_ms,
+                    "algorithmic_flops": k_flops,
+                    "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit counts and clock)"}
+    roof_u64 = None
+    if upd64 and upd64["ms_colupd"] > 0:
+        ach = upd64["colupd_flops"] / (upd64["ms_colupd"] * 1e-3) / 1e12
+        roof_u64 = {"kernel": "colupd_kernel (FP64 DFMA column update, Eq. subtr)", "bound": "alu", "achieved": ach,
+                    "peak": peak_fp64, "unit": "TFLOP/s", "frac": ach / peak_fp64, "traffic": None,
+                    "factor_ms": upd64["factor_ms"], "M": upd64["M"],
+                    "peak_source": "FP64 DFMA pipe: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit counts and clock)"}
+    peak_mib = clk.peak_memory_mib()
+    memory = {"device_peak_gb": (peak_mib - used0_mib) * 2 ** 20 / 1e9 if peak_mib else None,
+              "vectors_gb": M * ((n_rows + 31) // 32 * 32) * 8.0 / 1e9, "cap_gb": 150.0,
+              "how": "nvidia-smi memory.used sampled every 0.2 s during the timed step, minus the use before it"}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if jk_mode == cd.CD_JK_FP64 else "f64+" + args.jk,
@@ -359,7 +449,9 @@ def run_ours(args, rank, world):
                             "factor_total": st["ms_total"], "blocks": st["blocks"], "eri_columns_computed": st["eri_columns"],
                             "eri_fp64_ops": st.get("eri_fp64_ops", 0.0)},
            "jk_alone_ms": jk, "pivot_policies": other_algs,
-           "roofline": roof, other_key: roof_other, "gpu_launches": int(launches), "clocks": clk.summary()}
+           "roofline": roof, other_key: roof_other, "roofline_j": roof_j, "roofline_k": roof_k,
+           "roofline_k_fp64": roof_k64, "roofline_update_fp64": roof_u64, "memory": memory,
+           "gpu_launches": int(launches), "clocks": clk.summary()}
     # end to end through the C ABI with host buffers
     if not args.no_e2e:
         torch.cuda.synchronize()
@@ -472,7 +564,10 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": args.workload, "M_assumed": M_est},
            "cpu_baseline": {"value": v, "unit": "s", "cores": vals[0]["cores"], "kind": "oracle",
-                            "sample": vals[0]["sample"]},
+                            "sample": vals[0]["sample"], "projected": True,
+                            "cd_s": float(np.mean([r["cd_s"] for r in vals])),
+                            "j_ms": float(np.mean([r["j_ms"] for r in vals])),
+                            "k_ms": float(np.mean([r["k_ms"] for r in vals]))},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0

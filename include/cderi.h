@@ -280,7 +280,7 @@ int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const double* Y, in
  * free its tensor memory and return, and the entry point returns CD_ETIMEOUT
  * with the device still usable.  This sets the limit for launches issued from
  * now on (process-wide; seconds in [0, 3600], 0 = give up at the first wait
- * that is not already satisfied) and returns the previous limit in *previous
+ * whose phase is not already complete) and returns the previous limit in *previous
  * (may be NULL).  Meant for tests of that error path and for tuning. */
 int cd_set_wait_limit(double seconds, double* previous);
 

@@ -291,6 +291,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   int64_t* order_dev = nullptr;      // live bra shell pairs, grouped by class
   uint8_t* cand_dev = nullptr;       // [n] candidate mask (working rows)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  EriStreams eri;                    // concurrent launches of the three ERI class kernels
   // second stream for the sliced update, used only with CDERI_OVERLAP_UPDATE=1
   // (by default the update runs on the main stream before the ERI columns)
   cudaStream_t st2 = nullptr;
@@ -306,6 +307,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
       scratch_free(p, st);
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {eri.fork, eri.join[0], eri.join[1]}) if (e) cudaEventDestroy(e);
+    for (cudaStream_t x : eri.side) if (x) cudaStreamDestroy(x);
     for (cudaEvent_t e : {ev_ready, ev_gemm, ev_g0, ev_g1}) if (e) cudaEventDestroy(e);
     if (st2) cudaStreamDestroy(st2);
   }
@@ -429,6 +432,9 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   w.cand_rows_h.resize(cand_cap);
   w.cand_vals_h.resize(cand_cap);
   for (auto& e : w.ev) CD_CUDA(cudaEventCreate(&e));
+  for (auto& x : w.eri.side) CD_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  CD_CUDA(cudaEventCreateWithFlags(&w.eri.fork, cudaEventDisableTiming));
+  for (auto& e : w.eri.join) CD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   if (slice) {
     CD_CUDA(cudaStreamCreateWithFlags(&w.st2, cudaStreamNonBlocking));
     CD_CUDA(cudaEventCreateWithFlags(&w.ev_ready, cudaEventDisableTiming));
@@ -689,7 +695,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     if (!kets.empty()) {
       CD_CUDA(cudaMemcpyAsync(w.kets_dev, groups.data(), sizeof(KetGroup) * groups.size(), cudaMemcpyHostToDevice, st));
       CD_TRY(launch_eri_columns(bra_v, order_v, cls_v, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
-                                s->boys, st, w.eri_ops));
+                                s->boys, st, w.eri_ops, getenv("CDERI_ERI_SERIAL") ? nullptr : &w.eri));
       eri_ints += (double)kets.size() * (double)n;
     }
     CD_CUDA(cudaEventRecord(w.ev[1], st));

@@ -412,18 +412,31 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* kets_dev, int nket,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,
-                       unsigned long long* op_count) {
+                       unsigned long long* op_count, const EriStreams* es) {
   if (nket <= 0) return CD_OK;
-  for (int cls = 0; cls < 3; ++cls) {
+  if (es) {
+    CD_CUDA(cudaEventRecord(es->fork, st));
+    CD_CUDA(cudaStreamWaitEvent(es->side[0], es->fork, 0));
+    CD_CUDA(cudaStreamWaitEvent(es->side[1], es->fork, 0));
+  }
+  // the most expensive class (pp bra pairs) is launched first, on the calling stream
+  for (int cls = 2; cls >= 0; --cls) {
     int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
     if (b1 <= b0) continue;
+    cudaStream_t s = es ? (cls == 2 ? st : es->side[cls]) : st;
     dim3 grid((unsigned)((b1 - b0 + 127) / 128), (unsigned)nket);
-    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else eri_columns_kernel<1, 1><<<grid, 128, 0, st>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    else eri_columns_kernel<1, 1><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
     count_launch();
   }
   CD_CUDA(cudaGetLastError());
+  if (es) {
+    for (int k = 0; k < 2; ++k) {
+      CD_CUDA(cudaEventRecord(es->join[k], es->side[k]));
+      CD_CUDA(cudaStreamWaitEvent(st, es->join[k], 0));
+    }
+  }
   return CD_OK;
 }
 

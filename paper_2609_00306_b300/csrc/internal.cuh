@@ -142,10 +142,21 @@ std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets);
 // bra_order: NULL (every bra shell pair; class c is [class_off[c], class_off[c+1]))
 // or a device list of bra shell pairs grouped by class, class c being entries
 // [class_off[c], class_off[c+1]) of the list.  Rows come from bra.row.
+// Optional side streams for the ERI launches: the three bra classes (pp, ps,
+// ss: different register budgets, so three kernels) run concurrently, the
+// expensive pp class first on the calling stream and the others on side[0],
+// side[1]; the calling stream then waits for both.  The last wave of each
+// class kernel is thereby filled with the other classes' work.
+struct EriStreams {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[2] = {nullptr, nullptr};
+};
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* groups_dev, int ngroups,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,
-                       unsigned long long* op_count = nullptr);  // FP64-pipe operation counter (optional)
+                       unsigned long long* op_count = nullptr,   // FP64-pipe operation counter (optional)
+                       const EriStreams* es = nullptr);
 // diag[row] = (row|row) for every shell pair in `ps` (rows from ps.row)
 int launch_eri_diag(const PairSet& ps, const int64_t* order, const int64_t* class_off,
                     double* diag, const double* boys, cudaStream_t st);

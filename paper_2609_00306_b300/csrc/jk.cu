@@ -20,44 +20,118 @@ __global__ void density_packed_kernel(const double* __restrict__ C, int N, int O
   d[r] = (a == b ? 2.0 : 4.0) * s;
 }
 
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[32];
+// ---- J, pass 1: v_P = sum_r L^P_r d_r.  A CTA takes VB consecutive vectors
+// and streams them against one read of d, 16 bytes per load (double2 for FP64
+// vectors, float4 for FP32; rows start on 256-byte boundaries because ld is a
+// multiple of 32).  The scalar tail covers n not divisible by the vector width.
+template <class T> struct Vec;
+template <> struct Vec<double> { using V = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
+
+__device__ __forceinline__ double dot_w(double2 l, const double* dd) { return fma(l.x, dd[0], l.y * dd[1]); }
+__device__ __forceinline__ double dot_w(float4 l, const double* dd) {
+  return fma((double)l.x, dd[0], fma((double)l.y, dd[1], fma((double)l.z, dd[2], (double)l.w * dd[3])));
+}
+__device__ __forceinline__ void axpy_w(double2 l, double vp, double* a) { a[0] = fma(l.x, vp, a[0]); a[1] = fma(l.y, vp, a[1]); }
+__device__ __forceinline__ void axpy_w(float4 l, double vp, double* a) {
+  a[0] = fma((double)l.x, vp, a[0]); a[1] = fma((double)l.y, vp, a[1]);
+  a[2] = fma((double)l.z, vp, a[2]); a[3] = fma((double)l.w, vp, a[3]);
+}
+
+constexpr int kJThreads = 256;
+constexpr int kJVB = 4;   // vectors per CTA in pass 1
+
+template <class T>
+__global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict__ L, int64_t ld, int64_t M, int64_t n,
+                                                            const double* __restrict__ d, double* __restrict__ v) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+  const int64_t P0 = (int64_t)blockIdx.x * kJVB;
+  const int nv = (int)min((int64_t)kJVB, M - P0);
+  double acc[kJVB];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
-  if (w == 0) {
+  for (int j = 0; j < kJVB; ++j) acc[j] = 0.0;
+  const int64_t nw = n / W;
+  const V* rowv[kJVB];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int j = 0; j < kJVB; ++j) rowv[j] = reinterpret_cast<const V*>(L + (P0 + (j < nv ? j : 0)) * ld);
+#pragma unroll 2
+  for (int64_t i = threadIdx.x; i < nw; i += kJThreads) {
+    double dd[W];
+    if constexpr (W == 2) {
+      const double2 x = __ldg(reinterpret_cast<const double2*>(d) + i);
+      dd[0] = x.x; dd[1] = x.y;
+    } else {
+      const double2 x0 = __ldg(reinterpret_cast<const double2*>(d) + 2 * i);
+      const double2 x1 = __ldg(reinterpret_cast<const double2*>(d) + 2 * i + 1);
+      dd[0] = x0.x; dd[1] = x0.y; dd[2] = x1.x; dd[3] = x1.y;
+    }
+#pragma unroll
+    for (int j = 0; j < kJVB; ++j)
+      if (j < nv) acc[j] += dot_w(__ldg(rowv[j] + i), dd);
   }
-  return v;
+  for (int64_t r = nw * W + threadIdx.x; r < n; r += kJThreads)
+#pragma unroll
+    for (int j = 0; j < kJVB; ++j)
+      if (j < nv) acc[j] = fma((double)L[(P0 + j) * ld + r], d[r], acc[j]);
+  // CTA reduction of the kJVB sums
+  __shared__ double sh[kJThreads / 32][kJVB];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < kJVB; ++j) {
+    double x = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[w][j] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < kJVB && (int)threadIdx.x < nv) {
+    double x = 0.0;
+#pragma unroll
+    for (int k = 0; k < kJThreads / 32; ++k) x += sh[k][threadIdx.x];
+    v[P0 + threadIdx.x] = x;
+  }
 }
 
+// ---- J, pass 2: y_r = sum_P L^P_r v_P.  A thread owns W consecutive rows and
+// walks the vectors [P0, P1) of its slab (16-byte loads, coalesced across the
+// warp); with one slab it stores y, with several it adds atomically into a
+// cleared y.
 template <class T>
-__global__ void __launch_bounds__(256) gemv_rows_kernel(const T* __restrict__ L, int64_t ld, int64_t n,
-                                                        const double* __restrict__ x, double* __restrict__ y) {
-  const int64_t P = blockIdx.x;
-  const T* row = L + P * ld;
-  double s = 0.0;
-  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s = fma((double)row[r], x[r], s);
-  s = block_sum(s);
-  if (threadIdx.x == 0) y[P] = s;
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) gemv_cols_kernel(const T* __restrict__ L, int64_t ld, int64_t M, int64_t n,
-                                                        const double* __restrict__ v, double* __restrict__ y,
-                                                        int64_t pchunk) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kJThreads) j_pass2_kernel(const T* __restrict__ L, int64_t ld, int64_t M, int64_t n,
+                                                            const double* __restrict__ v, double* __restrict__ y,
+                                                            int64_t pchunk, int atomic) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::W;
+  const int64_t i = (int64_t)blockIdx.x * kJThreads + threadIdx.x;   // group of W rows
+  const int64_t r0 = i * W;
+  if (r0 >= n) return;
   const int64_t P0 = (int64_t)blockIdx.y * pchunk;
   const int64_t P1 = min(M, P0 + pchunk);
-  if (r >= n) return;
-  double s = 0.0;
-  for (int64_t P = P0; P < P1; ++P) s = fma((double)L[P * ld + r], v[P], s);
-  atomicAdd(y + r, s);
+  double a[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) a[k] = 0.0;
+  if (r0 + W <= n) {
+    const V* base = reinterpret_cast<const V*>(L) + i;
+    const int64_t ldv = ld / W;
+    int64_t P = P0;
+    for (; P + 4 <= P1; P += 4) {
+      const V l0 = __ldg(base + (P + 0) * ldv), l1 = __ldg(base + (P + 1) * ldv);
+      const V l2 = __ldg(base + (P + 2) * ldv), l3 = __ldg(base + (P + 3) * ldv);
+      axpy_w(l0, __ldg(v + P + 0), a); axpy_w(l1, __ldg(v + P + 1), a);
+      axpy_w(l2, __ldg(v + P + 2), a); axpy_w(l3, __ldg(v + P + 3), a);
+    }
+    for (; P < P1; ++P) axpy_w(__ldg(base + P * ldv), __ldg(v + P), a);
+  } else {
+    for (int64_t P = P0; P < P1; ++P)
+      for (int k = 0; k < W && r0 + k < n; ++k) a[k] = fma((double)L[P * ld + r0 + k], v[P], a[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    if (r0 + k >= n) break;
+    if (atomic) atomicAdd(y + r0 + k, a[k]);
+    else y[r0 + k] = a[k];
+  }
 }
 
 __global__ void unpack_sym_kernel(const double* __restrict__ packed, const int32_t* __restrict__ mu,
@@ -95,7 +169,8 @@ int launch_density_packed(const double* C, int N, int O, const int32_t* mu, cons
 template <class T>
 int launch_gemv_rows(const T* L, int64_t ld, int64_t M, int64_t n, const double* x, double* y, cudaStream_t st) {
   if (M <= 0) return CD_OK;
-  gemv_rows_kernel<T><<<(unsigned)M, 256, 0, st>>>(L, ld, n, x, y);
+  if (ld % Vec<T>::W) { set_error("J: vector leading dimension not a multiple of the load width"); return CD_EINVAL; }
+  j_pass1_kernel<T><<<(unsigned)((M + kJVB - 1) / kJVB), kJThreads, 0, st>>>(L, ld, M, n, x, y);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -104,18 +179,20 @@ int launch_gemv_rows(const T* L, int64_t ld, int64_t M, int64_t n, const double*
 template <class T>
 int launch_gemv_cols(const T* L, int64_t ld, int64_t M, int64_t n, const double* v, double* y, cudaStream_t st) {
   if (n <= 0) return CD_OK;
-  // y accumulates with atomics: clear it first, also when there is no vector
-  // (M = 0 gives y = 0)
-  CD_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
-  if (M <= 0) return CD_OK;
-  const int64_t tiles = (n + 255) / 256;
-  int64_t splits = (148 * 8 + tiles - 1) / tiles;
-  if (splits < 1) splits = 1;
+  if (ld % Vec<T>::W) { set_error("J: vector leading dimension not a multiple of the load width"); return CD_EINVAL; }
+  constexpr int W = Vec<T>::W;
+  const int64_t tiles = (n + (int64_t)W * kJThreads - 1) / ((int64_t)W * kJThreads);
+  // enough CTAs for two waves of 8 per SM: split the vectors into slabs when the rows alone do not give them
+  int64_t splits = (2 * 148 * 8 + tiles - 1) / tiles;
   if (splits > M) splits = M;
-  const int64_t pchunk = (M + splits - 1) / splits;
-  splits = (M + pchunk - 1) / pchunk;
+  if (splits < 1) splits = 1;
+  const int64_t pchunk = M > 0 ? (M + splits - 1) / splits : 0;
+  if (M > 0) splits = (M + pchunk - 1) / pchunk;
+  // y is stored directly by a single slab; several slabs (and M = 0: y = 0) need it cleared
+  if (splits > 1 || M <= 0) CD_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, st));
+  if (M <= 0) return CD_OK;
   dim3 grid((unsigned)tiles, (unsigned)splits);
-  gemv_cols_kernel<T><<<grid, 256, 0, st>>>(L, ld, M, n, v, y, pchunk);
+  j_pass2_kernel<T><<<grid, kJThreads, 0, st>>>(L, ld, M, n, v, y, pchunk, splits > 1 ? 1 : 0);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;

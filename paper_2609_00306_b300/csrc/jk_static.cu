@@ -81,8 +81,10 @@ extern "C" int cd_jk_coulomb_static(const cd_factor_t* f, const double* C_occ_de
   const int N = f->sys->hb.nbf;
   const int32_t* mu = f->sys->row_mu_dev;
   const int32_t* nu = f->sys->row_nu_dev;
-  // d and v are fully overwritten; Jp is cleared inside launch_gemv_cols (it
-  // accumulates with atomics) and J inside launch_unpack_sym.
+  // d and v are fully overwritten; every entry of Jp is written by
+  // launch_gemv_cols (stored by a single slab of vectors, or cleared and then
+  // accumulated by several; cleared when there is no vector), and J is cleared
+  // inside launch_unpack_sym.
   CD_TRY(launch_density_packed(C_occ_dev, N, n_occ, mu, nu, f->n, d, st));
   CD_TRY(launch_gemv_rows<double>(f->L, f->ld, f->M, f->n, d, v, st));
   CD_TRY(launch_gemv_cols<double>(f->L, f->ld, f->M, f->n, v, Jp, st));

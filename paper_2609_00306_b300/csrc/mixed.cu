@@ -68,6 +68,69 @@ __global__ void slice_kernel(const T* __restrict__ X, int64_t ldx, int64_t rows,
   for (int s = 0; s < S; ++s) dst[((int64_t)s * rows + r) * kpitch + c] = __float2bfloat16_rn(a[s]);
 }
 
+// idx[mu*N + nu] = row of the pair (max(mu, nu), min(mu, nu)); the caller
+// fills idx with -1 first, which then marks the screened-out pairs
+__global__ void pair_index_kernel(const int32_t* __restrict__ mu, const int32_t* __restrict__ nu, int64_t n, int N,
+                                  int32_t* __restrict__ idx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int a = mu[r], b = nu[r];
+  idx[(int64_t)a * N + b] = (int32_t)r;
+  idx[(int64_t)b * N + a] = (int32_t)r;
+}
+
+// One CTA per dense row (p, mu) of the chunk's vectors L^{P0+p} (symmetric
+// N x N unpacking of a packed vector): the row is gathered straight from the
+// packed vector through idx, its exponent e = frexp exponent of the row
+// maximum is found, and the row is cut into S exact 8-bit slices of
+// x / 2^e, written in the k-contiguous layout dst[s][row][kpitch] that the
+// tensor-core product loads by TMA.  The two sweeps over the row read the
+// packed vector twice; the second read comes from L2.  This replaces a dense
+// FP64/FP32 unpacking (a cleared N x N matrix per vector), a separate
+// row-exponent pass and a separate slicing pass.
+constexpr int kUnpackThreads = 128;
+template <class T, int S>
+__global__ void __launch_bounds__(kUnpackThreads) unpack_slice_kernel(const T* __restrict__ L, int64_t ld, int64_t P0,
+                                                                      const int32_t* __restrict__ idx, int N,
+                                                                      int64_t rows, int64_t kpitch,
+                                                                      int32_t* __restrict__ e,
+                                                                      __nv_bfloat16* __restrict__ dst) {
+  const int64_t row = blockIdx.x;                  // p * N + mu
+  const int64_t p = row / N, mu = row % N;
+  const T* __restrict__ Lp = L + (P0 + p) * ld;
+  const int32_t* __restrict__ ir = idx + mu * N;
+  unsigned long long m = 0;
+  for (int nu = threadIdx.x; nu < N; nu += kUnpackThreads) {
+    const int32_t r = __ldg(ir + nu);
+    if (r >= 0) m = max(m, mag_bits(__ldg(Lp + r)));
+  }
+  __shared__ unsigned long long sh[kUnpackThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+#pragma unroll
+  for (int w = 0; w < kUnpackThreads / 32; ++w) m = max(m, sh[w]);
+  int ex = 0;
+  if (m != 0) {
+    const double mx = sizeof(T) == 8 ? __longlong_as_double((long long)m) : (double)__uint_as_float((unsigned)m);
+    frexp(mx, &ex);
+  }
+  if (threadIdx.x == 0) e[row] = ex;
+  const int k = 8 * S - 1 - ex;
+  for (int64_t nu = threadIdx.x; nu < kpitch; nu += kUnpackThreads) {
+    long long v = 0;
+    if (nu < N) {
+      const int32_t r = __ldg(ir + nu);
+      if (r >= 0) v = scaled_double_to_ll(__ldg(Lp + r), k);   // integer operations only
+    }
+    float a[S];
+    fixed_digits<S>(v, a);
+#pragma unroll
+    for (int s = 0; s < S; ++s) dst[((int64_t)s * rows + row) * kpitch + nu] = __float2bfloat16_rn(a[s]);
+  }
+}
+
 // B chunk from the fixed-point product: D[i][p*N + mu] (i < O) -> Bm[mu][p*Op + i]
 __global__ void half_finalize_kernel(const unsigned long long* __restrict__ D, int64_t ldd, int Pc, int N, int O,
                                      int Op, const int32_t* __restrict__ eL, const int32_t* __restrict__ eC, int F,
@@ -117,6 +180,34 @@ int launch_slice3(const T* X, int64_t ldx, int64_t rows, int64_t k, const int32_
   return CD_OK;
 }
 
+// pair -> row table of the dense unpacking ([N][N] int32, -1 = screened out)
+int build_pair_index(const int32_t* mu, const int32_t* nu, int64_t n, int N, int32_t* idx, cudaStream_t st) {
+  CD_CUDA(cudaMemsetAsync(idx, 0xFF, sizeof(int32_t) * (size_t)N * N, st));
+  if (n <= 0) return CD_OK;
+  pair_index_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mu, nu, n, N, idx);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+// rows (p, mu) of vectors P0 .. P0+pc-1: exponents e [pc*N] and slices dst [S][pc*N][kpitch]
+template <class T>
+int launch_unpack_slice(const T* L, int64_t ld, int64_t P0, int pc, const int32_t* idx, int N, int64_t kpitch,
+                        int S, int32_t* e, void* dst, cudaStream_t st) {
+  const int64_t rows = (int64_t)pc * N;
+  if (rows <= 0) return CD_OK;
+  __nv_bfloat16* d = (__nv_bfloat16*)dst;
+  const unsigned grid = (unsigned)rows;
+  if (S == 3) unpack_slice_kernel<T, 3><<<grid, kUnpackThreads, 0, st>>>(L, ld, P0, idx, N, rows, kpitch, e, d);
+  else if (S == 4) unpack_slice_kernel<T, 4><<<grid, kUnpackThreads, 0, st>>>(L, ld, P0, idx, N, rows, kpitch, e, d);
+  else if (S == 5) unpack_slice_kernel<T, 5><<<grid, kUnpackThreads, 0, st>>>(L, ld, P0, idx, N, rows, kpitch, e, d);
+  else if (S == 7) unpack_slice_kernel<T, 7><<<grid, kUnpackThreads, 0, st>>>(L, ld, P0, idx, N, rows, kpitch, e, d);
+  else { set_error("unpack_slice: unsupported slice count"); return CD_EINVAL; }
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
 int ilog2_ceil(int64_t v) {
   int l = 0;
   while ((1ll << l) < v) ++l;
@@ -138,7 +229,6 @@ int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* d
 namespace {
 struct MixedBufs {
   cudaStream_t st = nullptr;
-  void* Lfull = nullptr;
   void* Ls = nullptr;
   void* Cs = nullptr;
   double* Ct = nullptr;
@@ -147,10 +237,11 @@ struct MixedBufs {
   double* Bm = nullptr;
   void* Bs = nullptr;
   double *d = nullptr, *v = nullptr, *Jp = nullptr;
+  int32_t* idx = nullptr;
   int* err = nullptr;
   ~MixedBufs() {
-    for (void* p : {Lfull, Ls, Cs, (void*)Ct, (void*)eL, (void*)eC, (void*)eB, (void*)D1, (void*)D2, (void*)Bm,
-                    Bs, (void*)d, (void*)v, (void*)Jp, (void*)err})
+    for (void* p : {Ls, Cs, (void*)Ct, (void*)eL, (void*)eC, (void*)eB, (void*)D1, (void*)D2, (void*)Bm,
+                    Bs, (void*)d, (void*)v, (void*)Jp, (void*)idx, (void*)err})
       scratch_free(p, st);
   }
 };
@@ -198,7 +289,7 @@ int jk_mixed_t(const TL* L32, int64_t ld, int64_t M, int64_t n, int N, int O, co
   StageTimer tm;
   tm.on = getenv("CDERI_TIMING") != nullptr;
   tm.st = st;
-  const char* names[] = {"start", "J", "unpack", "slice_L", "gemm_BLC", "finalize_B", "slice_B", "gemm_K", "accum_K"};
+  const char* names[] = {"start", "J", "unused", "unpack_slice_L", "gemm_BLC", "finalize_B", "slice_B", "gemm_K", "accum_K"};
   tm.mark(0);
   MixedBufs b;
   b.st = st;
@@ -216,9 +307,10 @@ int jk_mixed_t(const TL* L32, int64_t ld, int64_t M, int64_t n, int N, int O, co
     const int64_t Np = (N + 7) / 8 * 8;                     // k pitch of the first product (16-byte rows)
     const int Op = (O + 63) / 64 * 64;                      // padded occupied count (k blocks of the second product)
     // chunk of vectors: k-dim of the second product Pc*Op, scratch ~ Pc*N^2*(4 + 6) bytes
-    int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(M, (int64_t)(2.0e9 / ((sizeof(TL) + 2.0 * S) * N * (double)N))));
+    int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(M, (int64_t)(2.0e9 / (2.0 * S * N * (double)N))));
     Pc = std::min(Pc, 64);
-    CD_TRY(scratch_alloc((TL**)&b.Lfull, (size_t)Pc * N * N, st));
+    CD_TRY(scratch_alloc(&b.idx, (size_t)N * N, st));
+    CD_TRY(build_pair_index(mu, nu, n, N, b.idx, st));
     CD_TRY(scratch_alloc((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np, st));
     CD_TRY(scratch_alloc((uint16_t**)&b.Cs, (size_t)S * O * Np, st));
     CD_TRY(scratch_alloc(&b.Ct, (size_t)O * N, st));
@@ -242,13 +334,9 @@ int jk_mixed_t(const TL* L32, int64_t ld, int64_t M, int64_t n, int N, int O, co
     p2.SA = p2.SB = S; p2.KEEP = S + 1;
     for (int64_t P0 = 0; P0 < M; P0 += Pc) {
       const int pc = (int)std::min<int64_t>(Pc, M - P0);
-      // dense FP32 L^P rows (p, mu), their exponents and slices
+      // rows (p, mu) of the dense L^P gathered from the packed vectors, their exponents and slices
       tm.mark(0);
-      TL* Lf = (TL*)b.Lfull;
-      CD_TRY(launch_unpack_vectors<TL>(L32, ld, P0, pc, mu, nu, n, N, Lf, st));
-      tm.mark(2);
-      CD_TRY(launch_row_exp_warp<TL>(Lf, N, (int64_t)pc * N, N, b.eL, st));
-      CD_TRY(launch_slice3<TL>(Lf, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+      CD_TRY(launch_unpack_slice<TL>(L32, ld, P0, pc, b.idx, N, Np, S, b.eL, b.Ls, st));
       tm.mark(3);
       // B^P = L^P C for the chunk: D1[i][p*N+mu]
       CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * O * pc * N, st));
@@ -317,7 +405,7 @@ int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64
                       cudaStream_t st) {
   if (nP <= 0) return CD_OK;
   const int64_t Np = (N + 7) / 8 * 8;
-  int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(nP, (int64_t)(1.5e9 / ((8.0 + 2.0 * S) * N * (double)N))));
+  int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(nP, (int64_t)(1.5e9 / (2.0 * S * N * (double)N))));
   Pc = std::min(Pc, 64);
   MixedBufs b;
   b.st = st;
@@ -329,7 +417,8 @@ int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64
     int32_t** e;
     ~Extra() { scratch_free(*d3, st); scratch_free(*e, st); }
   } extra{st, &D3, &eBt};
-  CD_TRY(scratch_alloc((double**)&b.Lfull, (size_t)Pc * N * N, st));
+  CD_TRY(scratch_alloc(&b.idx, (size_t)N * N, st));
+  CD_TRY(build_pair_index(mu, nu, n, N, b.idx, st));
   CD_TRY(scratch_alloc((uint16_t**)&b.Ls, (size_t)S * Pc * N * Np, st));
   CD_TRY(scratch_alloc((uint16_t**)&b.Cs, (size_t)S * n_mo * Np, st));
   CD_TRY(scratch_alloc(&b.Ct, (size_t)n_mo * N, st));
@@ -352,10 +441,7 @@ int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64
   pl.F = 61 - ilog2_ceil(N);
   for (int64_t Q0 = P0; Q0 < P0 + nP; Q0 += Pc) {
     const int pc = (int)std::min<int64_t>(Pc, P0 + nP - Q0);
-    double* Lf = (double*)b.Lfull;
-    CD_TRY(launch_unpack_vectors<double>(L, ld, Q0, pc, mu, nu, n, N, Lf, st));
-    CD_TRY(launch_row_exp_warp<double>(Lf, N, (int64_t)pc * N, N, b.eL, st));
-    CD_TRY(launch_slice3<double>(Lf, N, (int64_t)pc * N, N, b.eL, b.Ls, Np, S, st));
+    CD_TRY(launch_unpack_slice<double>(L, ld, Q0, pc, b.idx, N, Np, S, b.eL, b.Ls, st));
     // B^P[mu][i]: D1[i][p*N + mu]
     CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * n_mo * pc * N, st));
     CD_TRY(ozaki_gemm(pl, b.Ls, (int64_t)pc * N, Np, b.Cs, n_mo, Np, N, b.D1, (int64_t)pc * N, 1, b.err, st));

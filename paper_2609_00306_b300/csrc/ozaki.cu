@@ -445,8 +445,7 @@ extern "C" int cd_set_wait_limit(double seconds, double* previous) {
     set_error("cd_set_wait_limit: seconds must be in [0, 3600]");
     return CD_EINVAL;
   }
-  const double ns = seconds * 1e9;
-  g_wait_ns.store(ns < 1.0 ? 1ull : (unsigned long long)ns);
+  g_wait_ns.store((unsigned long long)(seconds * 1e9));
   return CD_OK;
 }
 

@@ -55,21 +55,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false when it gave up (time limit, or another CTA/role gave up)
+// non-blocking probe of a phase
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false when it gave up (time limit, or another CTA/role gave
+// up).  limit_ns = 0 gives up at the first wait whose phase is not already
+// complete (the test of this error path).  try_wait itself may suspend the
+// thread for a hardware-defined time, so the clock is read on every retry.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                           int which, unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 0u) {
-      if (*abort_flag || (err && *(volatile int*)err)) { *abort_flag = 1; return false; }
-      if (globaltimer_ns() - t0 > limit_ns) {
-        *abort_flag = 1;
-        if (err) atomicOr(err, which);
-        return false;
-      }
+  for (uint32_t it = 0;; ++it) {
+    if (limit_ns == 0 || globaltimer_ns() - t0 > limit_ns) {
+      *abort_flag = 1;
+      if (err) atomicOr(err, which);
+      return false;
     }
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 15u) == 15u && (*abort_flag || (err && *(volatile int*)err))) { *abort_flag = 1; return false; }
   }
 }
 // wait for work this CTA already issued (a TMA copy or an MMA commit) after an

@@ -1,7 +1,8 @@
 """Error paths and degenerate inputs on the GPU, made on the host (no GPU fault):
 
 * CD_ETIMEOUT: the tensor-core pipeline's bounded waits, with their limit set
-  to 1 ns through cd_set_wait_limit, give up; every CTA lets its in-flight
+  to 0 through cd_set_wait_limit (give up at the first wait whose phase is not
+  already complete), give up; every CTA lets its in-flight
   copies and MMAs finish, frees its tensor memory and returns, and the call
   reports CD_ETIMEOUT.  The same process then runs a normal product on the
   same device and checks it.
@@ -38,7 +39,7 @@ def test_bounded_wait_times_out_and_device_stays_usable():
     rng = np.random.default_rng(3)
     X = torch.tensor(rng.standard_normal((1024, 2048)), device="cuda")
     Y = torch.tensor(rng.standard_normal((256, 2048)), device="cuda")
-    prev = cd.set_wait_limit(1e-9)
+    prev = cd.set_wait_limit(0.0)
     try:
         with pytest.raises(cd.CDError) as e:
             slice_matmul(X, Y, 7)
@@ -58,7 +59,7 @@ def test_bounded_wait_timeout_inside_the_decomposition():
     factorisation follows on the same device."""
     import paper_2609_00306_b300 as cd
     s = synth.make_workload("sp18")
-    prev = cd.set_wait_limit(1e-9)
+    prev = cd.set_wait_limit(0.0)
     try:
         with pytest.raises(cd.CDError) as e:
             cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
