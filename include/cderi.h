@@ -214,6 +214,15 @@ int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, d
  * operation counts of their recurrences); [13] first-step ms, [14] first-step
  * macro iterations, [15] first-step ERI columns of CD_ALG_TWOSTEP (0 otherwise). */
 int cd_factor_stats(const cd_factor_t* f, double* stats16);
+/* Device memory of the decomposition (measurement; the paper reports the
+ * memory of its runs, e.g. the CV storage of Sec. 4.1): *peak_bytes = the
+ * scratch pool's high-water mark during the call (residual diagonals, column
+ * pool, BF16 slices of the vectors, ...) plus the vector array at its final
+ * capacity -- both are largest together, at the end of the pivot loop; in a
+ * batch the pool figure includes the systems running at the same time.
+ * *resident_bytes = what the factor keeps afterwards (vectors, and their FP32
+ * copy with CD_VEC_FP32).  Either output may be NULL. */
+int cd_factor_memory(const cd_factor_t* f, double* peak_bytes, double* resident_bytes);
 /* Number of CUDA kernel launches issued by this library in this process
  * (measurement; no counterpart in the paper). */
 long long cd_kernel_launches(void);

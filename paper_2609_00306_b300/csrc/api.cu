@@ -292,6 +292,20 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   uint8_t* cand_dev = nullptr;       // [n] candidate mask (working rows)
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   EriStreams eri;                    // concurrent launches of the three ERI class kernels
+  // device-driven pivot steps (full pivoting): state, slot map, pivots, and the
+  // CUDA graph of b step launches (re-captured when its buffers move)
+  DevStep* ds_dev = nullptr;
+  DevStep ds_h;
+  int32_t* slot_of_row = nullptr;
+  int64_t* piv_dev = nullptr;
+  double* pivd_dev = nullptr;
+  int64_t* sm_rows = nullptr;
+  int32_t* sm_slots = nullptr;
+  std::vector<int64_t> piv_h;
+  std::vector<double> pivd_h;
+  cudaStream_t cap_st = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  const void* step_key[3] = {nullptr, nullptr, nullptr};   // L, pool, D buffers the graph was captured with
   // second stream for the sliced update, used only with CDERI_OVERLAP_UPDATE=1
   // (by default the update runs on the main stream before the ERI columns)
   cudaStream_t st2 = nullptr;
@@ -308,6 +322,11 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {eri.fork, eri.join[0], eri.join[1]}) if (e) cudaEventDestroy(e);
+    for (void* p : {(void*)ds_dev, (void*)slot_of_row, (void*)piv_dev, (void*)pivd_dev, (void*)sm_rows,
+                    (void*)sm_slots})
+      scratch_free(p, st);
+    if (step_exec) cudaGraphExecDestroy(step_exec);
+    if (cap_st) cudaStreamDestroy(cap_st);
     for (cudaStream_t x : eri.side) if (x) cudaStreamDestroy(x);
     for (cudaEvent_t e : {ev_ready, ev_gemm, ev_g0, ev_g1}) if (e) cudaEventDestroy(e);
     if (st2) cudaStreamDestroy(st2);
@@ -385,6 +404,21 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   f->n = n;
   f->ld = ld;
   f->vec_precision = o->vec_precision;
+  // device-memory accounting: scratch comes from the default pool (its
+  // high-water mark is reset here), the vector arrays from cudaMalloc
+  cudaMemPool_t mpool = nullptr;
+  uint64_t pool_used0 = 0;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&mpool, dev) == cudaSuccess) {
+      uint64_t zero = 0;
+      cudaMemPoolSetAttribute(mpool, cudaMemPoolAttrUsedMemHigh, &zero);
+      cudaMemPoolGetAttribute(mpool, cudaMemPoolAttrUsedMemCurrent, &pool_used0);
+    } else {
+      mpool = nullptr;
+      cudaGetLastError();
+    }
+  }
   Work w;
   w.st = st;
   CD_TRY(dalloc(&f->L, (size_t)Mcap * ld));
@@ -435,6 +469,20 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   for (auto& x : w.eri.side) CD_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
   CD_CUDA(cudaEventCreateWithFlags(&w.eri.fork, cudaEventDisableTiming));
   for (auto& e : w.eri.join) CD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  // full pivoting runs the in-block steps on the device (CDERI_HOST_STEPS=1: one
+  // host round trip per step instead)
+  const bool dev_steps = !forced && !span_mode && !reduce && getenv("CDERI_HOST_STEPS") == nullptr;
+  if (dev_steps) {
+    CD_TRY(scratch_alloc(&w.ds_dev, 1, st));
+    CD_TRY(scratch_alloc(&w.slot_of_row, (size_t)std::max<int64_t>(n, 1), st));
+    CD_TRY(scratch_alloc(&w.piv_dev, (size_t)Mmax, st));
+    CD_TRY(scratch_alloc(&w.pivd_dev, (size_t)Mmax, st));
+    CD_TRY(scratch_alloc(&w.sm_rows, (size_t)b, st));
+    CD_TRY(scratch_alloc(&w.sm_slots, (size_t)b, st));
+    CD_CUDA(cudaStreamCreateWithFlags(&w.cap_st, cudaStreamNonBlocking));
+    w.piv_h.resize(b);
+    w.pivd_h.resize(b);
+  }
   if (slice) {
     CD_CUDA(cudaStreamCreateWithFlags(&w.st2, cudaStreamNonBlocking));
     CD_CUDA(cudaEventCreateWithFlags(&w.ev_ready, cudaEventDisableTiming));
@@ -741,7 +789,107 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     }
     CD_CUDA(cudaStreamSynchronize(st));  // columns of this block are complete
     const double t_blk = now_ms();
-    // ---- serial pivot steps inside the block
+    if (dev_steps) {
+      // ---- the block's pivot steps on the device: one upload of the state,
+      // one graph launch of b step kernels, one read-back
+      std::vector<int64_t> srows;
+      std::vector<int32_t> sslots;
+      for (int sl = 0; sl < b; ++sl)
+        if (slot_row[sl] >= 0) { srows.push_back(slot_row[sl]); sslots.push_back(sl); }
+      const int nocc = (int)srows.size();
+      if (K + nocc > f->Mcap && f->Mcap < Mmax) {
+        int64_t nc = std::min<int64_t>(Mmax, std::max<int64_t>(K + nocc, f->Mcap + f->Mcap / 4 + 64));
+        if (fixed + per_vec * nc > budget) nc = (int64_t)((budget - fixed) / per_vec);
+        if (nc > f->Mcap) CD_TRY(grow_vectors(f, &w, slice, b, nc, K, st));
+      }
+      if (nocc > 0) {
+        CD_CUDA(cudaMemcpyAsync(w.sm_rows, srows.data(), sizeof(int64_t) * nocc, cudaMemcpyHostToDevice, st));
+        CD_CUDA(cudaMemcpyAsync(w.sm_slots, sslots.data(), sizeof(int32_t) * nocc, cudaMemcpyHostToDevice, st));
+      }
+      CD_TRY(launch_slot_map(w.slot_of_row, n, w.sm_rows, w.sm_slots, nocc, st));
+      w.ds_h.res = res;
+      w.ds_h.K = K;
+      w.ds_h.Kb = K;
+      w.ds_h.Kcap = f->Mcap;
+      w.ds_h.Dcur0 = Dcur;
+      w.ds_h.Dnext0 = Dnext;
+      w.ds_h.tau = tau;
+      w.ds_h.done = 0;
+      w.ds_h.reason = 0;
+      CD_CUDA(cudaMemcpyAsync(w.ds_dev, &w.ds_h, sizeof(DevStep), cudaMemcpyHostToDevice, st));
+      if (!w.step_exec || w.step_key[0] != f->L || w.step_key[1] != w.pool) {
+        if (w.step_exec) { cudaGraphExecDestroy(w.step_exec); w.step_exec = nullptr; }
+        cudaGraph_t g = nullptr;
+        CD_CUDA(cudaStreamBeginCapture(w.cap_st, cudaStreamCaptureModeThreadLocal));
+        int crc = CD_OK;
+        for (int i = 0; i < b && crc == CD_OK; ++i)
+          crc = launch_finalize_dev(w.ds_dev, w.slot_of_row, w.pool, f->L, ld, n, neg_tol, cmask, w.piv_dev,
+                                    w.pivd_dev, w.sc, w.cap_st);
+        cudaError_t ce = cudaStreamEndCapture(w.cap_st, &g);
+        count_launch(-b);   // counted below, per graph launch
+        if (crc != CD_OK) { if (g) cudaGraphDestroy(g); return crc; }
+        if (ce != cudaSuccess) { set_error(std::string("step graph capture: ") + cudaGetErrorString(ce)); return CD_ECUDA; }
+        ce = cudaGraphInstantiate(&w.step_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) { set_error(std::string("step graph: ") + cudaGetErrorString(ce)); return CD_ECUDA; }
+        w.step_key[0] = f->L;
+        w.step_key[1] = w.pool;
+      }
+      CD_CUDA(cudaGraphLaunch(w.step_exec, st));
+      count_launch(b);
+      CD_CUDA(cudaMemcpyAsync(&w.ds_h, w.ds_dev, sizeof(DevStep), cudaMemcpyDeviceToHost, st));
+      // at most min(nocc, Mcap - K) steps can have run (piv_dev holds Mmax >= Mcap entries)
+      const int64_t ncopy = std::min<int64_t>(nocc, f->Mcap - K);
+      if (ncopy > 0) {
+        CD_CUDA(cudaMemcpyAsync(w.piv_h.data(), w.piv_dev + K, sizeof(int64_t) * ncopy, cudaMemcpyDeviceToHost, st));
+        CD_CUDA(cudaMemcpyAsync(w.pivd_h.data(), w.pivd_dev + K, sizeof(double) * ncopy, cudaMemcpyDeviceToHost, st));
+      }
+      CD_CUDA(cudaStreamSynchronize(st));
+      const int64_t Knew = w.ds_h.K;
+      if (Knew < K || Knew > K + std::max<int64_t>(ncopy, 0)) {
+        set_error("internal: device step count out of range");
+        return CD_EINVAL;
+      }
+      for (int64_t k = K; k < Knew; ++k) {
+        const int64_t p = w.piv_h[k - K];
+        f->piv.push_back(p);
+        f->gaps.push_back(0.0);
+        f->pivd.push_back(w.pivd_h[k - K]);
+        auto it = row2slot.find(p);
+        if (it == row2slot.end()) { set_error("internal: device step took a row outside the block"); return CD_EINVAL; }
+        slot_row[it->second] = -1;
+        row2slot.erase(it);
+      }
+      if ((Knew - K) & 1) std::swap(Dcur, Dnext);
+      res = w.ds_h.res;
+      const bool stepped = Knew > K;
+      K = Knew;
+      if (stepped) {
+        float a = 0, c = 0;
+        cudaEventElapsedTime(&a, w.ev[0], w.ev[1]);
+        if (slice) {
+          if (gemm_issued) cudaEventElapsedTime(&c, w.ev_g0, w.ev_g1);
+        } else {
+          cudaEventElapsedTime(&c, w.ev[1], w.ev[2]);
+        }
+        t_eri += a;
+        t_upd += c;
+        first = false;
+      }
+      const int reason = w.ds_h.done ? w.ds_h.reason : 0;
+      if (reason == kStepNotPsd) {
+        if (res.bad) set_error("residual diagonal below -1e-10 max D (matrix not PSD) after step " + std::to_string(K));
+        else set_error("pivot diagonal not positive (matrix not PSD) at step " + std::to_string(K));
+        return CD_ENOTPSD;
+      }
+      if (reason == kStepCapacity) {
+        if (f->Mcap >= Mmax) set_error("number of vectors exceeds max_vectors = " + std::to_string(Mmax));
+        else set_error("device memory budget exhausted at M = " + std::to_string(K));
+        return CD_ENOMEM;
+      }
+      if (reason == kStepConverged) done = true;
+    } else
+    // ---- serial pivot steps inside the block, one host round trip each
     for (;;) {
       int64_t p;
       double dp;
@@ -874,10 +1022,18 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   scratch_free(w.Ls, st); w.Ls = nullptr;
   scratch_free(w.Bs, st); w.Bs = nullptr;
   scratch_free(w.pool, st); w.pool = nullptr;
+  if (mpool) {
+    uint64_t high = 0;
+    cudaMemPoolGetAttribute(mpool, cudaMemPoolAttrUsedMemHigh, &high);
+    // the slices and the vectors are both at their largest at the end of the loop
+    f->mem_peak = (double)(high > pool_used0 ? high - pool_used0 : 0) + 8.0 * (double)f->Mcap * (double)ld;
+  }
   if (f->vec_precision == CD_VEC_FP32 && K > 0) {
     CD_TRY(dalloc(&f->L32, (size_t)K * ld));
     CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
+    f->mem_peak = std::max(f->mem_peak, 8.0 * (double)f->Mcap * ld + 4.0 * (double)K * ld);
   }
+  f->mem_resident = 8.0 * (double)f->Mcap * ld + (f->L32 ? 4.0 * (double)K * ld : 0.0);
   CD_CUDA(cudaStreamSynchronize(st));
   const double t_all = now_ms() - t_start;
   f->stats[0] = s->ms_setup;
@@ -1034,6 +1190,13 @@ int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packe
     if (gaps) gaps[k] = f->gaps[k];
   }
   if (resid_diag && f->n > 0) std::memcpy(resid_diag, f->resid.data(), sizeof(double) * f->n);
+  return CD_OK;
+}
+
+int cd_factor_memory(const cd_factor_t* f, double* peak_bytes, double* resident_bytes) {
+  if (!f) { set_error("cd_factor_memory: factor is NULL"); return CD_EINVAL; }
+  if (peak_bytes) *peak_bytes = f->mem_peak;
+  if (resident_bytes) *resident_bytes = f->mem_resident;
   return CD_OK;
 }
 

@@ -20,6 +20,7 @@ struct Status {
   do {                                                                        \
     cudaError_t _e = (call);                                                  \
     if (_e != cudaSuccess) {                                                  \
+      cudaGetLastError(); /* a non-sticky error must not leak into later calls */ \
       ::cd::set_error(std::string("CUDA: ") + cudaGetErrorString(_e) + " at " \
                       + __FILE__ + ":" + std::to_string(__LINE__));           \
       return CD_ECUDA;                                                        \
@@ -200,4 +201,6 @@ struct cd_factor {
   std::vector<double> resid;
   double resid_max = 0.0;
   double stats[16] = {0};
+  double mem_peak = 0.0;       // device bytes at the decomposition's peak (pool high-water mark + vector arrays)
+  double mem_resident = 0.0;   // device bytes the factor keeps after the call
 };

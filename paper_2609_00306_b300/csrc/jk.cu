@@ -2,6 +2,7 @@
 // (Sec. 4.1).  Packed density d_r = D_{mu nu} (2 - delta_{mu nu}), D = 2 C C^T.
 //   J: v_P = sum_r L^P_r d_r (pass 1 over L), J_r = sum_P L^P_r v_P (pass 2).
 //   K: B^P = unpack(L^P) C (N x O), K = 2 sum_P B^P B^P^T.
+#include <algorithm>
 #include "internal.cuh"
 #include "pivot.cuh"
 
@@ -41,9 +42,13 @@ __device__ __forceinline__ void axpy_w(float4 l, double vp, double* a) {
 constexpr int kJThreads = 256;
 constexpr int kJVB = 4;   // vectors per CTA in pass 1
 
+// grid (vector groups, row slabs): a CTA covers groups of W rows [w0, w1) of
+// its vectors and adds its partial sums into v (cleared by the launcher), so
+// that the grid is many waves deep and the last wave is short
 template <class T>
 __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict__ L, int64_t ld, int64_t M, int64_t n,
-                                                            const double* __restrict__ d, double* __restrict__ v) {
+                                                            const double* __restrict__ d, double* __restrict__ v,
+                                                            int64_t wchunk) {
   using V = typename Vec<T>::V;
   constexpr int W = Vec<T>::W;
   const int64_t P0 = (int64_t)blockIdx.x * kJVB;
@@ -52,11 +57,13 @@ __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict_
 #pragma unroll
   for (int j = 0; j < kJVB; ++j) acc[j] = 0.0;
   const int64_t nw = n / W;
+  const int64_t w0 = (int64_t)blockIdx.y * wchunk;
+  const int64_t w1 = min(nw, w0 + wchunk);
   const V* rowv[kJVB];
 #pragma unroll
   for (int j = 0; j < kJVB; ++j) rowv[j] = reinterpret_cast<const V*>(L + (P0 + (j < nv ? j : 0)) * ld);
 #pragma unroll 2
-  for (int64_t i = threadIdx.x; i < nw; i += kJThreads) {
+  for (int64_t i = w0 + threadIdx.x; i < w1; i += kJThreads) {
     double dd[W];
     if constexpr (W == 2) {
       const double2 x = __ldg(reinterpret_cast<const double2*>(d) + i);
@@ -70,10 +77,11 @@ __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict_
     for (int j = 0; j < kJVB; ++j)
       if (j < nv) acc[j] += dot_w(__ldg(rowv[j] + i), dd);
   }
-  for (int64_t r = nw * W + threadIdx.x; r < n; r += kJThreads)
+  if (blockIdx.y == gridDim.y - 1)   // the rows past the last whole group of W
+    for (int64_t r = nw * W + threadIdx.x; r < n; r += kJThreads)
 #pragma unroll
-    for (int j = 0; j < kJVB; ++j)
-      if (j < nv) acc[j] = fma((double)L[(P0 + j) * ld + r], d[r], acc[j]);
+      for (int j = 0; j < kJVB; ++j)
+        if (j < nv) acc[j] = fma((double)L[(P0 + j) * ld + r], d[r], acc[j]);
   // CTA reduction of the kJVB sums
   __shared__ double sh[kJThreads / 32][kJVB];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict_
     double x = 0.0;
 #pragma unroll
     for (int k = 0; k < kJThreads / 32; ++k) x += sh[k][threadIdx.x];
-    v[P0 + threadIdx.x] = x;
+    atomicAdd(v + P0 + threadIdx.x, x);
   }
 }
 
@@ -166,11 +174,23 @@ int launch_density_packed(const double* C, int N, int O, const int32_t* mu, cons
   return CD_OK;
 }
 
+// resident CTAs of the J kernels (256 threads, < 64 registers: 8 per SM) and the
+// grid depth aimed at, in waves
+constexpr int64_t kJResident = 148 * 8;
+constexpr int64_t kJWaves = 8;
+
 template <class T>
 int launch_gemv_rows(const T* L, int64_t ld, int64_t M, int64_t n, const double* x, double* y, cudaStream_t st) {
   if (M <= 0) return CD_OK;
   if (ld % Vec<T>::W) { set_error("J: vector leading dimension not a multiple of the load width"); return CD_EINVAL; }
-  j_pass1_kernel<T><<<(unsigned)((M + kJVB - 1) / kJVB), kJThreads, 0, st>>>(L, ld, M, n, x, y);
+  const int64_t groups = (M + kJVB - 1) / kJVB;
+  const int64_t nw = n / Vec<T>::W;
+  int64_t rs = (kJWaves * kJResident + groups - 1) / groups;          // row slabs per vector group
+  rs = std::max<int64_t>(1, std::min<int64_t>(rs, (nw + kJThreads - 1) / kJThreads));
+  const int64_t wchunk = std::max<int64_t>(1, (nw + rs - 1) / rs);
+  rs = std::max<int64_t>(1, (nw + wchunk - 1) / wchunk);
+  CD_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * M, st));
+  j_pass1_kernel<T><<<dim3((unsigned)groups, (unsigned)rs), kJThreads, 0, st>>>(L, ld, M, n, x, y, wchunk);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -182,8 +202,8 @@ int launch_gemv_cols(const T* L, int64_t ld, int64_t M, int64_t n, const double*
   if (ld % Vec<T>::W) { set_error("J: vector leading dimension not a multiple of the load width"); return CD_EINVAL; }
   constexpr int W = Vec<T>::W;
   const int64_t tiles = (n + (int64_t)W * kJThreads - 1) / ((int64_t)W * kJThreads);
-  // enough CTAs for two waves of 8 per SM: split the vectors into slabs when the rows alone do not give them
-  int64_t splits = (2 * 148 * 8 + tiles - 1) / tiles;
+  // split the vectors into slabs so that the grid is kJWaves waves deep
+  int64_t splits = (kJWaves * kJResident + tiles - 1) / tiles;
   if (splits > M) splits = M;
   if (splits < 1) splits = 1;
   const int64_t pchunk = M > 0 ? (M + splits - 1) / splits : 0;

@@ -128,6 +128,123 @@ __global__ void __launch_bounds__(kStepThreads) finalize_kernel(
   grid_finish(bv, bi, bad, sc, res);
 }
 
+// One device-driven step (see DevStep).  Thread 0 of every CTA reads the
+// state; all CTAs reach the same decision because the state only changes at
+// the end of a step, after every CTA of that step has read it (the last CTA to
+// finish writes it).
+__global__ void __launch_bounds__(kStepThreads) finalize_dev_kernel(
+    DevStep* __restrict__ ds, int32_t* __restrict__ slot_of_row, const double* __restrict__ pool,
+    const double* __restrict__ L, int64_t ld, int64_t n, double neg_tol, const uint8_t* __restrict__ cand,
+    int64_t* __restrict__ piv, double* __restrict__ pivd, StepScratch* sc) {
+  __shared__ int s_go;
+  __shared__ int64_t s_p, s_K, s_Kb;
+  __shared__ int s_slot, s_odd;
+  __shared__ double s_dp;
+  __shared__ double g[kMaxBlock];
+  if (threadIdx.x == 0) {
+    const volatile DevStep* v = ds;
+    int reason = 0;
+    const int64_t K = v->K, Kb = v->Kb, idx = v->res.idx;
+    const double dmax = v->res.dmax;
+    int slot = -1;
+    double dp = 0.0;
+    const int odd = (int)((K - Kb) & 1);
+    if (v->done) reason = -1;
+    else if (v->res.bad) reason = kStepNotPsd;
+    else if (!(dmax >= v->tau) || idx < 0 || idx >= n) reason = kStepConverged;
+    else if (K >= v->Kcap || K - Kb >= kMaxBlock) reason = kStepCapacity;
+    else {
+      slot = slot_of_row[idx];
+      if (slot < 0) reason = kStepOutside;
+      else {
+        const double* Din = odd ? v->Dnext0 : v->Dcur0;
+        dp = Din[idx];
+        if (!(dp > 0.0)) reason = kStepNotPsd;
+      }
+    }
+    s_go = reason == 0;
+    s_p = idx; s_K = K; s_Kb = Kb; s_slot = slot; s_odd = odd; s_dp = dp;
+    if (reason > 0 && blockIdx.x == 0) {
+      ds->done = 1;
+      ds->reason = reason;
+    }
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const int64_t prow = s_p, K = s_K, Kb = s_Kb;
+  const double* Din = s_odd ? ds->Dnext0 : ds->Dcur0;
+  double* Dout = s_odd ? const_cast<double*>(ds->Dcur0) : ds->Dnext0;
+  const double* col = pool + (int64_t)s_slot * ld;
+  double* Lout = const_cast<double*>(L) + K * ld;
+  const int nk = (int)(K - Kb);
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) g[k] = L[(Kb + k) * ld + prow];
+  __syncthreads();
+  const double inv = 1.0 / sqrt(s_dp);
+  double bv = -DBL_MAX;
+  int64_t bi = INT64_MAX;
+  int bad = 0;
+  const double* Lb = L + Kb * ld;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double acc = col[r];
+    int k = 0;
+    for (; k + 4 <= nk; k += 4) {
+      double a0 = Lb[(k + 0) * ld + r], a1 = Lb[(k + 1) * ld + r];
+      double a2 = Lb[(k + 2) * ld + r], a3 = Lb[(k + 3) * ld + r];
+      acc = fma(-a0, g[k + 0], acc);
+      acc = fma(-a1, g[k + 1], acc);
+      acc = fma(-a2, g[k + 2], acc);
+      acc = fma(-a3, g[k + 3], acc);
+    }
+    for (; k < nk; ++k) acc = fma(-Lb[k * ld + r], g[k], acc);
+    const double vv = acc * inv;
+    Lout[r] = vv;
+    const double d = fma(-vv, vv, Din[r]);
+    Dout[r] = d;
+    if (d < neg_tol) bad = 1;
+    if ((!cand || cand[r]) && better(d, r, bv, bi)) { bv = d; bi = r; }
+  }
+  block_argmax(bv, bi);
+  // grid finish: the last CTA reduces the partial argmaxes and advances the state
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    sc->part_val[blockIdx.x] = bv;
+    sc->part_idx[blockIdx.x] = bi;
+    if (bad) atomicOr(&sc->bad, 1);
+    __threadfence();
+    unsigned t = atomicAdd(&sc->counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  bv = -DBL_MAX;
+  bi = INT64_MAX;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    double v2 = ((volatile double*)sc->part_val)[b];
+    int64_t i2 = ((volatile int64_t*)sc->part_idx)[b];
+    if (better(v2, i2, bv, bi)) { bv = v2; bi = i2; }
+  }
+  block_argmax(bv, bi);
+  if (threadIdx.x == 0) {
+    ds->res.dmax = bv;
+    ds->res.idx = bi;
+    ds->res.bad = *(volatile int*)&sc->bad;
+    sc->bad = 0;
+    sc->counter = 0;
+    piv[K] = prow;
+    pivd[K] = s_dp;
+    slot_of_row[prow] = -1;
+    ds->K = K + 1;
+    __threadfence();
+  }
+}
+
+__global__ void slot_map_kernel(int32_t* __restrict__ slot_of_row, const int64_t* __restrict__ rows,
+                                const int32_t* __restrict__ slots, int nb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nb) slot_of_row[rows[j]] = slots[j];
+}
+
 // Bg[k][j] = L[k][rows[j]] for k in [k0, k1), j < nb (row-major, leading dim nb)
 __global__ void gather_kernel(const double* __restrict__ L, int64_t ld, const int64_t* __restrict__ rows, int nb,
                               int64_t k0, int64_t k1, double* __restrict__ Bg) {
@@ -227,6 +344,26 @@ int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, 
   if (K - Kb > kMaxBlock) { set_error("finalize: block too large"); return CD_EINVAL; }
   finalize_kernel<<<kStepGrid, kStepThreads, 0, st>>>(col, L, ld, Kb, K, prow, Din, Dout, Lout, n, neg_tol, cand, sc,
                                                       res);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_finalize_dev(DevStep* ds, int32_t* slot_of_row, const double* pool, const double* L, int64_t ld,
+                        int64_t n, double neg_tol, const uint8_t* cand, int64_t* piv, double* pivd,
+                        StepScratch* sc, cudaStream_t st) {
+  finalize_dev_kernel<<<kStepGrid, kStepThreads, 0, st>>>(ds, slot_of_row, pool, L, ld, n, neg_tol, cand, piv, pivd,
+                                                          sc);
+  count_launch();
+  CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int launch_slot_map(int32_t* slot_of_row, int64_t n, const int64_t* rows, const int32_t* slots, int nb,
+                    cudaStream_t st) {
+  if (n > 0) CD_CUDA(cudaMemsetAsync(slot_of_row, 0xFF, sizeof(int32_t) * n, st));
+  if (nb <= 0) return CD_OK;
+  slot_map_kernel<<<(nb + 127) / 128, 128, 0, st>>>(slot_of_row, rows, slots, nb);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;

@@ -44,6 +44,38 @@ int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, 
 int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
                   double* Bg, cudaStream_t st);
 
+// ---- device-driven pivot steps of one block (full pivoting) ----------------
+// The state the step kernels read at their start and the last CTA of each
+// step updates: the host uploads it once per block, enqueues up to b step
+// launches (captured once in a CUDA graph) and reads it back once per block,
+// instead of a round trip per step.
+struct DevStep {
+  StepResult res;          // argmax of the current residual diagonal
+  int64_t K;               // vectors so far
+  int64_t Kb;              // vectors at the start of the block (in-block vectors: [Kb, K))
+  int64_t Kcap;            // vector capacity of L
+  const double* Dcur0;     // residual diagonal at the block's first step; steps alternate
+  double* Dnext0;          //   Dcur0 -> Dnext0 -> Dcur0 ...
+  double tau;
+  int32_t done;            // set once a step declines to run; later steps do nothing
+  int32_t reason;          // kStep* below
+};
+constexpr int kStepConverged = 1;   // max D < tau (or no candidate)
+constexpr int kStepOutside = 2;     // argmax row has no column in the block: start a new block
+constexpr int kStepCapacity = 3;    // K reached Kcap
+constexpr int kStepNotPsd = 4;      // pivot diagonal <= 0 or a residual below the tolerance
+
+// slot_of_row [n]: pool slot of each row in the block, -1 elsewhere.  Step k
+// of the block: p = res.idx; L^K from pool column slot_of_row[p] (vectors
+// [Kb, K) applied), D' = D - (L^K)^2, argmax of D'; piv[K] = p, pivd[K] = D_p,
+// slot_of_row[p] = -1, K += 1.
+int launch_finalize_dev(DevStep* ds, int32_t* slot_of_row, const double* pool, const double* L, int64_t ld,
+                        int64_t n, double neg_tol, const uint8_t* cand, int64_t* piv, double* pivd,
+                        StepScratch* sc, cudaStream_t st);
+// slot_of_row[rows[j]] = slots[j] for j < nb (after clearing all n entries to -1)
+int launch_slot_map(int32_t* slot_of_row, int64_t n, const int64_t* rows, const int32_t* slots, int nb,
+                    cudaStream_t st);
+
 // row compaction (first step of the two-step scheme): keep rows idx[0..m) (increasing)
 int launch_compact_f64(const double* src, int64_t lds, const int32_t* idx, int64_t m, int64_t ncol, double* dst,
                        int64_t ldd, cudaStream_t st);
