@@ -257,6 +257,7 @@ def run_ours(args, rank, world):
             tot_ms += ev0.elapsed_time(ev1)
             stats.append(f.stats())
             mem_lib = f.memory()
+            eri_work = f.eri_work()
             M = f.M
             resid = f.max_resid
             if i < args.steps - 1:
@@ -379,15 +380,21 @@ def run_ours(args, rank, world):
                                    "and clocks; microbenchmark measured 1.128 TFLOP/s at 1935 MHz)",
                     "share_of_step": st["ms_colupd"] / ms if ms else None}
     eri_ops = st.get("eri_fp64_ops", 0.0)
-    eri_ach = eri_ops / (st["ms_eri"] * 1e-3) / 1e12 if st["ms_eri"] > 0 and eri_ops > 0 else None
+    alg_ops = eri_work["algorithmic_ops"]
+    eri_ach = alg_ops / (st["ms_eri"] * 1e-3) / 1e12 if st["ms_eri"] > 0 and alg_ops > 0 else None
+    exec_ach = eri_ops / (st["ms_eri"] * 1e-3) / 1e12 if st["ms_eri"] > 0 and eri_ops > 0 else None
     roof_eri = {"kernel": "eri_columns_kernel (FP64 ERI columns, Eq. subtr first term)", "bound": "alu",
-                "achieved": eri_ach, "peak": peak_fp64_ops, "unit": "T FP64-pipe ops/s",
+                "achieved": eri_ach, "peak": peak_fp64_ops, "unit": "T FP64 ops/s",
                 "frac": (eri_ach / peak_fp64_ops) if eri_ach else None, "traffic": None,
                 "peak_source": "FP64 pipe: 148 SMs x 2 operations/clk x 2.032 GHz (recipe unit counts and clocks; "
                                "microbenchmark 1.128 TFLOP/s = 2 DFMA/clk/SM at 1935 MHz)",
-                "work_per_launch": "FP64-pipe operations counted by the kernel per primitive quartet from its "
-                                   "recurrences (set-up, Boys branch taken, bra/ket recurrences)",
-                "fp64_ops_total": eri_ops, "share_of_step": st["ms_eri"] / ms if ms else None}
+                "work_per_launch": "algorithmic FP64 operations: primitive quartets per class x a plain "
+                                   "Obara-Saika/Head-Gordon-Pople count per quartet (cd_factor_eri_work; "
+                                   "the per-class formula is in csrc/eri.cu)",
+                "algorithmic_ops_total": alg_ops, "primitive_quartets": eri_work["quartets"],
+                "executed_fp64_pipe_ops_total": eri_ops,
+                "executed_frac": (exec_ach / peak_fp64_ops) if exec_ach else None,
+                "share_of_step": st["ms_eri"] / ms if ms else None}
     if st["ms_eri"] >= st["ms_colupd"]:
         roof, roof_other, other_key = roof_eri, roof_upd, "roofline_update"
     else:

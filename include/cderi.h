@@ -214,6 +214,13 @@ int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, d
  * operation counts of their recurrences); [13] first-step ms, [14] first-step
  * macro iterations, [15] first-step ERI columns of CD_ALG_TWOSTEP (0 otherwise). */
 int cd_factor_stats(const cd_factor_t* f, double* stats16);
+/* Work of the ERI column kernels (measurement; no counterpart in the paper):
+ * primitive quartets evaluated, and their algorithmic FP64 operation count --
+ * a plain Obara-Saika / Head-Gordon-Pople evaluation per quartet and class,
+ * every add, multiply, fused multiply-add, reciprocal, square root and
+ * exponential counted once, nothing shared between ket components -- the
+ * numerator of the ERI kernel's roofline.  Either output may be NULL. */
+int cd_factor_eri_work(const cd_factor_t* f, double* quartets, double* algorithmic_ops);
 /* Device memory of the decomposition (measurement; the paper reports the
  * memory of its runs, e.g. the CV storage of Sec. 4.1): *peak_bytes = the
  * scratch pool's high-water mark during the call (residual diagonals, column

@@ -30,7 +30,7 @@ _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENO
 # every symbol declared in include/cderi.h
 EXPORTS = ["cd_system_create", "cd_system_free", "cd_system_info", "cd_system_rows", "cd_eri_columns",
            "cd_eri_factor", "cd_eri_factor_sys", "cd_factor_free", "cd_factor_info", "cd_factor_pivots",
-           "cd_factor_vectors", "cd_factor_pivot_diag", "cd_factor_memory", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_set_wait_limit", "cd_last_error", "cd_version"]
+           "cd_factor_vectors", "cd_factor_pivot_diag", "cd_factor_memory", "cd_factor_eri_work", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_set_wait_limit", "cd_last_error", "cd_version"]
 
 
 class CDError(RuntimeError):
@@ -79,6 +79,7 @@ def load(path: Optional[str] = None):
         "cd_factor_vectors": (ctypes.c_int, [P, P, P, P, P]),
         "cd_factor_pivot_diag": (ctypes.c_int, [P, P]),
         "cd_factor_memory": (ctypes.c_int, [P, P, P]),
+        "cd_factor_eri_work": (ctypes.c_int, [P, P, P]),
         "cd_set_wait_limit": (ctypes.c_int, [D, P]),
         "cd_factor_stats": (ctypes.c_int, [P, P]),
         "cd_factor_gather": (ctypes.c_int, [P, P, I32, P]),
@@ -213,6 +214,12 @@ class Factor:
         out = np.zeros(self.M)
         _check(load().cd_factor_pivot_diag(self._h, _p(out)))
         return out
+
+    def eri_work(self) -> dict:
+        """Primitive quartets of the ERI column kernels and their algorithmic FP64 operations."""
+        q, a = ctypes.c_double(), ctypes.c_double()
+        _check(load().cd_factor_eri_work(self._h, ctypes.byref(q), ctypes.byref(a)))
+        return {"quartets": q.value, "algorithmic_ops": a.value}
 
     def memory(self) -> dict:
         """Device bytes at the decomposition's peak and kept by the factor."""

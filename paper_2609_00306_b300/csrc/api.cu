@@ -178,6 +178,10 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
     if (r >= 0) r = p2r[r];
   s->bra_to_all = kall;
   s->bra_row_h = hbra.row;
+  s->bra_npp_h.resize(hbra.pp_off.empty() ? 0 : hbra.pp_off.size() - 1);
+  for (size_t k = 0; k + 1 < hbra.pp_off.size(); ++k) s->bra_npp_h[k] = hbra.pp_off[k + 1] - hbra.pp_off[k];
+  s->all_npp_h.resize(hall.pp_off.empty() ? 0 : hall.pp_off.size() - 1);
+  for (size_t k = 0; k + 1 < hall.pp_off.size(); ++k) s->all_npp_h[k] = hall.pp_off[k + 1] - hall.pp_off[k];
   rc = upload_pairs(hbra, &s->bra, st);
   if (rc != CD_OK) { system_release(s); return rc; }
   // per-row data: diagonal, (mu, nu), ket descriptor pieces
@@ -529,6 +533,20 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   std::vector<int64_t> slot_row(b, -1), slot_valid(b, 0);
   std::unordered_map<int64_t, int> row2slot;
   int64_t K = 0;
+  // surviving bra primitive pairs per class (for the algorithmic ERI count);
+  // recomputed from the live list after each compaction
+  double bra_npp_cls[3] = {0.0, 0.0, 0.0};
+  auto count_bra = [&](const std::vector<int64_t>* order_h) {
+    for (int c = 0; c < 3; ++c) {
+      bra_npp_cls[c] = 0.0;
+      if (order_h) {
+        for (int64_t i = cls_v[c]; i < cls_v[c + 1]; ++i) bra_npp_cls[c] += s->bra_npp_h[(*order_h)[i]];
+      } else {
+        for (int64_t k = s->bra_class_off[c]; k < s->bra_class_off[c + 1]; ++k) bra_npp_cls[c] += s->bra_npp_h[k];
+      }
+    }
+  };
+  count_bra(nullptr);
   // compacts when forced, or when fewer than 3/4 of the working rows are live
   auto compact_rows = [&](bool force) -> int {
     std::vector<double> dh(n);
@@ -620,6 +638,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     bra_v.row = w.rowmap_dev;
     order_v = w.order_dev;
     for (int c = 0; c < 4; ++c) cls_v[c] = co[c];
+    count_bra(&order);
     n = m;
     ld = ldm;
     f->n = n;
@@ -745,6 +764,15 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       CD_TRY(launch_eri_columns(bra_v, order_v, cls_v, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
                                 s->boys, st, w.eri_ops, getenv("CDERI_ERI_SERIAL") ? nullptr : &w.eri));
       eri_ints += (double)kets.size() * (double)n;
+      // algorithmic work of the launch: per bra class, its primitive pairs x each group's ket primitive pairs
+      for (const KetGroup& g : groups) {
+        const double npk = (double)s->all_npp_h[g.sp];
+        for (int c = 0; c < 3; ++c) {
+          const double q = bra_npp_cls[c] * npk;
+          f->eri_quartets += q;
+          f->eri_alg_ops += q * eri_alg_ops_per_quartet(c, g.lc + g.ld, g.nc);
+        }
+      }
     }
     CD_CUDA(cudaEventRecord(w.ev[1], st));
     if (slice) {
@@ -1190,6 +1218,13 @@ int cd_factor_pivots(const cd_factor_t* f, int64_t* piv_rows, int64_t* piv_packe
     if (gaps) gaps[k] = f->gaps[k];
   }
   if (resid_diag && f->n > 0) std::memcpy(resid_diag, f->resid.data(), sizeof(double) * f->n);
+  return CD_OK;
+}
+
+int cd_factor_eri_work(const cd_factor_t* f, double* quartets, double* algorithmic_ops) {
+  if (!f) { set_error("cd_factor_eri_work: factor is NULL"); return CD_EINVAL; }
+  if (quartets) *quartets = f->eri_quartets;
+  if (algorithmic_ops) *algorithmic_ops = f->eri_alg_ops;
   return CD_OK;
 }
 

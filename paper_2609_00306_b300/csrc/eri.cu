@@ -459,6 +459,47 @@ int launch_eri_diag(const PairSet& ps, const int64_t* /*order*/, const int64_t* 
 }  // namespace cd
 
 namespace cd {
+// Algorithmic operation count of one primitive quartet (every add, multiply,
+// fused multiply-add, reciprocal, square root and exponential is one
+// operation), from the recurrences as written in the Obara-Saika /
+// Head-Gordon-Pople scheme, with nothing shared between ket components:
+//   set-up       PQ (3), |PQ|^2 (3), zeta+eta, 1/(zeta+eta), rho, T, prefactor (2): 12
+//   Boys         F_L(T) from a tabulated Taylor series (8), exp(-T) (1), the
+//                downward recursion (2 per order): 9 + 2L; scaled [0]^(m): L + 1
+//   bra VRR      [e+1_i]^(m) = PA_i [e]^(m) + WP_i [e]^(m+1) (2) + N_i(e)/(2 zeta)
+//                ([e-1_i]^(m) - rho/zeta [e-1_i]^(m+1)) (2 when N_i(e) > 0):
+//                [p]^(m), m < L: 6L; [d]^(m), m < L-1: (3 x 4 + 3 x 2)(L-1)
+//   ket VRR, per component, for every bra function e (NE of them: 1, 3 or 9):
+//                [e|f+1_k]^(m) = QC_k [e|f]^(m) + WQ_k [e|f]^(m+1) (2)
+//                + f-term (2 when f_k > 0) + N_k(e)/(2(zeta+eta)) [e-1_k|f]^(m+1)
+//                (1 when N_k(e) > 0); level 1 for m < FK, level 2 for m = 0
+//   contraction  one add per [e|f] result kept (NE per ket level needed)
+// The horizontal recurrences run once per contracted integral (not per
+// quartet) and are not counted.
+double eri_alg_ops_per_quartet(int EB, int FK, int nc) {
+  const int L = EB + FK;
+  double ops = 12.0 + (9.0 + 2.0 * L) + (L + 1.0);
+  if (EB >= 1) ops += 6.0 * L;
+  if (EB == 2) ops += 18.0 * (L - 1);
+  // bra functions e (s | p | s, p, d) and how many of them carry a given
+  // Cartesian direction k (N_k(e) > 0): p: 1 of 3; d: 3 of 6 (e.g. x: xx, xy, xz)
+  const int NE = EB == 0 ? 1 : (EB == 1 ? 3 : 9);
+  const int withk = EB == 0 ? 0 : (EB == 1 ? 1 : 1 + 3);
+  if (FK == 0) return ops + NE;
+  double per = 0.0;
+  // level 1 ([e|1_k]^(m), m < FK): 2 per value, + 1 where N_k(e) > 0
+  per += FK * (2.0 * NE + withk);
+  if (FK == 2) {
+    // level 2 ([e|1_k + 1_l]^(0)): 2, + 2 for the f-term when k = l (1 of 3
+    // components on average: counted as 2/3), + 1 where N_l(e) > 0
+    per += 2.0 * NE + (2.0 / 3.0) * 2.0 * NE + withk;
+    per += 2.0 * NE;   // contraction of the two ket levels the HRR needs
+  } else {
+    per += NE;         // contraction
+  }
+  return ops + nc * per;
+}
+
 std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets) {
   std::vector<KetDesc> k(kets);
   // same shell pair together, and within it the same kc (the level-1 recurrence is then shared)

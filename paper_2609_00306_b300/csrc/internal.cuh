@@ -138,6 +138,13 @@ struct KetGroup {
 // group ket descriptors of the same shell pair
 std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets);
 
+// Algorithmic FP64 operation count of one primitive quartet of a column
+// block: bra shell pair of class EB = la + lb (all its components) against nc
+// ket components of a ket shell pair of class FK = lc + ld, by a plain
+// Obara-Saika / Head-Gordon-Pople evaluation (see eri.cu).  Independent of how
+// the kernel shares work between components.
+double eri_alg_ops_per_quartet(int EB, int FK, int nc);
+
 // ERI kernels (eri.cu)
 // out[slot * ld + row] = (bra rows | ket component) for every bra shell pair in `bra`
 // bra_order: NULL (every bra shell pair; class c is [class_off[c], class_off[c+1]))
@@ -173,6 +180,8 @@ struct cd_system {
   int64_t bra_class_off[4] = {0, 0, 0, 0};
   std::vector<int32_t> bra_to_all;          // bra shell pair -> index in `all`
   std::vector<int32_t> bra_row_h;           // host copy of bra.row ([n][9] row of each component, -1 = none)
+  std::vector<int32_t> bra_npp_h;           // surviving primitive pairs of each bra shell pair
+  std::vector<int32_t> all_npp_h;           // primitive pairs of each shell pair of `all`
   std::vector<int64_t> all_class_off_h;     // class offsets of `all` (sorted by class)
   int64_t all_class_off[4] = {0, 0, 0, 0};
   int64_t n_rows = 0, n_rows_pad = 0;
@@ -201,6 +210,8 @@ struct cd_factor {
   std::vector<double> resid;
   double resid_max = 0.0;
   double stats[16] = {0};
+  double eri_quartets = 0.0;   // primitive quartets of the ERI column kernels
+  double eri_alg_ops = 0.0;    // their algorithmic FP64 operation count (eri_alg_ops_per_quartet)
   double mem_peak = 0.0;       // device bytes at the decomposition's peak (pool high-water mark + vector arrays)
   double mem_resident = 0.0;   // device bytes the factor keeps after the call
 };
