@@ -44,7 +44,9 @@ extern "C" {
 
 /* ---- precision / mode flags --------------------------------------------- */
 #define CD_FP64          0  /* vectors stored FP64; J/K in FP64 */
-#define CD_VEC_FP32      1  /* after the (FP64) factorisation, vectors rounded once to FP32 */
+#define CD_VEC_FP32      1  /* after the (FP64) factorisation, vectors rounded once to FP32 and kept
+                               * only in FP32 (the FP64 array is released: half the memory); every
+                               * consumer reads the FP32 values, accumulating in FP64 */
 
 #define CD_JK_FP64       0  /* J and K contractions in FP64 */
 #define CD_JK_BF16X3     1  /* FP32 vectors; BF16 tensor-core products of 3 exact 8-bit slices per operand row */

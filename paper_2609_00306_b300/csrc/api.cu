@@ -22,8 +22,8 @@ static std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_counter() { return g_launches.load(); }
 int launch_to_fp32(const double* src, int64_t ld, int64_t M, int64_t n, float* dst, cudaStream_t st);
-int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N, int n_mo,
-                      const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
+int mo_vectors_sliced(const float* L32, const double* L64, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N,
+                      int n_mo, const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
                       cudaStream_t st);
 int jk_mixed(const float* L32, const double* L64, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,
              const int32_t* mu, const int32_t* nu, double* J_dev, double* K_dev, bool wantJ, bool wantK,
@@ -1057,11 +1057,15 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     f->mem_peak = (double)(high > pool_used0 ? high - pool_used0 : 0) + 8.0 * (double)f->Mcap * (double)ld;
   }
   if (f->vec_precision == CD_VEC_FP32 && K > 0) {
+    // the stored vectors become FP32: the FP64 array is released once the copy is made
     CD_TRY(dalloc(&f->L32, (size_t)K * ld));
     CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
     f->mem_peak = std::max(f->mem_peak, 8.0 * (double)f->Mcap * ld + 4.0 * (double)K * ld);
+    CD_CUDA(cudaStreamSynchronize(st));
+    cudaFree(f->L);
+    f->L = nullptr;
   }
-  f->mem_resident = 8.0 * (double)f->Mcap * ld + (f->L32 ? 4.0 * (double)K * ld : 0.0);
+  f->mem_resident = (f->L ? 8.0 * (double)f->Mcap * ld : 0.0) + (f->L32 ? 4.0 * (double)K * ld : 0.0);
   CD_CUDA(cudaStreamSynchronize(st));
   const double t_all = now_ms() - t_start;
   f->stats[0] = s->ms_setup;
@@ -1273,7 +1277,8 @@ int cd_factor_gather(const cd_factor_t* f, const int64_t* rows, int32_t nrows, d
   if (rc != CD_OK) { cudaFree(rd); return rc; }
   rc = CD_ECUDA;
   if (cudaMemcpy(rd, rows, sizeof(int64_t) * nrows, cudaMemcpyHostToDevice) == cudaSuccess &&
-      launch_gather(f->L, f->ld, rd, nrows, 0, f->M, od, nullptr) == CD_OK &&
+      (f->L ? launch_gather(f->L, f->ld, rd, nrows, 0, f->M, od, nullptr)
+            : launch_gather(f->L32, f->ld, rd, nrows, 0, f->M, od, nullptr)) == CD_OK &&
       cudaMemcpy(out, od, sizeof(double) * nrows * f->M, cudaMemcpyDeviceToHost) == cudaSuccess)
     rc = CD_OK;
   if (rc != CD_OK) set_error("cd_factor_gather: CUDA failure");
@@ -1345,8 +1350,13 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
       if ((rc = scratch_alloc(&v, (size_t)std::max<int64_t>(M, 1), st)) != CD_OK) return fail(rc);
       if ((rc = scratch_alloc(&Jp, (size_t)std::max<int64_t>(n, 1), st)) != CD_OK) return fail(rc);
       if ((rc = launch_density_packed(dC, N, O, f->sys->row_mu_dev, f->sys->row_nu_dev, n, d, st)) != CD_OK) return fail(rc);
-      if ((rc = launch_gemv_rows<double>(f->L, ld, M, n, d, v, st)) != CD_OK) return fail(rc);
-      if ((rc = launch_gemv_cols<double>(f->L, ld, M, n, v, Jp, st)) != CD_OK) return fail(rc);
+      if (f->L) {
+        if ((rc = launch_gemv_rows<double>(f->L, ld, M, n, d, v, st)) != CD_OK) return fail(rc);
+        if ((rc = launch_gemv_cols<double>(f->L, ld, M, n, v, Jp, st)) != CD_OK) return fail(rc);
+      } else {  // FP32-stored vectors, FP64 accumulation
+        if ((rc = launch_gemv_rows<float>(f->L32, ld, M, n, d, v, st)) != CD_OK) return fail(rc);
+        if ((rc = launch_gemv_cols<float>(f->L32, ld, M, n, v, Jp, st)) != CD_OK) return fail(rc);
+      }
       if ((rc = launch_unpack_sym(Jp, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, dJ, st)) != CD_OK) return fail(rc);
     }
     if (wantK) {
@@ -1357,7 +1367,11 @@ int cd_jk(const cd_factor_t* f, const double* C_occ, int32_t n_occ, double* J, d
       if (cudaMemsetAsync(dK, 0, sizeof(double) * N * N, st) != cudaSuccess) return fail(CD_ECUDA);
       for (int64_t P0 = 0; P0 < M; P0 += Pc) {
         const int pc = (int)std::min<int64_t>(Pc, M - P0);
-        if ((rc = launch_unpack_vectors<double>(f->L, ld, P0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, Lfull, st)) != CD_OK) return fail(rc);
+        rc = f->L ? launch_unpack_vectors<double, double>(f->L, ld, P0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n,
+                                                          N, Lfull, st)
+                  : launch_unpack_vectors<float, double>(f->L32, ld, P0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev,
+                                                         n, N, Lfull, st);
+        if (rc != CD_OK) return fail(rc);
         // B[p] = Lfull[p] (N x N) * C (N x O)
         if ((rc = launch_dgemm(N, O, N, pc, 1.0, Lfull, N, 1, (int64_t)N * N, dC, O, 1, 0, B, O, (int64_t)N * O, false, st)) != CD_OK) return fail(rc);
         // K += 2 sum_p B[p] B[p]^T
@@ -1411,7 +1425,8 @@ int cd_mo_vectors(const cd_factor_t* f, const double* C, int32_t n_mo, int64_t P
     }
   }
   if (slices > 0) {
-    rc = mo_vectors_sliced(f->L, ld, P0, nP, n, N, n_mo, dC, f->sys->row_mu_dev, f->sys->row_nu_dev, slices, dOut, st);
+    rc = mo_vectors_sliced(f->L ? nullptr : f->L32, f->L, ld, P0, nP, n, N, n_mo, dC, f->sys->row_mu_dev,
+                           f->sys->row_nu_dev, slices, dOut, st);
     if (rc != CD_OK) return done(rc);
   } else {
     // FP64: per chunk of vectors, U^P = unpack(L^P), B^P = U^P C, out^P = C^T B^P
@@ -1421,8 +1436,11 @@ int cd_mo_vectors(const cd_factor_t* f, const double* C, int32_t n_mo, int64_t P
     if ((rc = scratch_alloc(&B, (size_t)Pc * N * n_mo, st)) != CD_OK) return done(rc);
     for (int64_t Q0 = P0; Q0 < P0 + nP; Q0 += Pc) {
       const int pc = (int)std::min<int64_t>(Pc, P0 + nP - Q0);
-      if ((rc = launch_unpack_vectors<double>(f->L, ld, Q0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N, U, st)) != CD_OK)
-        return done(rc);
+      rc = f->L ? launch_unpack_vectors<double, double>(f->L, ld, Q0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n, N,
+                                                        U, st)
+                : launch_unpack_vectors<float, double>(f->L32, ld, Q0, pc, f->sys->row_mu_dev, f->sys->row_nu_dev, n,
+                                                       N, U, st);
+      if (rc != CD_OK) return done(rc);
       if ((rc = launch_dgemm(N, n_mo, N, pc, 1.0, U, N, 1, (int64_t)N * N, dC, n_mo, 1, 0, B, n_mo,
                              (int64_t)N * n_mo, false, st)) != CD_OK)
         return done(rc);

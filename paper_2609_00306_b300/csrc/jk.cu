@@ -151,14 +151,14 @@ __global__ void unpack_sym_kernel(const double* __restrict__ packed, const int32
   out[(int64_t)nu[r] * N + mu[r]] = v;
 }
 
-template <class T>
+template <class T, class TO>
 __global__ void unpack_vectors_kernel(const T* __restrict__ L, int64_t ld, int64_t P0, const int32_t* __restrict__ mu,
-                                      const int32_t* __restrict__ nu, int64_t n, int N, T* __restrict__ out) {
+                                      const int32_t* __restrict__ nu, int64_t n, int N, TO* __restrict__ out) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (r >= n) return;
-  const T v = L[(P0 + p) * ld + r];
-  T* o = out + (int64_t)p * N * N;
+  const TO v = (TO)L[(P0 + p) * ld + r];
+  TO* o = out + (int64_t)p * N * N;
   o[(int64_t)mu[r] * N + nu[r]] = v;
   o[(int64_t)nu[r] * N + mu[r]] = v;
 }
@@ -228,13 +228,13 @@ int launch_unpack_sym(const double* packed, const int32_t* mu, const int32_t* nu
   return CD_OK;
 }
 
-template <class T>
+template <class T, class TO>
 int launch_unpack_vectors(const T* L, int64_t ld, int64_t P0, int Pc, const int32_t* mu, const int32_t* nu,
-                          int64_t n, int N, T* out, cudaStream_t st) {
-  CD_CUDA(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)Pc * N * N, st));
+                          int64_t n, int N, TO* out, cudaStream_t st) {
+  CD_CUDA(cudaMemsetAsync(out, 0, sizeof(TO) * (size_t)Pc * N * N, st));
   if (n <= 0 || Pc <= 0) return CD_OK;
   dim3 grid((unsigned)((n + 255) / 256), (unsigned)Pc);
-  unpack_vectors_kernel<T><<<grid, 256, 0, st>>>(L, ld, P0, mu, nu, n, N, out);
+  unpack_vectors_kernel<T, TO><<<grid, 256, 0, st>>>(L, ld, P0, mu, nu, n, N, out);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
@@ -244,9 +244,9 @@ template int launch_gemv_rows<double>(const double*, int64_t, int64_t, int64_t, 
 template int launch_gemv_rows<float>(const float*, int64_t, int64_t, int64_t, const double*, double*, cudaStream_t);
 template int launch_gemv_cols<double>(const double*, int64_t, int64_t, int64_t, const double*, double*, cudaStream_t);
 template int launch_gemv_cols<float>(const float*, int64_t, int64_t, int64_t, const double*, double*, cudaStream_t);
-template int launch_unpack_vectors<double>(const double*, int64_t, int64_t, int, const int32_t*, const int32_t*,
-                                           int64_t, int, double*, cudaStream_t);
-template int launch_unpack_vectors<float>(const float*, int64_t, int64_t, int, const int32_t*, const int32_t*,
-                                          int64_t, int, float*, cudaStream_t);
+template int launch_unpack_vectors<double, double>(const double*, int64_t, int64_t, int, const int32_t*,
+                                                   const int32_t*, int64_t, int, double*, cudaStream_t);
+template int launch_unpack_vectors<float, double>(const float*, int64_t, int64_t, int, const int32_t*,
+                                                  const int32_t*, int64_t, int, double*, cudaStream_t);
 
 }  // namespace cd

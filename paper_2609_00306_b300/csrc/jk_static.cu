@@ -86,8 +86,13 @@ extern "C" int cd_jk_coulomb_static(const cd_factor_t* f, const double* C_occ_de
   // accumulated by several; cleared when there is no vector), and J is cleared
   // inside launch_unpack_sym.
   CD_TRY(launch_density_packed(C_occ_dev, N, n_occ, mu, nu, f->n, d, st));
-  CD_TRY(launch_gemv_rows<double>(f->L, f->ld, f->M, f->n, d, v, st));
-  CD_TRY(launch_gemv_cols<double>(f->L, f->ld, f->M, f->n, v, Jp, st));
+  if (f->L) {
+    CD_TRY(launch_gemv_rows<double>(f->L, f->ld, f->M, f->n, d, v, st));
+    CD_TRY(launch_gemv_cols<double>(f->L, f->ld, f->M, f->n, v, Jp, st));
+  } else {  // FP32-stored vectors (CD_VEC_FP32), FP64 accumulation
+    CD_TRY(launch_gemv_rows<float>(f->L32, f->ld, f->M, f->n, d, v, st));
+    CD_TRY(launch_gemv_cols<float>(f->L32, f->ld, f->M, f->n, v, Jp, st));
+  }
   CD_TRY(launch_unpack_sym(Jp, mu, nu, f->n, N, J_dev, st));
   return CD_OK;
 }

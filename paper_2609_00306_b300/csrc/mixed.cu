@@ -400,9 +400,10 @@ __global__ void mo_out_kernel(const unsigned long long* __restrict__ D, int Pc, 
 // CV -> MO transformation (Sec. 4.1: the vectors transformed to the MO basis
 // for CASSCF / CC), out[P - P0][i][j] = sum_{mu nu} C[mu][i] L^P_{mu nu} C[nu][j],
 // as two exact-slice products per chunk of vectors: B^P = L^P C, then C^T B^P.
-int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N, int n_mo,
-                      const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
-                      cudaStream_t st) {
+template <class TL>
+int mo_vectors_sliced_t(const TL* L, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N, int n_mo,
+                        const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
+                        cudaStream_t st) {
   if (nP <= 0) return CD_OK;
   const int64_t Np = (N + 7) / 8 * 8;
   int Pc = (int)std::max<int64_t>(1, std::min<int64_t>(nP, (int64_t)(1.5e9 / (2.0 * S * N * (double)N))));
@@ -441,7 +442,7 @@ int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64
   pl.F = 61 - ilog2_ceil(N);
   for (int64_t Q0 = P0; Q0 < P0 + nP; Q0 += Pc) {
     const int pc = (int)std::min<int64_t>(Pc, P0 + nP - Q0);
-    CD_TRY(launch_unpack_slice<double>(L, ld, Q0, pc, b.idx, N, Np, S, b.eL, b.Ls, st));
+    CD_TRY(launch_unpack_slice<TL>(L, ld, Q0, pc, b.idx, N, Np, S, b.eL, b.Ls, st));
     // B^P[mu][i]: D1[i][p*N + mu]
     CD_CUDA(cudaMemsetAsync(b.D1, 0, sizeof(unsigned long long) * n_mo * pc * N, st));
     CD_TRY(ozaki_gemm(pl, b.Ls, (int64_t)pc * N, Np, b.Cs, n_mo, Np, N, b.D1, (int64_t)pc * N, 1, b.err, st));
@@ -469,6 +470,13 @@ int mo_vectors_sliced(const double* L, int64_t ld, int64_t P0, int64_t nP, int64
   CD_CUDA(cudaStreamSynchronize(st));
   if (herr) { set_error("MO transform: a bounded tensor-core pipeline wait timed out"); return CD_ETIMEOUT; }
   return CD_OK;
+}
+
+int mo_vectors_sliced(const float* L32, const double* L64, int64_t ld, int64_t P0, int64_t nP, int64_t n, int N,
+                      int n_mo, const double* C_dev, const int32_t* mu, const int32_t* nu, int S, double* out_dev,
+                      cudaStream_t st) {
+  if (L32) return mo_vectors_sliced_t<float>(L32, ld, P0, nP, n, N, n_mo, C_dev, mu, nu, S, out_dev, st);
+  return mo_vectors_sliced_t<double>(L64, ld, P0, nP, n, N, n_mo, C_dev, mu, nu, S, out_dev, st);
 }
 
 int jk_mixed(const float* L32, const double* L64, int64_t ld, int64_t M, int64_t n, int N, int O, const double* C_dev,

@@ -246,7 +246,8 @@ __global__ void slot_map_kernel(int32_t* __restrict__ slot_of_row, const int64_t
 }
 
 // Bg[k][j] = L[k][rows[j]] for k in [k0, k1), j < nb (row-major, leading dim nb)
-__global__ void gather_kernel(const double* __restrict__ L, int64_t ld, const int64_t* __restrict__ rows, int nb,
+template <class T>
+__global__ void gather_kernel(const T* __restrict__ L, int64_t ld, const int64_t* __restrict__ rows, int nb,
                               int64_t k0, int64_t k1, double* __restrict__ Bg) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nk = k1 - k0;
@@ -369,14 +370,23 @@ int launch_slot_map(int32_t* slot_of_row, int64_t n, const int64_t* rows, const 
   return CD_OK;
 }
 
-int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
-                  double* Bg, cudaStream_t st) {
+template <class T>
+static int launch_gather_t(const T* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                           double* Bg, cudaStream_t st) {
   int64_t tot = (k1 - k0) * nb;
   if (tot <= 0) return CD_OK;
-  gather_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, ld, rows_dev, nb, k0, k1, Bg);
+  gather_kernel<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(L, ld, rows_dev, nb, k0, k1, Bg);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
+}
+int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                  double* Bg, cudaStream_t st) {
+  return launch_gather_t(L, ld, rows_dev, nb, k0, k1, Bg, st);
+}
+int launch_gather(const float* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                  double* Bg, cudaStream_t st) {
+  return launch_gather_t(L, ld, rows_dev, nb, k0, k1, Bg, st);
 }
 
 }  // namespace cd

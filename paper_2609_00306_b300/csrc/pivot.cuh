@@ -43,6 +43,8 @@ int launch_finalize(const double* col, const double* L, int64_t ld, int64_t Kb, 
                     StepScratch* sc, StepResult* res, cudaStream_t st, const uint8_t* cand = nullptr);
 int launch_gather(const double* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
                   double* Bg, cudaStream_t st);
+int launch_gather(const float* L, int64_t ld, const int64_t* rows_dev, int nb, int64_t k0, int64_t k1,
+                  double* Bg, cudaStream_t st);
 
 // ---- device-driven pivot steps of one block (full pivoting) ----------------
 // The state the step kernels read at their start and the last CTA of each
@@ -98,9 +100,10 @@ template <class T>
 int launch_gemv_cols(const T* L, int64_t ld, int64_t M, int64_t n, const double* v, double* y, cudaStream_t st);
 int launch_unpack_sym(const double* packed, const int32_t* mu, const int32_t* nu, int64_t n, int N, double* out,
                       cudaStream_t st);
-template <class T>
+// dense symmetric N x N unpacking of vectors P0 .. P0+Pc-1 (T: stored type, TO: output type)
+template <class T, class TO>
 int launch_unpack_vectors(const T* L, int64_t ld, int64_t P0, int Pc, const int32_t* mu, const int32_t* nu,
-                          int64_t n, int N, T* out, cudaStream_t st);
+                          int64_t n, int N, TO* out, cudaStream_t st);
 // generic FP64 GEMM: C[b] (+)= alpha * A[b] B[b]; element (i,k) of A at A + i*ars + k*acs + b*abs
 int launch_dgemm(int m, int n, int k, int batch, double alpha,
                  const double* A, int64_t ars, int64_t acs, int64_t abs_,

@@ -67,7 +67,7 @@ def test_sp400_full_parity():
 def sp2000():
     import paper_2609_00306_b300 as cd
     s = synth.make_workload("sp2000")
-    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=cd.CD_VEC_FP32)
+    f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
     sysm = cd.System(s.basis, s.schwarz)
     packed, diag = sysm.rows()
     prow, ppk, gaps, resid = f.pivots()
@@ -125,9 +125,11 @@ def test_sp2000_mixed_jk_error_report(sp2000):
     s, f, packed, diag, prow, resid = sp2000
     J64, K64 = f.jk(s.C_occ, cd.CD_JK_FP64)
     Dm = oracle.density(s.C_occ)
+    from paper_2609_00306_b300.cderi import CD_JK_VEC_FP32
     for mode, tol in ((cd.CD_JK_BF16X3, 3e-6), (cd.CD_JK_BF16X4, 3e-7), (cd.CD_JK_BF16X5, 3e-7)):
-        # the factor keeps FP32 vectors (vec_precision=CD_VEC_FP32): FP32 storage limits K to ~1e-7
-        Jm, Km = f.jk(s.C_occ, mode)
+        # vectors rounded to FP32 before the contraction (the FP32 storage pattern): FP32
+        # storage alone limits K to ~1e-7
+        Jm, Km = f.jk(s.C_occ, mode | CD_JK_VEC_FP32)
         eJ = np.max(np.abs(Jm - J64)) / np.max(np.abs(J64))
         eK = np.max(np.abs(Km - K64)) / np.max(np.abs(K64))
         tJ = abs(np.sum(Dm * (Jm - J64))) / abs(np.sum(Dm * J64))
@@ -173,3 +175,35 @@ def test_sp1200_precision_report():
         cm, cn = oracle.unpack_pair(packed[prow[K]])
         ref = np.array([o.eri(a, b, int(cm), int(cn)) for a, b in zip(pm, pn)])
         assert np.max(np.abs(Lp.T @ Lc[:, j] - ref)) < 1e-12 * max(1.0, float(np.sqrt(diag[prow[K]] * np.max(diag))))
+
+
+def test_fp32_storage_releases_the_fp64_vectors():
+    """CD_VEC_FP32: after the (FP64) decomposition the vectors are kept in FP32
+    only -- half the memory -- and every consumer reads them: gathered entries,
+    FP64 J/K and the mixed J/K agree with the FP64-stored factor to the FP32
+    rounding of the vectors (2^-24 relative per entry)."""
+    import paper_2609_00306_b300 as cd
+    from paper_2609_00306_b300.cderi import CD_JK_VEC_FP32
+    s = synth.make_workload("sp400")
+    f64 = cd.cd_eri_factor(s.basis, s.tau, s.schwarz)
+    f32 = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=cd.CD_VEC_FP32)
+    assert f32.M == f64.M and np.array_equal(f32.pivots()[0], f64.pivots()[0])
+    ld = (f64.n_rows + 31) // 32 * 32
+    assert f32.memory()["resident_bytes"] == 4.0 * f32.M * ld
+    assert f64.memory()["resident_bytes"] >= 8.0 * f64.M * ld
+    rows = np.random.default_rng(4).integers(0, f64.n_rows, 50)
+    g64, g32 = f64.gather(rows), f32.gather(rows)
+    assert np.max(np.abs(g32 - g64)) <= 2.0 ** -24 * np.max(np.abs(g64))
+    assert np.array_equal(g32, g32.astype(np.float32).astype(np.float64))
+    J64, K64 = f64.jk(s.C_occ, cd.CD_JK_FP64)
+    J32, K32 = f32.jk(s.C_occ, cd.CD_JK_FP64)
+    assert np.max(np.abs(J32 - J64)) <= 1e-6 * np.max(np.abs(J64))
+    assert np.max(np.abs(K32 - K64)) <= 1e-6 * np.max(np.abs(K64))
+    # the mixed contraction of the FP32-stored vectors equals the one that rounds FP64 vectors on the fly
+    Jm32, Km32 = f32.jk(s.C_occ, cd.CD_JK_BF16X4)
+    Jm64, Km64 = f64.jk(s.C_occ, cd.CD_JK_BF16X4 | CD_JK_VEC_FP32)
+    assert np.max(np.abs(Km32 - Km64)) <= 1e-12 * np.max(np.abs(Km64))
+    assert np.max(np.abs(Jm32 - Jm64)) <= 1e-12 * np.max(np.abs(Jm64))
+    mo64 = f64.mo_vectors(s.C_occ[:, :8], P0=0, nP=16, slices=0)
+    mo32 = f32.mo_vectors(s.C_occ[:, :8], P0=0, nP=16, slices=0)
+    assert np.max(np.abs(mo32 - mo64)) <= 1e-6 * np.max(np.abs(mo64))
