@@ -50,7 +50,7 @@ def sample_indices(name: str, n_rows: int, N: int):
     return lrows, jkrows, X
 
 
-def run(name: str, threads: int | None) -> str:
+def run(name: str, threads: int | None, mcap: int | None = None) -> str:
     import oracle
     import synth
     if threads:
@@ -64,7 +64,9 @@ def run(name: str, threads: int | None) -> str:
     n = rows.shape[0]
     print(f"[{name}] N={N} rows={n} tau={s.tau} screening {t_screen:.1f}s", flush=True)
     t0 = time.perf_counter()
-    mcap = min(n, 8 * N)
+    # vector capacity: large enough for the run (M/N is 5-7 for these systems);
+    # the work array is zero-filled lazily, so only the vectors made use memory
+    mcap = min(n, mcap or 8 * N)
     r = o.cd(rows, s.tau, mcap=mcap, copy=False)
     t_cd = time.perf_counter() - t0
     print(f"[{name}] M={r.M} max D={r.D.max():.6e} decomposition {t_cd:.1f}s", flush=True)
@@ -155,6 +157,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("names", nargs="+")
     ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--mcap", type=int, default=None, help="vector capacity (default 8 N)")
     ap.add_argument("--twostep", action="store_true",
                     help="the two-step scheme (span 0.01, qualified set of 64) instead of full pivoting")
     a = ap.parse_args()
@@ -162,7 +165,7 @@ def main():
         if a.twostep:
             run_twostep(name, 0.01, 64, a.threads)
         else:
-            run(name, a.threads)
+            run(name, a.threads, a.mcap)
 
 
 if __name__ == "__main__":
