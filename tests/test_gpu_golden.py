@@ -96,6 +96,16 @@ def test_free_run_matches_oracle(name):
         assert abs(pd[k] - g["pivD"][k]) < 1e-12, (k, pd[k], g["pivD"][k])
         if k > 0:
             assert np.max(np.abs(pd[:k] - g["pivD"][:k])) < 1e-12
+        # after the near-tie the two factorisations differ, but each reproduces
+        # the exact J/K within its truncation bound (Sec. 2: every residual
+        # element is below max D < tau), so they agree within twice that bound
+        J, K = f.jk(s.C_occ, cd.CD_JK_FP64)
+        Dm = oracle.density(s.C_occ)
+        bound = 2.0 * s.tau * np.sum(np.abs(Dm))
+        assert np.max(np.abs(J[g["jkrows"]] - g["J_rows"])) <= bound
+        assert np.max(np.abs(K[g["jkrows"]] - g["K_rows"])) <= bound
+        errs = _jk_errors(g, J, K, Dm)
+        print(f"{name} FP64 J/K (free run, after the near-tie) vs oracle: {errs}; tau bound {bound / g['maxJ']:.2e} of max|J|")
         return
     assert np.max(np.abs(pd - g["pivD"])) < 1e-12
     Lg = f.gather(g["lrows"])
