@@ -29,9 +29,17 @@ template <class T> struct Vec;
 template <> struct Vec<double> { using V = double2; static constexpr int W = 2; };
 template <> struct Vec<float> { using V = float4; static constexpr int W = 4; };
 
-__device__ __forceinline__ double dot_w(double2 l, const double* dd) { return fma(l.x, dd[0], l.y * dd[1]); }
-__device__ __forceinline__ double dot_w(float4 l, const double* dd) {
-  return fma((double)l.x, dd[0], fma((double)l.y, dd[1], fma((double)l.z, dd[2], (double)l.w * dd[3])));
+// acc += l . dd with one FP64 FMA per element (the FP64 pipe, not HBM, bounds J
+// on this GPU: 2 FP64 operations/clk/SM), split over two accumulators
+__device__ __forceinline__ void dot_w(double2 l, const double* dd, double& a0, double& a1) {
+  a0 = fma(l.x, dd[0], a0);
+  a1 = fma(l.y, dd[1], a1);
+}
+__device__ __forceinline__ void dot_w(float4 l, const double* dd, double& a0, double& a1) {
+  a0 = fma((double)l.x, dd[0], a0);
+  a1 = fma((double)l.y, dd[1], a1);
+  a0 = fma((double)l.z, dd[2], a0);
+  a1 = fma((double)l.w, dd[3], a1);
 }
 __device__ __forceinline__ void axpy_w(double2 l, double vp, double* a) { a[0] = fma(l.x, vp, a[0]); a[1] = fma(l.y, vp, a[1]); }
 __device__ __forceinline__ void axpy_w(float4 l, double vp, double* a) {
@@ -53,9 +61,9 @@ __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict_
   constexpr int W = Vec<T>::W;
   const int64_t P0 = (int64_t)blockIdx.x * kJVB;
   const int nv = (int)min((int64_t)kJVB, M - P0);
-  double acc[kJVB];
+  double acc[kJVB], acc2[kJVB];
 #pragma unroll
-  for (int j = 0; j < kJVB; ++j) acc[j] = 0.0;
+  for (int j = 0; j < kJVB; ++j) acc[j] = acc2[j] = 0.0;
   const int64_t nw = n / W;
   const int64_t w0 = (int64_t)blockIdx.y * wchunk;
   const int64_t w1 = min(nw, w0 + wchunk);
@@ -75,8 +83,10 @@ __global__ void __launch_bounds__(kJThreads) j_pass1_kernel(const T* __restrict_
     }
 #pragma unroll
     for (int j = 0; j < kJVB; ++j)
-      if (j < nv) acc[j] += dot_w(__ldg(rowv[j] + i), dd);
+      if (j < nv) dot_w(__ldg(rowv[j] + i), dd, acc[j], acc2[j]);
   }
+#pragma unroll
+  for (int j = 0; j < kJVB; ++j) acc[j] += acc2[j];
   if (blockIdx.y == gridDim.y - 1)   // the rows past the last whole group of W
     for (int64_t r = nw * W + threadIdx.x; r < n; r += kJThreads)
 #pragma unroll

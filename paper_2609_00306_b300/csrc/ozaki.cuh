@@ -25,13 +25,15 @@ namespace cd {
 // FP64 pipe of this GPU is the scarce unit.)
 template <int S>
 __device__ __forceinline__ void fixed_digits(long long v, float (&a)[S]) {
+  // every digit fits a 32-bit int; converting from int32 keeps the
+  // conversion off the FP64 pipe (a 64-bit integer conversion runs there)
 #pragma unroll
   for (int s = S - 1; s >= 1; --s) {
     const long long d = ((v + 128) & 255) - 128;
-    a[s] = (float)d;
+    a[s] = (float)(int)d;
     v = (v - d) >> 8;
   }
-  a[0] = (float)v;
+  a[0] = (float)(int)v;
 }
 // round(x * 2^k) for a finite double x with |x * 2^k| < 2^62, by integer
 // operations on the bit pattern (ties away from zero).  A direct double ->
