@@ -241,7 +241,8 @@ static KetDesc ket_of_row(const cd_system* s, int64_t r, int32_t slot) {
 // ---------------------------------------------------------------- factor ----
 static void factor_release(cd_factor* f) {
   if (!f) return;
-  cudaFree(f->L);
+  f->Lvm.release();
+  f->L = nullptr;
   cudaFree(f->L32);
   if (f->owns_sys) system_release(f->sys);
   delete f;
@@ -272,7 +273,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   StepResult* res_h = res_hv;
   double* dp_h = dp_hv;
   // sliced update
-  void* Ls = nullptr;               // bf16 [kSlices][n][kcap]
+  VmArray Lsvm;                     // slice store, grows in place
+  void* Ls = nullptr;               // bf16 [kcap/32][kSlices][n][32] (the base of Lsvm)
   void* Bs = nullptr;               // bf16 [kSlices][b][kcap]
   unsigned long long* Dint = nullptr;  // int64 [b][ld]
   int32_t* erow = nullptr;          // [n]
@@ -318,7 +320,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   std::vector<int64_t> upd_rows, upd_valid;
   ~Work() {
     for (void* p : {(void*)pool, (void*)D0, (void*)D1, (void*)Bg, (void*)slots_dev, (void*)rows_dev,
-                    (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Ls, Bs, (void*)Dint,
+                    (void*)valid_dev, (void*)kets_dev, (void*)sc, (void*)res_dev, Bs, (void*)Dint,
                     (void*)erow, (void*)err, (void*)sel, (void*)cand_rows, (void*)cand_vals, (void*)eri_ops,
                     (void*)slot_rows_dev, (void*)slot_vals_dev, (void*)rowmap_dev, (void*)order_dev,
                     (void*)cand_dev})
@@ -338,32 +340,32 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
 };
 }  // namespace
 
-// Grow the vector store to `newcap` vectors (and the slice store with it).
+// Bytes of one k-chunk (32 vectors) of the slice store over n rows.
+static size_t slice_chunk_bytes(int64_t n) { return (size_t)kSlices * (size_t)std::max<int64_t>(n, 1) * 32 * 2; }
+
+// Grow the vector store to `newcap` vectors, and the slice store with it: more
+// memory is mapped behind the same addresses, nothing is copied.
 static int grow_vectors(cd_factor* f, Work* w, bool slice, int b, int64_t newcap, int64_t K, cudaStream_t st) {
-  double* nL = nullptr;
-  CD_TRY(dalloc(&nL, (size_t)newcap * f->ld));
-  if (K > 0) CD_CUDA(cudaMemcpyAsync(nL, f->L, sizeof(double) * K * f->ld, cudaMemcpyDeviceToDevice, st));
+  (void)K;
+  CD_TRY(f->Lvm.grow(sizeof(double) * (size_t)newcap * f->ld));
   if (slice) {
     const int64_t nk = (newcap + 31) / 32 * 32;
-    void* nLs = nullptr;
-    void* nBs = nullptr;
-    int rc = scratch_alloc((uint16_t**)&nLs, (size_t)kSlices * f->n * nk, st);
-    if (rc == CD_OK) rc = scratch_alloc((uint16_t**)&nBs, (size_t)kSlices * b * nk, st);
-    if (rc != CD_OK) { cudaFree(nL); scratch_free(nLs, st); return rc; }
-    if (K > 0 && f->n > 0)
-      CD_CUDA(cudaMemcpy2DAsync(nLs, nk * 2, w->Ls, w->kcap * 2, K * 2, (size_t)kSlices * f->n,
-                                cudaMemcpyDeviceToDevice, st));
-    scratch_free(w->Ls, st);
+    CD_TRY(w->Lsvm.grow(slice_chunk_bytes(f->n) * (size_t)(nk / 32)));
+    void* nBs = nullptr;   // the update's B operand is rebuilt for every block: no copy
+    CD_TRY(scratch_alloc((uint16_t**)&nBs, (size_t)kSlices * b * nk, st));
     scratch_free(w->Bs, st);
-    w->Ls = nLs;
     w->Bs = nBs;
     w->kcap = nk;
   }
-  CD_CUDA(cudaStreamSynchronize(st));
-  cudaFree(f->L);
-  f->L = nL;
   f->Mcap = newcap;
   return CD_OK;
+}
+
+// capacity after growth: what is needed, and at least 256 vectors more, in whole 32-vector chunks
+static int64_t grown_capacity(int64_t need, int64_t cap, int64_t Mmax) {
+  int64_t nc = std::max<int64_t>(need, cap + 256);
+  nc = (nc + 31) / 32 * 32;
+  return std::min<int64_t>(nc, Mmax);
 }
 
 // reduce = true: first step of the two-step scheme (rows below tau dropped and
@@ -399,7 +401,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   // bytes per vector of capacity, and the fixed part
   const double per_vec = 8.0 * ld + (slice ? 2.0 * kSlices * (n + b) : 0.0);
   const double fixed = 8.0 * ld * (b + 2) + 8.0 * Mmax * b + (slice ? 8.0 * b * ld + 4.0 * n : 0.0);
-  int64_t Mcap = std::min<int64_t>(Mmax, std::max<int64_t>(256, 5 * N));
+  // the stores grow in place, so they start small (one vector per basis function)
+  int64_t Mcap = std::min<int64_t>(Mmax, std::max<int64_t>(256, N));
   if (fixed + per_vec * Mcap > budget) {
     Mcap = (int64_t)((budget - fixed) / per_vec);
     if (Mcap < 1) { set_error("device memory budget too small for the decomposition"); return CD_ENOMEM; }
@@ -425,7 +428,9 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   }
   Work w;
   w.st = st;
-  CD_TRY(dalloc(&f->L, (size_t)Mcap * ld));
+  CD_TRY(f->Lvm.reserve(sizeof(double) * (size_t)Mmax * ld));
+  CD_TRY(f->Lvm.grow(sizeof(double) * (size_t)Mcap * ld));
+  f->L = (double*)f->Lvm.base;
   f->Mcap = Mcap;
   CD_TRY(scratch_alloc(&w.pool, (size_t)b * ld, st));
   CD_TRY(scratch_alloc(&w.D0, (size_t)ld, st));
@@ -439,7 +444,9 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   CD_TRY(scratch_alloc(&w.res_dev, 1, st));
   if (slice) {
     w.kcap = (Mcap + 31) / 32 * 32;
-    CD_TRY(scratch_alloc((uint16_t**)&w.Ls, (size_t)kSlices * std::max<int64_t>(n, 1) * w.kcap, st));
+    CD_TRY(w.Lsvm.reserve(slice_chunk_bytes(n) * (size_t)((Mmax + 31) / 32)));
+    CD_TRY(w.Lsvm.grow(slice_chunk_bytes(n) * (size_t)(w.kcap / 32)));
+    w.Ls = w.Lsvm.base;
     CD_TRY(scratch_alloc((uint16_t**)&w.Bs, (size_t)kSlices * b * w.kcap, st));
     CD_TRY(scratch_alloc(&w.Dint, (size_t)b * ld, st));
     CD_TRY(scratch_alloc(&w.erow, (size_t)std::max<int64_t>(n, 1), st));
@@ -561,8 +568,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     int32_t* idx_dev = nullptr;
     CD_TRY(scratch_alloc(&idx_dev, (size_t)std::max<int64_t>(m, 1), st));
     if (m > 0) CD_CUDA(cudaMemcpyAsync(idx_dev, idx.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-    double* nL = nullptr;
-    CD_TRY(dalloc(&nL, (size_t)f->Mcap * ldm));
+    VmArray nLvm;
+    CD_TRY(nLvm.reserve(sizeof(double) * (size_t)Mmax * ldm));
+    CD_TRY(nLvm.grow(sizeof(double) * (size_t)f->Mcap * ldm));
+    double* nL = (double*)nLvm.base;
     CD_TRY(launch_compact_f64(f->L, ld, idx_dev, m, K, nL, ldm, st));
     double *npool = nullptr, *nD0 = nullptr, *nD1 = nullptr;
     CD_TRY(scratch_alloc(&npool, (size_t)b * ldm, st));
@@ -573,21 +582,25 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     CD_CUDA(cudaMemsetAsync(nD1, 0, sizeof(double) * ldm, st));
     CD_TRY(launch_compact_f64(w.pool, ld, idx_dev, m, b, npool, ldm, st));
     CD_TRY(launch_compact_f64(Dcur, ld, idx_dev, m, 1, nD0, ldm, st));
+    VmArray nLsvm;
     if (slice) {
-      void* nLs = nullptr;
       int32_t* nerow = nullptr;
-      CD_TRY(scratch_alloc((uint16_t**)&nLs, (size_t)kSlices * std::max<int64_t>(m, 1) * w.kcap, st));
+      CD_TRY(nLsvm.reserve(slice_chunk_bytes(m) * (size_t)((Mmax + 31) / 32)));
+      CD_TRY(nLsvm.grow(slice_chunk_bytes(m) * (size_t)(w.kcap / 32)));
       CD_TRY(scratch_alloc(&nerow, (size_t)std::max<int64_t>(m, 1), st));
-      CD_TRY(launch_compact_rows16(w.Ls, n, idx_dev, m, kSlices, w.kcap * 2, nLs, st));
+      // every (chunk, slice) plane keeps the live rows, 64 bytes each
+      CD_TRY(launch_compact_rows16(w.Ls, n, idx_dev, m, (int)((w.kcap / 32) * kSlices), 64, nLsvm.base, st));
       CD_TRY(launch_compact_i32(w.erow, idx_dev, m, nerow, st));
-      scratch_free(w.Ls, st);
       scratch_free(w.erow, st);
-      w.Ls = nLs;
       w.erow = nerow;
     }
     CD_CUDA(cudaStreamSynchronize(st));
-    cudaFree(f->L);
-    f->L = nL;
+    f->Lvm.swap(nLvm);        // the old stores are released when nLvm / nLsvm go out of scope
+    f->L = (double*)f->Lvm.base;
+    if (slice) {
+      w.Lsvm.swap(nLsvm);
+      w.Ls = w.Lsvm.base;
+    }
     scratch_free(w.pool, st);
     scratch_free(w.D0, st);
     scratch_free(w.D1, st);
@@ -748,9 +761,9 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         CD_CUDA(cudaMemcpyAsync(w.slots_dev, w.upd_slots.data(), sizeof(int32_t) * nb_upd, cudaMemcpyHostToDevice, s2));
         CD_CUDA(cudaMemcpyAsync(w.rows_dev, w.upd_rows.data(), sizeof(int64_t) * nb_upd, cudaMemcpyHostToDevice, s2));
         CD_CUDA(cudaMemcpyAsync(w.valid_dev, w.upd_valid.data(), sizeof(int64_t) * nb_upd, cudaMemcpyHostToDevice, s2));
-        CD_TRY(launch_gather_slices(w.Ls, n, w.kcap, w.rows_dev, w.valid_dev, nb_upd, kSlices, K, w.Bs, w.kcap, s2));
+        CD_TRY(launch_gather_slices(w.Ls, n, w.rows_dev, w.valid_dev, nb_upd, kSlices, K, w.Bs, w.kcap, s2));
         CD_CUDA(cudaMemsetAsync(w.Dint, 0, sizeof(unsigned long long) * nb_upd * ld, s2));
-        CD_TRY(ozaki_gemm(plan, w.Ls, n, w.kcap, w.Bs, nb_upd, w.kcap, K, w.Dint, ld, 1, w.err, s2));
+        CD_TRY(ozaki_gemm(plan, w.Ls, n, w.kcap, w.Bs, nb_upd, w.kcap, K, w.Dint, ld, 1, w.err, s2, false, true));
         CD_CUDA(cudaEventRecord(w.ev_g1, s2));
         CD_CUDA(cudaEventRecord(w.ev_gemm, s2));
         for (int x = 0; x < nb_upd; ++x) upd_flops += 2.0 * (double)n * (double)(K - w.upd_valid[x]);
@@ -826,7 +839,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
         if (slot_row[sl] >= 0) { srows.push_back(slot_row[sl]); sslots.push_back(sl); }
       const int nocc = (int)srows.size();
       if (K + nocc > f->Mcap && f->Mcap < Mmax) {
-        int64_t nc = std::min<int64_t>(Mmax, std::max<int64_t>(K + nocc, f->Mcap + f->Mcap / 4 + 64));
+        int64_t nc = grown_capacity(K + nocc, f->Mcap, Mmax);
         if (fixed + per_vec * nc > budget) nc = (int64_t)((budget - fixed) / per_vec);
         if (nc > f->Mcap) CD_TRY(grow_vectors(f, &w, slice, b, nc, K, st));
       }
@@ -962,7 +975,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
           set_error("number of vectors exceeds max_vectors = " + std::to_string(Mmax));
           return CD_ENOMEM;
         }
-        int64_t nc = std::min<int64_t>(Mmax, f->Mcap + f->Mcap / 4 + 64);
+        int64_t nc = grown_capacity(K + 1, f->Mcap, Mmax);
         if (fixed + per_vec * nc > budget) nc = (int64_t)((budget - fixed) / per_vec);
         if (nc <= f->Mcap) { set_error("device memory budget exhausted at M = " + std::to_string(K)); return CD_ENOMEM; }
         CD_TRY(grow_vectors(f, &w, slice, b, nc, K, st));
@@ -1028,7 +1041,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     }
     // slices of this block's vectors, for the next block's update
     if (slice && !done && K > Kb)
-      CD_TRY(launch_slice_rows_f64(f->L + Kb * ld, 1, ld, n, K - Kb, w.erow, kSlices, w.Ls, n, w.kcap, Kb, st));
+      CD_TRY(launch_slice_rows_f64(f->L + Kb * ld, 1, ld, n, K - Kb, w.erow, kSlices, w.Ls, n, w.kcap, Kb, st, true));
   }
   if (slice) {
     int herr = 0;
@@ -1047,25 +1060,26 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   }
   // the slice store is no longer needed: release it before the FP32 copy
   CD_CUDA(cudaStreamSynchronize(st));
-  scratch_free(w.Ls, st); w.Ls = nullptr;
-  scratch_free(w.Bs, st); w.Bs = nullptr;
-  scratch_free(w.pool, st); w.pool = nullptr;
   if (mpool) {
     uint64_t high = 0;
     cudaMemPoolGetAttribute(mpool, cudaMemPoolAttrUsedMemHigh, &high);
-    // the slices and the vectors are both at their largest at the end of the loop
-    f->mem_peak = (double)(high > pool_used0 ? high - pool_used0 : 0) + 8.0 * (double)f->Mcap * (double)ld;
+    // the slice and vector stores are both at their largest at the end of the loop
+    f->mem_peak = (double)(high > pool_used0 ? high - pool_used0 : 0) + (double)f->Lvm.mapped + (double)w.Lsvm.mapped;
   }
+  w.Lsvm.release();
+  w.Ls = nullptr;
+  scratch_free(w.Bs, st); w.Bs = nullptr;
+  scratch_free(w.pool, st); w.pool = nullptr;
   if (f->vec_precision == CD_VEC_FP32 && K > 0) {
     // the stored vectors become FP32: the FP64 array is released once the copy is made
     CD_TRY(dalloc(&f->L32, (size_t)K * ld));
     CD_TRY(launch_to_fp32(f->L, ld, K, ld, f->L32, st));
-    f->mem_peak = std::max(f->mem_peak, 8.0 * (double)f->Mcap * ld + 4.0 * (double)K * ld);
+    f->mem_peak = std::max(f->mem_peak, (double)f->Lvm.mapped + 4.0 * (double)K * ld);
     CD_CUDA(cudaStreamSynchronize(st));
-    cudaFree(f->L);
+    f->Lvm.release();
     f->L = nullptr;
   }
-  f->mem_resident = (f->L ? 8.0 * (double)f->Mcap * ld : 0.0) + (f->L32 ? 4.0 * (double)K * ld : 0.0);
+  f->mem_resident = (double)f->Lvm.mapped + (f->L32 ? 4.0 * (double)K * ld : 0.0);
   CD_CUDA(cudaStreamSynchronize(st));
   const double t_all = now_ms() - t_start;
   f->stats[0] = s->ms_setup;

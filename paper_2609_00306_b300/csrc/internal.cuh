@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 #include "../../include/cderi.h"
 
@@ -47,6 +48,31 @@ template <class T>
 int scratch_alloc(T** p, size_t n, cudaStream_t st) {
   return scratch_alloc_bytes((void**)p, sizeof(T) * (n ? n : 1), st);
 }
+
+// ----- device arrays that grow in place (vmm.cu) ------------------------------
+// A virtual address range reserved once; physical memory mapped into it in
+// granules as the array grows.  The address never changes and growing copies
+// nothing.  release() waits for the device (like cudaFree) before unmapping.
+struct VmArray {
+  void* base = nullptr;
+  size_t reserved = 0;      // bytes of address space
+  size_t mapped = 0;        // bytes backed by device memory (a multiple of gran)
+  size_t gran = 0;
+  int device = 0;
+  struct Piece { size_t offset, size; unsigned long long handle; };
+  std::vector<Piece> pieces;
+  int reserve(size_t bytes);     // reserve address space (nothing mapped)
+  int grow(size_t bytes);        // map memory so that [0, bytes) is usable
+  void release();
+  void swap(VmArray& o) {
+    std::swap(base, o.base); std::swap(reserved, o.reserved); std::swap(mapped, o.mapped);
+    std::swap(gran, o.gran); std::swap(device, o.device); pieces.swap(o.pieces);
+  }
+  VmArray() = default;
+  VmArray(const VmArray&) = delete;
+  VmArray& operator=(const VmArray&) = delete;
+  ~VmArray() { release(); }
+};
 
 // ----- Boys function table (Taylor expansion about grid points) ------------
 // Row k holds F_0..F_12 at T_k = k * kBoysStep and, in the last column,
@@ -204,7 +230,8 @@ struct cd_factor {
   cd_system* sys = nullptr;
   bool owns_sys = false;
   int64_t M = 0, Mcap = 0, ld = 0, n = 0;
-  double* L = nullptr;      // FP64 vectors [Mcap][ld]
+  double* L = nullptr;      // FP64 vectors [Mcap][ld] (the base of Lvm)
+  cd::VmArray Lvm;          // their storage: grows in place as vectors are added
   float* L32 = nullptr;     // FP32 copy [M][ld] when requested
   int vec_precision = CD_FP64;
   std::vector<int64_t> piv;

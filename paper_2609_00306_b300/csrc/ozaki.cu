@@ -71,7 +71,8 @@ template <int SA, int SB, int KEEP, int BN, int STAGES>
 __global__ void __launch_bounds__(kThreads, BN == 32 ? 2 : 1)
 ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              int64_t m_rows, int64_t n_rows, int nkb_total, int kb_per_split, int kcb, int F,
-             unsigned long long* __restrict__ D, int64_t ldd, int* err, int sym, unsigned long long wait_ns) {
+             unsigned long long* __restrict__ D, int64_t ldd, int* err, int sym, unsigned long long wait_ns,
+             int a4d) {
   using C = Cfg<SA, SB, KEEP, BN, STAGES>;
   // symmetric product (A == B): tiles entirely below the diagonal are skipped
   if (sym && (int64_t)blockIdx.x * BN + BN <= (int64_t)blockIdx.y * BM) return;
@@ -119,7 +120,8 @@ ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
           uint8_t* b = a + C::A_BYTES;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE_BYTES);
           const int kx = (kb0 + i) * BK;
-          tc::tma_load_3d(a, &tmA, kx, (int32_t)m0, 0, &full[s]);
+          if (a4d) tc::tma_load_4d(a, &tmA, 0, (int32_t)m0, 0, kb0 + i, &full[s]);   // chunk kb = 32 k-values
+          else tc::tma_load_3d(a, &tmA, kx, (int32_t)m0, 0, &full[s]);
           tc::tma_load_3d(b, &tmB, kx, (int32_t)n0, 0, &full[s]);
           issued = i + 1;
         }
@@ -270,9 +272,26 @@ int make_map(CUtensorMap* map, const void* base, int S, int64_t rows, int64_t kd
   return CD_OK;
 }
 
+// 4D map over slices stored in k-chunks of 32: [chunks][S][rows][32] bf16; box {32, box_rows, S, 1}
+int make_map_chunked(CUtensorMap* map, const void* base, int S, int64_t rows, int64_t kdim, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) { set_error("cuTensorMapEncodeTiled unavailable"); return CD_ECUDA; }
+  if ((uintptr_t)base & 15) { set_error("slice tensor not 16-byte aligned"); return CD_EINVAL; }
+  const int64_t chunks = (kdim + BK - 1) / BK;
+  cuuint64_t dims[4] = {(cuuint64_t)BK, (cuuint64_t)rows, (cuuint64_t)S, (cuuint64_t)chunks};
+  cuuint64_t strides[3] = {(cuuint64_t)(BK * 2), (cuuint64_t)(BK * 2 * rows), (cuuint64_t)(BK * 2 * rows * S)};
+  cuuint32_t box[4] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)S, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled (chunked) failed: " + std::to_string((int)r)); return CD_EINVAL; }
+  return CD_OK;
+}
+
 template <int SA, int SB, int KEEP, int BN, int STAGES>
 int run(const CUtensorMap& ta, const CUtensorMap& tb, int64_t a_rows, int64_t b_rows, int nkb, int ksplit, int kcb,
-        int F, unsigned long long* D, int64_t ldd, int* err, int sym, cudaStream_t st) {
+        int F, unsigned long long* D, int64_t ldd, int* err, int sym, cudaStream_t st, int a4d) {
   using C = Cfg<SA, SB, KEEP, BN, STAGES>;
   auto k = ozaki_kernel<SA, SB, KEEP, BN, STAGES>;
   CD_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
@@ -281,13 +300,13 @@ int run(const CUtensorMap& ta, const CUtensorMap& tb, int64_t a_rows, int64_t b_
   const int64_t row_tiles = (a_rows + BM - 1) / BM;
   if (row_tiles > 65535) { set_error("ozaki_gemm: too many row tiles"); return CD_EINVAL; }
   dim3 grid((unsigned)((b_rows + BN - 1) / BN), (unsigned)row_tiles, (unsigned)nsplit);
-  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err, sym, wait_limit_ns());
+  k<<<grid, kThreads, C::SMEM, st>>>(ta, tb, a_rows, b_rows, nkb, per, kcb, F, D, ldd, err, sym, wait_limit_ns(), a4d);
   count_launch();
   CD_CUDA(cudaGetLastError());
   return CD_OK;
 }
 
-template <int S>
+template <int S, bool CHUNKED>
 __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t src_rs, int64_t src_ks, int64_t rows,
                                   int64_t kcount, const int32_t* __restrict__ row_exp,
                                   __nv_bfloat16* __restrict__ dst, int64_t dst_rows, int64_t kpitch, int64_t k0) {
@@ -297,47 +316,58 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, int64_t src_rs
   // round(x 2^(8S-1-e)) from the bit pattern, then integer digits
   float a[S];
   fixed_digits<S>(scaled_double_to_ll(src[r * src_rs + k * src_ks], 8 * S - 1 - row_exp[r]), a);
+  const int64_t kk = k0 + k;
 #pragma unroll
-  for (int s = 0; s < S; ++s) dst[((int64_t)s * dst_rows + r) * kpitch + k0 + k] = __float2bfloat16_rn(a[s]);
+  for (int s = 0; s < S; ++s) {
+    const int64_t at = CHUNKED ? (((kk / kSliceChunk) * S + s) * dst_rows + r) * kSliceChunk + kk % kSliceChunk
+                               : ((int64_t)s * dst_rows + r) * kpitch + kk;
+    dst[at] = __float2bfloat16_rn(a[s]);
+  }
 }
 
 }  // namespace
 
 int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpitch, const void* Bs, int64_t b_rows,
                int64_t b_kpitch, int64_t kdim, unsigned long long* D, int64_t ldd, int ksplit, int* err_dev,
-               cudaStream_t st, bool sym) {
+               cudaStream_t st, bool sym, bool a_chunked) {
   const int symi = sym ? 1 : 0;
   if (kdim <= 0 || a_rows <= 0 || b_rows <= 0) return CD_OK;
   CUtensorMap ta, tb;
   const int bn = (p.SA >= 5) ? 32 : 64;   // accumulator width: 2 x groups x bn must fit 512 TMEM columns
-  CD_TRY(make_map(&ta, As, p.SA, a_rows, kdim, a_kpitch, BM));
+  if (a_chunked) CD_TRY(make_map_chunked(&ta, As, p.SA, a_rows, kdim, BM));
+  else CD_TRY(make_map(&ta, As, p.SA, a_rows, kdim, a_kpitch, BM));
+  const int a4d = a_chunked ? 1 : 0;
   CD_TRY(make_map(&tb, Bs, p.SB, b_rows, kdim, b_kpitch, bn));
   const int nkb = (int)((kdim + BK - 1) / BK);
   // exactness of the FP32 accumulation: (products sharing an accumulator) * kc * 129^2 <= 2^24
   const int maxg = std::min(p.KEEP - 1, std::min(p.SA, p.SB));
   int kc = (int)(16777216.0 / (std::max(1, maxg) * kSliceProdMax));
   int kcb = std::max(1, kc / BK);
-  if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 64, 5>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
-  if (p.SA == 5 && p.SB == 5 && p.KEEP == 6) return run<5, 5, 6, 32, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
-  if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
-  if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 32, 3>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
-  if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st);
+  if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 64, 5>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
+  if (p.SA == 5 && p.SB == 5 && p.KEEP == 6) return run<5, 5, 6, 32, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
+  if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
+  if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 32, 3>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
+  if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
   set_error("ozaki_gemm: unsupported slice plan");
   return CD_EINVAL;
 }
 
 int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int64_t rows, int64_t kcount,
                           const int32_t* row_exp, int S, void* dst, int64_t dst_rows, int64_t kpitch, int64_t k0,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool chunked) {
   const int64_t tot = rows * kcount;
   if (tot <= 0) return CD_OK;
   const unsigned grid = (unsigned)((tot + 255) / 256);
   __nv_bfloat16* d = (__nv_bfloat16*)dst;
-  if (S == 7) slice_rows_kernel<7><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
-  else if (S == 5) slice_rows_kernel<5><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
-  else if (S == 4) slice_rows_kernel<4><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
-  else if (S == 3) slice_rows_kernel<3><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
-  else if (S == 1) slice_rows_kernel<1><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  if (chunked) {
+    if (S != 7) { set_error("slice: the chunked layout holds 7 slices"); return CD_EINVAL; }
+    slice_rows_kernel<7, true><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  }
+  else if (S == 7) slice_rows_kernel<7, false><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 5) slice_rows_kernel<5, false><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 4) slice_rows_kernel<4, false><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 3) slice_rows_kernel<3, false><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
+  else if (S == 1) slice_rows_kernel<1, false><<<grid, 256, 0, st>>>(src, src_rs, src_ks, rows, kcount, row_exp, d, dst_rows, kpitch, k0);
   else { set_error("slice: unsupported slice count"); return CD_EINVAL; }
   count_launch();
   CD_CUDA(cudaGetLastError());
@@ -463,8 +493,9 @@ __global__ void row_exp_sqrt_kernel(const double* __restrict__ d, int64_t n, int
   if (v > 0.0) frexp(sqrt(v), &ex);
   e[r] = ex;
 }
-// Bs[s][j][k] = Ls[s][rows[j]][k] for valid[j] <= k < K, else 0 (k < kfill)
-__global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64_t n, int64_t kpitch,
+// Bs[s][j][k] = slice s of row rows[j], vector k, for valid[j] <= k < K, else 0
+// (k < kfill); Ls holds the slices in k-chunks of 32: [k/32][S][n][32]
+__global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64_t n,
                                      const int64_t* __restrict__ rows, const int64_t* __restrict__ valid, int nb,
                                      int S, int64_t K, int64_t kfill, __nv_bfloat16* __restrict__ Bs,
                                      int64_t bpitch) {
@@ -476,7 +507,8 @@ __global__ void gather_slices_kernel(const __nv_bfloat16* __restrict__ Ls, int64
   const int j = (int)(rem / kfill);
   const int64_t k = rem % kfill;
   __nv_bfloat16 v = __float2bfloat16(0.0f);
-  if (k >= valid[j] && k < K) v = Ls[((int64_t)s * n + rows[j]) * kpitch + k];
+  if (k >= valid[j] && k < K)
+    v = Ls[(((k / kSliceChunk) * S + s) * n + rows[j]) * kSliceChunk + k % kSliceChunk];
   Bs[((int64_t)s * nb + j) * bpitch + k] = v;
 }
 // cols[slot[j]][r] -= 2^(e_r + e_{row j} - F) * D[j][r]
@@ -501,12 +533,12 @@ int launch_row_exp_sqrt(const double* d, int64_t n, int32_t* e, cudaStream_t st)
   return CD_OK;
 }
 
-int launch_gather_slices(const void* Ls, int64_t n, int64_t kpitch, const int64_t* rows, const int64_t* valid, int nb,
+int launch_gather_slices(const void* Ls, int64_t n, const int64_t* rows, const int64_t* valid, int nb,
                          int S, int64_t K, void* Bs, int64_t bpitch, cudaStream_t st) {
   const int64_t kfill = (K + 31) / 32 * 32;
   const int64_t tot = (int64_t)S * nb * kfill;
   if (tot <= 0) return CD_OK;
-  gather_slices_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((const __nv_bfloat16*)Ls, n, kpitch, rows, valid,
+  gather_slices_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>((const __nv_bfloat16*)Ls, n, rows, valid,
                                                                       nb, S, K, kfill, (__nv_bfloat16*)Bs, bpitch);
   count_launch();
   CD_CUDA(cudaGetLastError());

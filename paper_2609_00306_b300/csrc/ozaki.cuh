@@ -77,19 +77,27 @@ struct OzakiPlan {
 // sym: A and B are the same matrix; tiles entirely below the diagonal
 // (column tile end <= row tile start) are skipped, so only D[n][m] with m <= n
 // (and some near the diagonal) is written.
+// a_chunked: A is stored in k-chunks of 32 instead, [kdim/32][SA][a_rows][32]
+// (the growable slice store of the decomposition; a_kpitch is then unused).
 int ozaki_gemm(const OzakiPlan& plan, const void* As, int64_t a_rows, int64_t a_kpitch,
                const void* Bs, int64_t b_rows, int64_t b_kpitch, int64_t kdim,
-               unsigned long long* D, int64_t ldd, int ksplit, int* err_dev, cudaStream_t st, bool sym = false);
+               unsigned long long* D, int64_t ldd, int ksplit, int* err_dev, cudaStream_t st, bool sym = false,
+               bool a_chunked = false);
 
 // Slicing: x = X / 2^e (row exponent e given) -> S bf16 integer slices.
 // src element (r, k) at src[r * src_rs + k * src_ks]; dst[s][r][k0 + k] with pitch kpitch.
+// chunked: dst in k-chunks of 32, [k/32][S][dst_rows][32] (kpitch unused).
 int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int64_t rows, int64_t kcount,
                           const int32_t* row_exp, int S, void* dst, int64_t dst_rows, int64_t kpitch, int64_t k0,
-                          cudaStream_t st);
+                          cudaStream_t st, bool chunked = false);
 
 int launch_row_exp_sqrt(const double* d, int64_t n, int32_t* e, cudaStream_t st);
-int launch_gather_slices(const void* Ls, int64_t n, int64_t kpitch, const int64_t* rows, const int64_t* valid, int nb,
+// Ls in k-chunks of 32 ([K/32][S][n][32], the decomposition's slice store);
+// Bs flat [S][nb][bpitch]
+int launch_gather_slices(const void* Ls, int64_t n, const int64_t* rows, const int64_t* valid, int nb,
                          int S, int64_t K, void* Bs, int64_t bpitch, cudaStream_t st);
+// elements of one k-chunk of 32 slices of one row: the chunk layout's row pitch is 64 bytes
+constexpr int kSliceChunk = 32;
 int launch_colupd_finalize(const unsigned long long* D, int64_t ldd, int64_t n, int nb, const int32_t* e,
                            const int64_t* rows, const int32_t* slots, int F, double* cols, int64_t ld, cudaStream_t st);
 
