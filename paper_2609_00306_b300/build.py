@@ -48,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int = 8) -> str:
     for p in procs:
         _wait(p, verbose)
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([NVCC, *FLAGS, "-shared", "-o", tmp, *objs, "-lcuda"])
+    subprocess.check_call([NVCC, *FLAGS, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
     return LIB
 
