@@ -86,7 +86,7 @@ typedef struct {
   double  span;         /* span factor eta in (0, 1] of CD_ALG_SPAN / CD_ALG_TWOSTEP (0 = 0.01) */
   const uint8_t* candidates; /* host [n_rows] (system row order), nonzero = the row may be a pivot;
                               * NULL = every row.  The Cholesky basis is then chosen from that
-                              * block of the matrix only (Sec. 5: the (LL|LL) diagonals of the
+                              * block of the matrix only (Sec. 6.2: the (LL|LL) diagonals of the
                               * spin-free relativistic matrix); the stop test max D < tau runs over
                               * the candidate rows, the vectors still cover every row, and rows
                               * outside the block carry no tau guarantee.  With CD_ALG_TWOSTEP the

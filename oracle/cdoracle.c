@@ -433,7 +433,7 @@ static void or_subtr_rows(void* h, const int* ri, const int* rj, int64_t r0, int
 /* and Dmax, the argmax and the stop test run over those rows; the vectors    */
 /* still cover every row.  This is the restriction of the Cholesky basis to  */
 /* one block of the matrix (the (LL|LL) diagonals in the spin-free            */
-/* relativistic case of Sec. 5, where no (SS|SS) diagonals are then needed).  */
+/* relativistic case of Sec. 6.2, where no (SS|SS) diagonals are then needed).  */
 /* L is row-major [mcap][npairs].  Returns M >= 0, or                         */
 /*   -1 if M would exceed mcap, -2 if a pivot diagonal is not positive or a   */
 /*   residual diagonal is below -1e-10 * max D^1 (matrix not PSD).            */

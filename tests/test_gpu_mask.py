@@ -1,5 +1,5 @@
 """Candidate-restricted decompositions on the GPU (cd_opts_t.candidates: the
-Cholesky basis chosen from one block of the matrix, Sec. 5) against the
+Cholesky basis chosen from one block of the matrix, Sec. 6.2) against the
 oracle's ``cd(candidates=...)`` / ``cd_span(candidates=...)``.
 
 Same bar as the other parity tests: identical basis and vector count except at

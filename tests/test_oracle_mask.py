@@ -1,6 +1,6 @@
 """Pins for the oracle's candidate-restricted decomposition (the Cholesky basis
 chosen from one block of the matrix only: the (LL|LL) diagonals of the
-spin-free relativistic case, Sec. 5):
+spin-free relativistic case, Sec. 6.2):
 
 * The residual diagonals of candidate rows depend only on the candidate block
   A[C, C] (they are its Schur complements), so the restricted pivot sequence is
