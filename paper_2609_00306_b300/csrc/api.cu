@@ -328,6 +328,7 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : {eri.fork, eri.join[0], eri.join[1]}) if (e) cudaEventDestroy(e);
+    scratch_free(eri.counters, st);
     for (void* p : {(void*)ds_dev, (void*)slot_of_row, (void*)piv_dev, (void*)pivd_dev, (void*)sm_rows,
                     (void*)sm_slots})
       scratch_free(p, st);
@@ -478,6 +479,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   w.cand_vals_h.resize(cand_cap);
   for (auto& e : w.ev) CD_CUDA(cudaEventCreate(&e));
   for (auto& x : w.eri.side) CD_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+  CD_TRY(scratch_alloc(&w.eri.counters, 3, st));
+  CD_TRY(eri_resident_ctas(w.eri.resident, &w.eri.sms));
   CD_CUDA(cudaEventCreateWithFlags(&w.eri.fork, cudaEventDisableTiming));
   for (auto& e : w.eri.join) CD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   // full pivoting runs the in-block steps on the device (CDERI_HOST_STEPS=1: one

@@ -359,16 +359,14 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
   }
 }
 
-// grid: x = tiles of bra shell pairs of one class, y = ket groups
+// One work item: bra shell pairs [b0 + 128 tile, +128) of one class against ket group g.
 template <int LA, int LB>
-__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, const int64_t* __restrict__ order, int64_t b0,
-                                                          int64_t b1, PairSet ket,
-                                                          const KetGroup* __restrict__ groups, double* __restrict__ out,
-                                                          int64_t ld, const double* __restrict__ tab,
-                                                          unsigned long long* __restrict__ op_count) {
-  const KetGroup kg = groups[blockIdx.y];
-  const int64_t ib = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long ops = 0;
+__device__ __forceinline__ void column_item(const PairSet& bra, const int64_t* __restrict__ order, int64_t b0,
+                                            int64_t b1, const PairSet& ket, const KetGroup* __restrict__ groups,
+                                            int64_t tile, int g, double* __restrict__ out, int64_t ld,
+                                            const double* __restrict__ tab, unsigned long long& ops) {
+  const KetGroup kg = groups[g];
+  const int64_t ib = b0 + tile * 128 + threadIdx.x;
   if (ib < b1) {
     // bra shell pair: the ib-th of the class range, or the ib-th entry of a subset list
     const int64_t sb = order ? __ldg(order + ib) : ib;
@@ -381,6 +379,37 @@ __global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, const int
       if (kg.nc == 1) column_block<LA, LB, 1, 1, 1>(bra, sb, ket, kg, out, ld, tab, ops);
       else if (kg.nc <= 3) column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab, ops);
       else column_block<LA, LB, 1, 1, kMaxKetGroup>(bra, sb, ket, kg, out, ld, tab, ops);
+    }
+  }
+}
+
+// Without a work counter: grid x = tiles of 128 bra shell pairs of one class,
+// y = ket groups.  With one (persistent): a grid of resident CTAs takes items
+// (tile, group) from the counter, tile-major, so the heaviest bra tiles (the
+// class is sorted by primitive pairs, descending) go first and the last items
+// are the lightest: the launch ends with a short tail.
+template <int LA, int LB>
+__global__ void __launch_bounds__(128) eri_columns_kernel(PairSet bra, const int64_t* __restrict__ order, int64_t b0,
+                                                          int64_t b1, PairSet ket,
+                                                          const KetGroup* __restrict__ groups, double* __restrict__ out,
+                                                          int64_t ld, const double* __restrict__ tab,
+                                                          unsigned long long* __restrict__ op_count,
+                                                          unsigned* __restrict__ work_counter, int ngroups) {
+  unsigned long long ops = 0;
+  if (!work_counter) {
+    column_item<LA, LB>(bra, order, b0, b1, ket, groups, blockIdx.x, blockIdx.y, out, ld, tab, ops);
+  } else {
+    const int64_t ntiles = (b1 - b0 + 127) / 128;
+    const unsigned long long nitems = (unsigned long long)ntiles * (unsigned long long)ngroups;
+    __shared__ unsigned s_item;
+    for (;;) {
+      if (threadIdx.x == 0) s_item = atomicAdd(work_counter, 1u);
+      __syncthreads();
+      const unsigned long long it = s_item;
+      __syncthreads();
+      if (it >= nitems) break;
+      column_item<LA, LB>(bra, order, b0, b1, ket, groups, (int64_t)(it / ngroups), (int)(it % ngroups), out, ld,
+                          tab, ops);
     }
   }
   if (op_count) {  // warp sum, one atomic per warp
@@ -419,15 +448,25 @@ int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64
     CD_CUDA(cudaStreamWaitEvent(es->side[0], es->fork, 0));
     CD_CUDA(cudaStreamWaitEvent(es->side[1], es->fork, 0));
   }
+  // persistent grids need one zeroed work counter per class
+  if (es && es->counters) CD_CUDA(cudaMemsetAsync(es->counters, 0, 3 * sizeof(unsigned), st));
   // the most expensive class (pp bra pairs) is launched first, on the calling stream
   for (int cls = 2; cls >= 0; --cls) {
     int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
     if (b1 <= b0) continue;
     cudaStream_t s = es ? (cls == 2 ? st : es->side[cls]) : st;
-    dim3 grid((unsigned)((b1 - b0 + 127) / 128), (unsigned)nket);
-    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
-    else eri_columns_kernel<1, 1><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count);
+    const int64_t ntiles = (b1 - b0 + 127) / 128;
+    unsigned* ctr = (es && es->counters) ? es->counters + cls : nullptr;
+    dim3 grid((unsigned)ntiles, (unsigned)nket);
+    if (ctr) {
+      // as many CTAs as are resident at once, or fewer when there are fewer items
+      const int per_sm = es->resident[cls] > 0 ? es->resident[cls] : 2;
+      const int64_t items = ntiles * (int64_t)nket;
+      grid = dim3((unsigned)std::min<int64_t>(items, (int64_t)per_sm * es->sms), 1);
+    }
+    if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
+    else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
+    else eri_columns_kernel<1, 1><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
     count_launch();
   }
   CD_CUDA(cudaGetLastError());
@@ -437,6 +476,16 @@ int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64
       CD_CUDA(cudaStreamWaitEvent(st, es->join[k], 0));
     }
   }
+  return CD_OK;
+}
+
+int eri_resident_ctas(int* per_sm3, int* sms) {
+  int dev = 0;
+  CD_CUDA(cudaGetDevice(&dev));
+  CD_CUDA(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+  CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[0], eri_columns_kernel<0, 0>, 128, 0));
+  CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[1], eri_columns_kernel<1, 0>, 128, 0));
+  CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[2], eri_columns_kernel<1, 1>, 128, 0));
   return CD_OK;
 }
 

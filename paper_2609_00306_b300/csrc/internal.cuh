@@ -188,7 +188,13 @@ struct EriStreams {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[2] = {nullptr, nullptr};
+  // persistent grids (optional): 3 device work counters (one per class), the
+  // resident CTAs per SM of each class kernel and the SM count
+  unsigned* counters = nullptr;
+  int resident[3] = {0, 0, 0};
+  int sms = 0;
 };
+int eri_resident_ctas(int* per_sm3, int* sms);
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* groups_dev, int ngroups,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,
