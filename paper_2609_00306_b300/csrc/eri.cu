@@ -558,8 +558,14 @@ std::vector<KetGroup> group_kets(const std::vector<KetDesc>& kets) {
   std::vector<KetGroup> out;
   for (size_t i = 0; i < k.size();) {
     size_t j = i;
-    // (pp) ket shell pairs: up to all 9 components in one group; others up to 3
-    const size_t cap = (k[i].lc == 1 && k[i].ld == 1) ? (size_t)kMaxKetGroup : 3;
+    // (pp) ket shell pairs: up to all 9 components in one group (CDERI_PP_KET_GROUP
+    // lowers the cap: fewer accumulators per thread, less sharing); others up to 3
+    static const size_t pp_cap = [] {
+      const char* e = getenv("CDERI_PP_KET_GROUP");
+      const long v = e ? strtol(e, nullptr, 10) : (long)kMaxKetGroup;
+      return (size_t)(v >= 1 && v <= kMaxKetGroup ? v : kMaxKetGroup);
+    }();
+    const size_t cap = (k[i].lc == 1 && k[i].ld == 1) ? pp_cap : 3;
     while (j < k.size() && k[j].sp == k[i].sp && j - i < cap) ++j;
     KetGroup g;
     std::memset(&g, 0, sizeof(g));
