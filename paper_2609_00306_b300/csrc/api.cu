@@ -309,7 +309,6 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
   int32_t* sm_slots = nullptr;
   std::vector<int64_t> piv_h;
   std::vector<double> pivd_h;
-  cudaStream_t cap_st = nullptr;
   cudaGraphExec_t step_exec = nullptr;
   const void* step_key[3] = {nullptr, nullptr, nullptr};   // L, pool, D buffers the graph was captured with
   // second stream for the sliced update, used only with CDERI_OVERLAP_UPDATE=1
@@ -333,7 +332,6 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
                     (void*)sm_slots})
       scratch_free(p, st);
     if (step_exec) cudaGraphExecDestroy(step_exec);
-    if (cap_st) cudaStreamDestroy(cap_st);
     for (cudaStream_t x : eri.side) if (x) cudaStreamDestroy(x);
     for (cudaEvent_t e : {ev_ready, ev_gemm, ev_g0, ev_g1}) if (e) cudaEventDestroy(e);
     if (st2) cudaStreamDestroy(st2);
@@ -493,7 +491,6 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     CD_TRY(scratch_alloc(&w.pivd_dev, (size_t)Mmax, st));
     CD_TRY(scratch_alloc(&w.sm_rows, (size_t)b, st));
     CD_TRY(scratch_alloc(&w.sm_slots, (size_t)b, st));
-    CD_CUDA(cudaStreamCreateWithFlags(&w.cap_st, cudaStreamNonBlocking));
     w.piv_h.resize(b);
     w.pivd_h.resize(b);
   }
@@ -863,19 +860,8 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
       CD_CUDA(cudaMemcpyAsync(w.ds_dev, &w.ds_h, sizeof(DevStep), cudaMemcpyHostToDevice, st));
       if (!w.step_exec || w.step_key[0] != f->L || w.step_key[1] != w.pool) {
         if (w.step_exec) { cudaGraphExecDestroy(w.step_exec); w.step_exec = nullptr; }
-        cudaGraph_t g = nullptr;
-        CD_CUDA(cudaStreamBeginCapture(w.cap_st, cudaStreamCaptureModeThreadLocal));
-        int crc = CD_OK;
-        for (int i = 0; i < b && crc == CD_OK; ++i)
-          crc = launch_finalize_dev(w.ds_dev, w.slot_of_row, w.pool, f->L, ld, n, neg_tol, cmask, w.piv_dev,
-                                    w.pivd_dev, w.sc, w.cap_st);
-        cudaError_t ce = cudaStreamEndCapture(w.cap_st, &g);
-        count_launch(-b);   // counted below, per graph launch
-        if (crc != CD_OK) { if (g) cudaGraphDestroy(g); return crc; }
-        if (ce != cudaSuccess) { set_error(std::string("step graph capture: ") + cudaGetErrorString(ce)); return CD_ECUDA; }
-        ce = cudaGraphInstantiate(&w.step_exec, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) { set_error(std::string("step graph: ") + cudaGetErrorString(ce)); return CD_ECUDA; }
+        CD_TRY(build_step_graph(&w.step_exec, b, w.ds_dev, w.slot_of_row, w.pool, f->L, ld, n, neg_tol, cmask,
+                                w.piv_dev, w.pivd_dev, w.sc));
         w.step_key[0] = f->L;
         w.step_key[1] = w.pool;
       }

@@ -10,6 +10,7 @@
 // The argmax is reduced warp -> CTA (shuffles) -> grid (last CTA to finish).
 #include <float.h>
 #include <math.h>
+#include <string>
 #include "internal.cuh"
 #include "pivot.cuh"
 
@@ -357,6 +358,46 @@ int launch_finalize_dev(DevStep* ds, int32_t* slot_of_row, const double* pool, c
                                                           sc);
   count_launch();
   CD_CUDA(cudaGetLastError());
+  return CD_OK;
+}
+
+int build_step_graph(cudaGraphExec_t* exec, int nsteps, DevStep* ds, int32_t* slot_of_row, const double* pool,
+                     const double* L, int64_t ld, int64_t n, double neg_tol, const uint8_t* cand, int64_t* piv,
+                     double* pivd, StepScratch* sc) {
+  // built node by node (no stream capture, so work that other threads put on
+  // the device meanwhile cannot disturb it)
+  *exec = nullptr;
+  cudaGraph_t g = nullptr;
+  CD_CUDA(cudaGraphCreate(&g, 0));
+  void* args[] = {(void*)&ds, (void*)&slot_of_row, (void*)&pool, (void*)&L, (void*)&ld, (void*)&n,
+                  (void*)&neg_tol, (void*)&cand, (void*)&piv, (void*)&pivd, (void*)&sc};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)finalize_dev_kernel;
+  p.gridDim = dim3(kStepGrid);
+  p.blockDim = dim3(kStepThreads);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  cudaGraphNode_t prev = nullptr;
+  for (int i = 0; i < nsteps; ++i) {
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphDestroy(g);
+      set_error(std::string("step graph: ") + cudaGetErrorString(e));
+      return CD_ECUDA;
+    }
+    prev = node;
+  }
+  cudaError_t e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *exec = nullptr;
+    set_error(std::string("step graph: ") + cudaGetErrorString(e));
+    return CD_ECUDA;
+  }
   return CD_OK;
 }
 

@@ -74,6 +74,10 @@ constexpr int kStepNotPsd = 4;      // pivot diagonal <= 0 or a residual below t
 int launch_finalize_dev(DevStep* ds, int32_t* slot_of_row, const double* pool, const double* L, int64_t ld,
                         int64_t n, double neg_tol, const uint8_t* cand, int64_t* piv, double* pivd,
                         StepScratch* sc, cudaStream_t st);
+// CUDA graph of nsteps launches of the step kernel above, in order
+int build_step_graph(cudaGraphExec_t* exec, int nsteps, DevStep* ds, int32_t* slot_of_row, const double* pool,
+                     const double* L, int64_t ld, int64_t n, double neg_tol, const uint8_t* cand, int64_t* piv,
+                     double* pivd, StepScratch* sc);
 // slot_of_row[rows[j]] = slots[j] for j < nb (after clearing all n entries to -1)
 int launch_slot_map(int32_t* slot_of_row, int64_t n, const int64_t* rows, const int32_t* slots, int nb,
                     cudaStream_t st);
