@@ -326,7 +326,8 @@ struct Work {  // scratch of one factorisation, freed (stream-ordered) at the en
       scratch_free(p, st);
 
     for (auto& e : ev) if (e) cudaEventDestroy(e);
-    for (cudaEvent_t e : {eri.fork, eri.join[0], eri.join[1]}) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {eri.fork, eri.join[0], eri.join[1], eri.counters_ready, eri.topup_done})
+      if (e) cudaEventDestroy(e);
     scratch_free(eri.counters, st);
     for (void* p : {(void*)ds_dev, (void*)slot_of_row, (void*)piv_dev, (void*)pivd_dev, (void*)sm_rows,
                     (void*)sm_slots})
@@ -479,6 +480,16 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   for (auto& x : w.eri.side) CD_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
   CD_TRY(scratch_alloc(&w.eri.counters, 3, st));
   CD_TRY(eri_resident_ctas(w.eri.resident, &w.eri.sms));
+  // the sliced update runs beside the ERI columns (CDERI_OVERLAP_UPDATE=0: in sequence)
+  const char* ov_env = getenv("CDERI_OVERLAP_UPDATE");
+  const bool overlap = slice && !(ov_env && ov_env[0] == '0');
+  if (overlap) {
+    int upd_regs = 0;
+    CD_TRY(update_cta_registers(&upd_regs));
+    CD_TRY(eri_coresident_ctas(upd_regs, w.eri.primary));
+    CD_CUDA(cudaEventCreateWithFlags(&w.eri.counters_ready, cudaEventDisableTiming));
+    CD_CUDA(cudaEventCreateWithFlags(&w.eri.topup_done, cudaEventDisableTiming));
+  }
   CD_CUDA(cudaEventCreateWithFlags(&w.eri.fork, cudaEventDisableTiming));
   for (auto& e : w.eri.join) CD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   // full pivoting runs the in-block steps on the device (CDERI_HOST_STEPS=1: one
@@ -676,10 +687,10 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
   int64_t nblocks = 0, ncols = 0;
   bool done = false;
   const bool dbg = getenv("CDERI_DEBUG") != nullptr;
-  // The sliced update runs on the main stream before the ERI columns: run
-  // beside them on a second stream (CDERI_OVERLAP_UPDATE=1) the two kernels
-  // compete for the same SMs and the block takes as long as in sequence.
-  const bool overlap = getenv("CDERI_OVERLAP_UPDATE") != nullptr;
+  // The sliced update (tensor cores, HBM) and the ERI columns (FP64 pipe) use
+  // different units: with `overlap` the update goes to the second stream and
+  // the ERI grids are sized to leave every SM room for one update CTA (see
+  // EriStreams); the ERI top-ups follow the update on that stream.
   while (!done) {
     if (reduce && K > 0) CD_TRY(compact_rows(false));
     if (forced ? (K >= nf) : !(res.dmax >= tau)) break;
@@ -774,6 +785,7 @@ static int factor_impl(cd_system* s, const cd_opts_t* o, cudaStream_t st, cd_fac
     std::vector<KetGroup> groups = group_kets(kets);
     if (!kets.empty()) {
       CD_CUDA(cudaMemcpyAsync(w.kets_dev, groups.data(), sizeof(KetGroup) * groups.size(), cudaMemcpyHostToDevice, st));
+      w.eri.topup = (overlap && gemm_issued) ? w.st2 : nullptr;
       CD_TRY(launch_eri_columns(bra_v, order_v, cls_v, s->all, w.kets_dev, (int)groups.size(), w.pool, ld,
                                 s->boys, st, w.eri_ops, getenv("CDERI_ERI_SERIAL") ? nullptr : &w.eri));
       eri_ints += (double)kets.size() * (double)n;

@@ -450,6 +450,31 @@ int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64
   }
   // persistent grids need one zeroed work counter per class
   if (es && es->counters) CD_CUDA(cudaMemsetAsync(es->counters, 0, 3 * sizeof(unsigned), st));
+  if (es && es->counters && es->topup) {
+    // beside the update: primary grids here, top-ups behind the update
+    CD_CUDA(cudaEventRecord(es->counters_ready, st));
+    CD_CUDA(cudaStreamWaitEvent(es->topup, es->counters_ready, 0));
+    for (int pass = 0; pass < 2; ++pass) {
+      cudaStream_t s = pass == 0 ? st : es->topup;
+      for (int cls = 2; cls >= 0; --cls) {
+        const int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
+        if (b1 <= b0) continue;
+        const int per_sm = pass == 0 ? es->primary[cls] : es->resident[cls] - es->primary[cls];
+        if (per_sm <= 0) continue;
+        const int64_t items = (b1 - b0 + 127) / 128 * (int64_t)nket;
+        dim3 grid((unsigned)std::min<int64_t>(items, (int64_t)per_sm * es->sms), 1);
+        unsigned* ctr = es->counters + cls;
+        if (cls == 0) eri_columns_kernel<0, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
+        else if (cls == 1) eri_columns_kernel<1, 0><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
+        else eri_columns_kernel<1, 1><<<grid, 128, 0, s>>>(bra, bra_order, b0, b1, ket, kets_dev, out, ld, boys, op_count, ctr, nket);
+        count_launch();
+      }
+    }
+    CD_CUDA(cudaGetLastError());
+    CD_CUDA(cudaEventRecord(es->topup_done, es->topup));
+    CD_CUDA(cudaStreamWaitEvent(st, es->topup_done, 0));
+    return CD_OK;
+  }
   // the most expensive class (pp bra pairs) is launched first, on the calling stream
   for (int cls = 2; cls >= 0; --cls) {
     int64_t b0 = class_off[cls], b1 = class_off[cls + 1];
@@ -486,6 +511,26 @@ int eri_resident_ctas(int* per_sm3, int* sms) {
   CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[0], eri_columns_kernel<0, 0>, 128, 0));
   CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[1], eri_columns_kernel<1, 0>, 128, 0));
   CD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm3[2], eri_columns_kernel<1, 1>, 128, 0));
+  return CD_OK;
+}
+
+int eri_coresident_ctas(int regs, int* per_sm3) {
+  int dev = 0;
+  CD_CUDA(cudaGetDevice(&dev));
+  int regs_sm = 0;
+  CD_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+  const void* k[3] = {(const void*)eri_columns_kernel<0, 0>, (const void*)eri_columns_kernel<1, 0>,
+                      (const void*)eri_columns_kernel<1, 1>};
+  for (int c = 0; c < 3; ++c) {
+    // the SM's shared memory goes to the update's CTA: same carveout for both kernels
+    CD_CUDA(cudaFuncSetAttribute(k[c], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
+    cudaFuncAttributes a;
+    CD_CUDA(cudaFuncGetAttributes(&a, k[c]));
+    const int per_warp = (a.numRegs * 32 + 255) / 256 * 256;   // registers are allocated per warp, 256 at a time
+    const int per_cta = per_warp * (128 / 32);
+    per_sm3[c] = std::max(0, (regs_sm - regs) / per_cta);
+  }
   return CD_OK;
 }
 

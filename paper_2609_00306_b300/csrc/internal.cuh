@@ -193,8 +193,21 @@ struct EriStreams {
   unsigned* counters = nullptr;
   int resident[3] = {0, 0, 0};
   int sms = 0;
+  // Co-residence with the tensor-core column update (optional): when `topup` is
+  // set, the update has been queued on it.  Each class then runs a primary
+  // persistent grid on the calling stream that leaves room for one update CTA
+  // on every SM (primary[c] CTAs per SM), and top-up grids queued on `topup`
+  // behind the update take the rest of the same work counters once the update
+  // is done.  The calling stream waits for the top-ups.
+  cudaStream_t topup = nullptr;
+  int primary[3] = {0, 0, 0};
+  cudaEvent_t counters_ready = nullptr, topup_done = nullptr;
 };
 int eri_resident_ctas(int* per_sm3, int* sms);
+// CTAs per SM of each class kernel that fit beside one CTA using `regs` registers
+// and all of the shared memory, with the kernels' shared-memory carveout set to
+// the maximum so that both can be resident together
+int eri_coresident_ctas(int regs, int* per_sm3);
 int launch_eri_columns(const PairSet& bra, const int64_t* bra_order, const int64_t* class_off,
                        const PairSet& ket, const KetGroup* groups_dev, int ngroups,
                        double* out, int64_t ld, const double* boys, cudaStream_t st,

@@ -468,6 +468,16 @@ extern "C" int cd_slice_matmul(const double* X, int64_t ldx, int64_t m, const do
   return fin(CD_OK);
 }
 
+namespace cd {
+// registers of one CTA of the column-update GEMM (allocated per warp, 256 at a time)
+int update_cta_registers(int* regs) {
+  cudaFuncAttributes a;
+  CD_CUDA(cudaFuncGetAttributes(&a, ozaki_kernel<7, 7, 8, 32, 3>));
+  *regs = (kThreads / 32) * ((a.numRegs * 32 + 255) / 256 * 256);
+  return CD_OK;
+}
+}  // namespace cd
+
 extern "C" int cd_set_wait_limit(double seconds, double* previous) {
   using namespace cd;
   if (previous) *previous = (double)g_wait_ns.load() * 1e-9;

@@ -92,6 +92,8 @@ int launch_slice_rows_f64(const double* src, int64_t src_rs, int64_t src_ks, int
                           cudaStream_t st, bool chunked = false);
 
 int launch_row_exp_sqrt(const double* d, int64_t n, int32_t* e, cudaStream_t st);
+// registers one CTA of the column-update GEMM occupies on its SM
+int update_cta_registers(int* regs);
 // Ls in k-chunks of 32 ([K/32][S][n][32], the decomposition's slice store);
 // Bs flat [S][nb][bpitch]
 int launch_gather_slices(const void* Ls, int64_t n, const int64_t* rows, const int64_t* valid, int nb,
