@@ -59,6 +59,7 @@ def _args():
     ap.add_argument("--jk-alone-modes", default="all",
                     help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=48)
+    ap.add_argument("--block", type=int, default=0, help="speculative column block b (0 = library default)")
     ap.add_argument("--no-fp64-update", action="store_true",
                     help="skip the factorisation with the FP64 DFMA column update (its roofline entry)")
     return ap.parse_args()
@@ -229,7 +230,7 @@ def run_ours(args, rank, world):
 
     def step():
         f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, vec_precision=vec_prec, algorithm=algs[args.algorithm],
-                             span=args.span)
+                             span=args.span, block=args.block)
         f.jk_device(C_dev, J_dev, K_dev, mode=jk_mode)
         return f
 

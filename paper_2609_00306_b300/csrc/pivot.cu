@@ -107,17 +107,19 @@ __global__ void __launch_bounds__(kStepThreads) finalize_kernel(
   int bad = 0;
   const double* Lb = L + Kb * ld;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = col[r];
+    // two independent FMA chains (even / odd in-block vectors) keep the FP64 pipe fed
+    double acc = col[r], acc2 = 0.0;
     int k = 0;
     for (; k + 4 <= nk; k += 4) {
       double a0 = Lb[(k + 0) * ld + r], a1 = Lb[(k + 1) * ld + r];
       double a2 = Lb[(k + 2) * ld + r], a3 = Lb[(k + 3) * ld + r];
       acc = fma(-a0, g[k + 0], acc);
-      acc = fma(-a1, g[k + 1], acc);
+      acc2 = fma(-a1, g[k + 1], acc2);
       acc = fma(-a2, g[k + 2], acc);
-      acc = fma(-a3, g[k + 3], acc);
+      acc2 = fma(-a3, g[k + 3], acc2);
     }
     for (; k < nk; ++k) acc = fma(-Lb[k * ld + r], g[k], acc);
+    acc += acc2;
     const double v = acc * inv;
     Lout[r] = v;
     const double d = fma(-v, v, Din[r]);
@@ -186,17 +188,19 @@ __global__ void __launch_bounds__(kStepThreads) finalize_dev_kernel(
   int bad = 0;
   const double* Lb = L + Kb * ld;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    double acc = col[r];
+    // two independent FMA chains (even / odd in-block vectors) keep the FP64 pipe fed
+    double acc = col[r], acc2 = 0.0;
     int k = 0;
     for (; k + 4 <= nk; k += 4) {
       double a0 = Lb[(k + 0) * ld + r], a1 = Lb[(k + 1) * ld + r];
       double a2 = Lb[(k + 2) * ld + r], a3 = Lb[(k + 3) * ld + r];
       acc = fma(-a0, g[k + 0], acc);
-      acc = fma(-a1, g[k + 1], acc);
+      acc2 = fma(-a1, g[k + 1], acc2);
       acc = fma(-a2, g[k + 2], acc);
-      acc = fma(-a3, g[k + 3], acc);
+      acc2 = fma(-a3, g[k + 3], acc2);
     }
     for (; k < nk; ++k) acc = fma(-Lb[k * ld + r], g[k], acc);
+    acc += acc2;
     const double vv = acc * inv;
     Lout[r] = vv;
     const double d = fma(-vv, vv, Din[r]);
