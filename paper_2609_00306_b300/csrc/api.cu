@@ -87,8 +87,13 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
     s2.insert(s2.end(), cs2[c].begin(), cs2[c].end());
   }
   s->all_class_off[3] = (int64_t)s1.size();
+  const bool dbg = getenv("CDERI_DEBUG") != nullptr;
+  auto phase = [&](const char* what) {
+    if (dbg) fprintf(stderr, "[cderi] system set-up: %-28s %8.1f ms\n", what, now_ms() - t0);
+  };
   PairSetHost hall;
   build_pairs(hb, s1, s2, &hall);
+  phase("all shell pairs built");
   rc = upload_pairs(hall, &s->all, st);
   if (rc != CD_OK) { system_release(s); return rc; }
   // diagonal of every packed pair (kernel a, diagonal mode)
@@ -102,6 +107,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   scratch_free(dall, st);
   if (rc == CD_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
   if (rc != CD_OK) { if (rc == CD_ECUDA) set_error("diagonal pass failed"); system_release(s); return rc; }
+  phase("diagonal on the device");
   for (int64_t p = 0; p < npk; ++p)
     if (!std::isfinite(hd[p])) { set_error("non-finite ERI diagonal"); system_release(s); return CD_EINVAL; }
   double dmax = 0.0;
@@ -138,6 +144,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
   s->n_rows_pad = std::max<int64_t>(32, (n + 31) / 32 * 32);
   std::vector<int32_t> p2r(npk, -1);
   for (int64_t r = 0; r < n; ++r) p2r[rows[r]] = (int32_t)r;
+  phase("screened rows");
   PairSetHost hbra;
   build_pairs(hb, ks1, ks2, &hbra, kPrimPrune);
   {
@@ -174,6 +181,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
     ks1.swap(p1); ks2.swap(p2); kall.swap(pa);
     build_pairs(hb, ks1, ks2, &hbra, kPrimPrune);
   }
+  phase("bra pairs ordered");
   for (auto& r : hbra.row)
     if (r >= 0) r = p2r[r];
   s->bra_to_all = kall;
@@ -219,6 +227,7 @@ static int system_create_impl(const cd_basis_t* basis, double schwarz, cudaStrea
     CD_CUDA(cudaMemcpyAsync(s->row_nu_dev, rnu.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
   }
   CD_CUDA(cudaStreamSynchronize(st));
+  phase("row tables uploaded");
   s->ms_setup = now_ms() - t0;
   *out = s;
   return CD_OK;

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <thread>
 #include "internal.cuh"
 
 namespace cd {
@@ -72,6 +73,25 @@ int validate_and_normalise(const cd_basis_t* b, HostBasis* hb) {
 
 // Records for the shell pairs (s1[k], s2[k]), s1 >= s2, in the given order.
 // row[] is filled with the packed pair index (callers remap it).
+// run body(k) for k in [0, n) on the host's cores, in contiguous chunks
+template <class F>
+static void parallel_for(size_t n, F&& body) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t nt = std::min<size_t>(hw, std::max<size_t>(1, n / 4096));
+  if (nt <= 1) {
+    for (size_t k = 0; k < n; ++k) body(k);
+    return;
+  }
+  std::vector<std::thread> th;
+  const size_t chunk = (n + nt - 1) / nt;
+  for (size_t t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      const size_t k0 = t * chunk, k1 = std::min(n, k0 + chunk);
+      for (size_t k = k0; k < k1; ++k) body(k);
+    });
+  for (auto& x : th) x.join();
+}
+
 void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std::vector<int32_t>& s2,
                  PairSetHost* out, double prune) {
   const double c0 = sqrt(2.0) * pow(kPi, 1.25);
@@ -81,53 +101,77 @@ void build_pairs(const HostBasis& hb, const std::vector<int32_t>& s1, const std:
   out->row.assign(9 * n, -1);
   out->s1 = s1; out->s2 = s2;
   out->swapped.resize(n);
-  size_t npp = 0;
-  for (size_t k = 0; k < n; ++k) npp += (size_t)hb.nprim[s1[k]] * hb.nprim[s2[k]];
-  out->zeta.resize(npp); out->P.resize(3 * npp); out->PA.resize(3 * npp); out->Kp.resize(npp); out->o2z.resize(npp);
+  // primitive-pair prefactor of primitives (i on A, j on B) of shell pair k
+  auto kp_of = [&](int A, int B, int i, int j, double AB2) {
+    const double a = hb.exps[hb.pofs[A] + i], b = hb.exps[hb.pofs[B] + j];
+    const double z = a + b;
+    return c0 * hb.dcoef[hb.pofs[A] + i] * hb.dcoef[hb.pofs[B] + j] * exp(-a * b / z * AB2) / z;
+  };
+  auto orient = [&](size_t k, int* A, int* B, double* AB2) {
+    const int S1 = s1[k], S2 = s2[k];
+    const int sw = hb.l[S1] < hb.l[S2];
+    *A = sw ? S2 : S1;
+    *B = sw ? S1 : S2;
+    double d = 0.0;
+    for (int x = 0; x < 3; ++x) d += (hb.cen[3 * *A + x] - hb.cen[3 * *B + x]) * (hb.cen[3 * *A + x] - hb.cen[3 * *B + x]);
+    *AB2 = d;
+    return sw;
+  };
+  // pass 1: surviving primitive pairs per shell pair, then their offsets
+  std::vector<int32_t> cnt(n, 0);
+  parallel_for(n, [&](size_t k) {
+    int A, B;
+    double AB2;
+    orient(k, &A, &B, &AB2);
+    int c = 0;
+    for (int i = 0; i < hb.nprim[A]; ++i)
+      for (int j = 0; j < hb.nprim[B]; ++j)
+        if (!(prune > 0.0 && fabs(kp_of(A, B, i, j, AB2)) < prune)) ++c;
+    cnt[k] = c;
+  });
   size_t q = 0;
-  for (size_t k = 0; k < n; ++k) {
-    int S1 = s1[k], S2 = s2[k];
-    int sw = hb.l[S1] < hb.l[S2];
-    int A = sw ? S2 : S1, B = sw ? S1 : S2;
+  for (size_t k = 0; k < n; ++k) { out->pp_off[k] = (int32_t)q; q += cnt[k]; }
+  out->pp_off[n] = (int32_t)q;
+  out->zeta.resize(q); out->P.resize(3 * q); out->PA.resize(3 * q); out->Kp.resize(q); out->o2z.resize(q);
+  // pass 2: the records
+  parallel_for(n, [&](size_t k) {
+    int A, B;
+    double AB2;
+    const int sw = orient(k, &A, &B, &AB2);
+    const int S1 = s1[k], S2 = s2[k];
     out->swapped[k] = (int8_t)sw;
     out->la[k] = (int8_t)hb.l[A];
     out->lb[k] = (int8_t)hb.l[B];
     const double* cA = &hb.cen[3 * A];
     const double* cB = &hb.cen[3 * B];
-    double AB2 = 0.0;
-    for (int x = 0; x < 3; ++x) {
-      out->AB[3 * k + x] = cA[x] - cB[x];
-      AB2 += (cA[x] - cB[x]) * (cA[x] - cB[x]);
-    }
-    out->pp_off[k] = (int32_t)q;
+    for (int x = 0; x < 3; ++x) out->AB[3 * k + x] = cA[x] - cB[x];
+    size_t w = (size_t)out->pp_off[k];
     for (int i = 0; i < hb.nprim[A]; ++i)
       for (int j = 0; j < hb.nprim[B]; ++j) {
-        double a = hb.exps[hb.pofs[A] + i], b = hb.exps[hb.pofs[B] + j];
-        double z = a + b;
-        const double kp = c0 * hb.dcoef[hb.pofs[A] + i] * hb.dcoef[hb.pofs[B] + j] * exp(-a * b / z * AB2) / z;
+        const double kp = kp_of(A, B, i, j, AB2);
         if (prune > 0.0 && fabs(kp) < prune) continue;
-        out->zeta[q] = z;
+        const double a = hb.exps[hb.pofs[A] + i], b = hb.exps[hb.pofs[B] + j];
+        const double z = a + b;
+        out->zeta[w] = z;
         for (int x = 0; x < 3; ++x) {
-          double P = (a * cA[x] + b * cB[x]) / z;
-          out->P[3 * q + x] = P;
-          out->PA[3 * q + x] = P - cA[x];
+          const double P = (a * cA[x] + b * cB[x]) / z;
+          out->P[3 * w + x] = P;
+          out->PA[3 * w + x] = P - cA[x];
         }
-        out->Kp[q] = kp;
-        out->o2z[q] = 0.5 / z;
-        ++q;
+        out->Kp[w] = kp;
+        out->o2z[w] = 0.5 / z;
+        ++w;
       }
     // components: i on A, j on B
-    int nA = 2 * hb.l[A] + 1, nB = 2 * hb.l[B] + 1;
+    const int nA = 2 * hb.l[A] + 1, nB = 2 * hb.l[B] + 1;
     for (int i = 0; i < nA; ++i)
       for (int j = 0; j < nB; ++j) {
-        int fA = hb.bf0[A] + i, fB = hb.bf0[B] + j;
+        const int fA = hb.bf0[A] + i, fB = hb.bf0[B] + j;
         if (S1 == S2 && fA < fB) continue;  // same shell: keep mu >= nu only
-        int64_t mu = std::max(fA, fB), nu = std::min(fA, fB);
+        const int64_t mu = std::max(fA, fB), nu = std::min(fA, fB);
         out->row[9 * k + 3 * i + j] = (int32_t)(mu * (mu + 1) / 2 + nu);
       }
-  }
-  out->pp_off[n] = (int32_t)q;
-  out->zeta.resize(q); out->P.resize(3 * q); out->PA.resize(3 * q); out->Kp.resize(q); out->o2z.resize(q);
+  });
 }
 
 template <class T>
