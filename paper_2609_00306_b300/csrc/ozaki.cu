@@ -333,7 +333,10 @@ int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpi
   const int symi = sym ? 1 : 0;
   if (kdim <= 0 || a_rows <= 0 || b_rows <= 0) return CD_OK;
   CUtensorMap ta, tb;
-  const int bn = (p.SA >= 5) ? 32 : 64;   // accumulator width: 2 x groups x bn must fit 512 TMEM columns
+  // B tile rows: the stacked B slices (SB x bn <= 256) and two accumulator sets
+  // (2 x groups x bn <= 512 TMEM columns) must fit; the widest tile that does
+  // reads each A slice from shared memory for the most products
+  const int bn = p.SA >= 7 ? 32 : (p.SA == 5 ? 48 : 64);
   if (a_chunked) CD_TRY(make_map_chunked(&ta, As, p.SA, a_rows, kdim, BM));
   else CD_TRY(make_map(&ta, As, p.SA, a_rows, kdim, a_kpitch, BM));
   const int a4d = a_chunked ? 1 : 0;
@@ -344,7 +347,7 @@ int ozaki_gemm(const OzakiPlan& p, const void* As, int64_t a_rows, int64_t a_kpi
   int kc = (int)(16777216.0 / (std::max(1, maxg) * kSliceProdMax));
   int kcb = std::max(1, kc / BK);
   if (p.SA == 3 && p.SB == 3 && p.KEEP == 4) return run<3, 3, 4, 64, 5>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
-  if (p.SA == 5 && p.SB == 5 && p.KEEP == 6) return run<5, 5, 6, 32, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
+  if (p.SA == 5 && p.SB == 5 && p.KEEP == 6) return run<5, 5, 6, 48, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
   if (p.SA == 4 && p.SB == 4 && p.KEEP == 5) return run<4, 4, 5, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
   if (p.SA == 7 && p.SB == 7 && p.KEEP == 8) return run<7, 7, 8, 32, 3>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
   if (p.SA == 1 && p.SB == 1 && p.KEEP == 2) return run<1, 1, 2, 64, 4>(ta, tb, a_rows, b_rows, nkb, ksplit, kcb, p.F, D, ldd, err_dev, symi, st, a4d);
