@@ -275,6 +275,35 @@ int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, 
                  const int32_t* n_occ, double* const* J, double* const* K, int32_t jk_mode, int32_t workers,
                  void* stream);
 
+/* The same computation (no paper counterpart either) in FP64 throughout, with
+ * the decompositions and J/K builds of all systems in ONE persistent kernel
+ * launch recorded in a CUDA graph.  Per system: the fully pivoted
+ * decomposition of Sec. 2 (blocked, b = opts[i].block <= 64, 0 = 64; ERI
+ * columns, DFMA column update, pivot steps on the device), then J and K of
+ * Sec. 4.1 with D = 2 C_occ C_occ^T.  Set-up (screening, diagonal) runs first
+ * on host workers.  Work items (a block's ERI columns, update tiles, the rows
+ * of a pivot step, J/K tiles) are claimed by the CTAs from per-system job
+ * words; the CTA that completes a job's last item publishes the next job.
+ * Inputs: bases, opts (tau, schwarz, block, max_vectors: vector capacity per
+ * system, 0 = 8 N; opts[0].mem_budget_gb caps the whole batch, 0 = 90% of
+ * free memory; CD_ALG_FULL only, no forced pivots, mask or shift), C_occ[i]
+ * host [N_i][n_occ[i]] row-major.  Outputs (host, caller-owned): J[i], K[i]
+ * [N_i][N_i]; M_out[i] the vector counts (may be NULL); stats (may be NULL,
+ * 23 entries): [0] set-up ms, [1] upload ms, [2] device ms of the launch, [3]
+ * host ms of the launch and read-back, [4] CTAs, [5] bytes reserved, [6 + k]
+ * CTA-seconds spent in items of kind k (1 select, 2 gather, 3 update, 4 step,
+ * 5 density, 6 v = L d, 7 J_p = L^T v, 8 J unpack, 10 ERI columns, 13 B = L C,
+ * 14 partial K tiles, 15 K sums), [22] CTA-seconds spent looking for work.  All device memory is
+ * allocated for the call and freed before it returns; `stream` is waited for
+ * before the work starts.  Errors: CD_EINVAL (arguments, names the system),
+ * CD_ENOMEM (batch over the budget, or a system needing more than its
+ * max_vectors), CD_ENOTPSD, CD_ETIMEOUT (a CTA waited longer than the wait
+ * limit of cd_set_wait_limit with no item completed anywhere; the launch
+ * then stops cleanly), CD_ECUDA. */
+int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts,
+                        const double* const* C_occ, const int32_t* n_occ, double* const* J, double* const* K,
+                        int64_t* M_out, double* stats, void* stream);
+
 /* ---- building block: exact-slice tensor-core product ------------------------ */
 /* out[i][j] = sum_k X[i][k] Y[j][k] for FP64 device matrices X [m][k] (leading
  * dimension ldx) and Y [n][k] (ldy); out FP64 device [m][n] (ldo).  Each row is

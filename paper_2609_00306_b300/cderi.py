@@ -30,7 +30,7 @@ _ERRNAMES = {CD_EINVAL: "CD_EINVAL", CD_ENOMEM: "CD_ENOMEM", CD_ENOTPSD: "CD_ENO
 # every symbol declared in include/cderi.h
 EXPORTS = ["cd_system_create", "cd_system_free", "cd_system_info", "cd_system_rows", "cd_eri_columns",
            "cd_eri_factor", "cd_eri_factor_sys", "cd_factor_free", "cd_factor_info", "cd_factor_pivots",
-           "cd_factor_vectors", "cd_factor_pivot_diag", "cd_factor_memory", "cd_factor_eri_work", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_slice_matmul", "cd_set_wait_limit", "cd_last_error", "cd_version"]
+           "cd_factor_vectors", "cd_factor_pivot_diag", "cd_factor_memory", "cd_factor_eri_work", "cd_factor_gather", "cd_factor_stats", "cd_kernel_launches", "cd_jk", "cd_mo_vectors", "cd_batch_run", "cd_batch_persistent", "cd_slice_matmul", "cd_set_wait_limit", "cd_last_error", "cd_version"]
 
 
 class CDError(RuntimeError):
@@ -87,6 +87,7 @@ def load(path: Optional[str] = None):
         "cd_mo_vectors": (ctypes.c_int, [P, P, I32, I64, I64, I32, P, I32, P]),
         "cd_kernel_launches": (ctypes.c_longlong, []),
         "cd_batch_run": (ctypes.c_int, [I32, P, P, P, P, P, P, I32, I32, P]),
+        "cd_batch_persistent": (ctypes.c_int, [I32, P, P, P, P, P, P, P, P, P]),
         "cd_slice_matmul": (ctypes.c_int, [P, I64, I64, P, I64, I64, I64, I32, P, I64, P]),
         "cd_last_error": (ctypes.c_char_p, []),
         "cd_version": (ctypes.c_char_p, []),
@@ -380,6 +381,42 @@ def batch_run(systems, jk_mode: int = CD_JK_FP64, workers: int = 0, blocks=None,
                                PArr(*[j.ctypes.data for j in Js]), PArr(*[k.ctypes.data for k in Ks]),
                                int(jk_mode), int(workers), _stream(stream)))
     return Js, Ks
+
+
+def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: float = 0.0, stream=None):
+    """Decompose and contract many independent systems in FP64 with one
+    persistent kernel launch recorded in a CUDA graph (C ABI cd_batch_persistent).
+
+    systems: sequence of synth.System-like objects (basis, C_occ, tau, schwarz).
+    blocks: per-system block size b <= 64 (e.g. from the autotuner), or None (64).
+    max_vectors: per-system vector capacity, or None (8 N).
+    Returns lists J, K of numpy arrays, the vector counts M and a dict of timings.
+    """
+    n = len(systems)
+    bargs = [_BasisArgs(s.basis) for s in systems]
+    bases = (cd_basis_t * n)(*[b.s for b in bargs])
+    opts = (cd_opts_t * n)(*[make_opts(s.tau, s.schwarz, CD_FP64, int(blocks[i]) if blocks is not None else 0,
+                                       int(max_vectors[i]) if max_vectors is not None else 0,
+                                       float(mem_budget_gb) if i == 0 else 0.0)[0]
+                             for i, s in enumerate(systems)])
+    Cs = [np.ascontiguousarray(s.C_occ, dtype=np.float64) for s in systems]
+    Js = [np.zeros((c.shape[0], c.shape[0])) for c in Cs]
+    Ks = [np.zeros((c.shape[0], c.shape[0])) for c in Cs]
+    PArr = ctypes.c_void_p * n
+    occ = np.array([c.shape[1] for c in Cs], dtype=np.int32)
+    M = np.zeros(n, dtype=np.int64)
+    stats = np.zeros(23)
+    _check(load().cd_batch_persistent(n, ctypes.byref(bases), ctypes.byref(opts),
+                                      PArr(*[c.ctypes.data for c in Cs]), _p(occ),
+                                      PArr(*[j.ctypes.data for j in Js]), PArr(*[k.ctypes.data for k in Ks]),
+                                      _p(M), _p(stats), _stream(stream)))
+    info = {"setup_ms": float(stats[0]), "upload_ms": float(stats[1]), "launch_device_ms": float(stats[2]),
+            "launch_host_ms": float(stats[3]), "ctas": int(stats[4]), "bytes": float(stats[5]),
+            "cta_s": {name: float(stats[6 + k]) for k, name in
+                      [(1, "select"), (2, "gather"), (3, "update"), (4, "step"), (5, "density"), (6, "v"),
+                       (7, "jp"), (8, "j_unpack"), (10, "eri"), (13, "b"), (14, "k_tiles"), (15, "k_sum")]},
+            "idle_cta_s": float(stats[22])}
+    return Js, Ks, [int(m) for m in M], info
 
 
 def set_wait_limit(seconds: float) -> float:

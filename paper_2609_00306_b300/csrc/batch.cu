@@ -1,0 +1,1462 @@
+// batch.cu -- many independent systems decomposed and contracted in one
+// persistent kernel launch, recorded in a CUDA graph.
+//
+// Every system runs the fully pivoted decomposition of Sec. 2 in the blocked
+// form of the single-system path (b candidate columns computed and brought up
+// to date together, then pivot steps while the global argmax of the residual
+// diagonal stays among them) and then the J/K build of Sec. 4.1, all in FP64.
+// A system's work is a sequence of jobs, each a set of independent items:
+//
+//   SELECT  1 item: the b largest residual diagonals >= tau (ties: lowest row)
+//           become the block's candidates (radix select over the IEEE-754 bit
+//           patterns); pool slots of columns still wanted are kept, the new
+//           rows get ket groups
+//   COLS    the pivot rows of the existing vectors gathered for the update
+//           (256 vectors per item), and the ERI columns of the new candidates
+//           (kernel a: 128 bra shell pairs x one ket group per item)
+//   UPDATE  col -= L Lp^T over the vectors not yet applied, Eq. (subtr): 128
+//           rows x <= 64 columns per item, register-tiled DFMA
+//   STEP    one pivot step, Eq. (subtr) in-block terms and Eq. (diag), over
+//           1024 rows per item, each item leaving its partial argmax
+//   JK1     d = packed density (1024 rows per item); B^P = L^P C (one vector
+//           per item, through a row list per basis function)
+//   JK2     v = L d (4 vectors per item); partial K tiles sum_P B^P B^P^T
+//           (64 x 64 tile x 128 vectors per item)
+//   JK3     J_p = L^T v (1024 rows per item); K tiles = 2 x the sum of partials
+//   JK4     J unpacked to N x N
+//
+// Jobs and stage flags.  A system holds one job at a time in a 64-bit word
+// (generation | item count | next item).  A CTA claims an item with one
+// atomic add on the word.  The CTA that completes a job's last item (counted
+// per system) runs the job's finish: it writes the next job's parameters and
+// then publishes the next word; the STEP finish reduces the step's argmax and
+// decides between another step, a new block and the J/K build.  Items never
+// wait for each other, so the launch needs no co-residency; the one wait is a
+// CTA's wait for work, which gives up and makes the call return CD_ETIMEOUT
+// once no item anywhere has completed for the wait limit (cd_set_wait_limit).
+// CTAs scan the systems largest first, so the largest systems take the GPU
+// first and the small ones fill the gaps.
+//
+// Memory is reserved per system before the launch (vectors for max_vectors,
+// default 8 N, plus the K intermediates); a system that needs more vectors
+// stops with CD_ENOMEM.  Loads of data that change during the launch (residual
+// diagonals, columns, gathered rows, job state) bypass L1 (ld.global.cg or
+// volatile): another SM may have rewritten them since this SM last cached them.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+#include "internal.cuh"
+#include "eri_dev.cuh"
+
+namespace cd {
+unsigned long long device_wait_limit_ns();  // ozaki.cu (cd_set_wait_limit)
+
+namespace {
+
+constexpr int kBT = 128;          // threads per CTA
+constexpr int kBMaxB = 64;        // largest block of the batch kernel
+constexpr int kStepRows = 1024;   // rows per STEP / DENS / JP / JUNPACK item
+constexpr int kRowTile = 128;     // rows per UPDATE item
+constexpr int kGatherQ = 256;     // vectors per gather item
+constexpr int kJvVec = 4;         // vectors per JV item
+constexpr int kKtSplit = 128;     // vectors per partial K tile
+constexpr int kKt = 64;           // K tile edge
+constexpr int kTieCap = 1024;     // tie-bin entries ranked directly by SELECT
+constexpr int kSmemBytes = 32768;
+
+enum JobType : int { kJobNone = 0, kJobSelect, kJobCols, kJobUpdate, kJobStep, kJobJk1, kJobJk2, kJobJk3, kJobJk4,
+                     kJobConverged = 100 /* pseudo job: the decomposition has converged */ };
+
+__host__ __device__ constexpr unsigned long long job_word(unsigned gen, unsigned count, unsigned next) {
+  return ((unsigned long long)(gen & 0xffffu) << 48) | ((unsigned long long)(count & 0xffffffu) << 24) |
+         (unsigned long long)(next & 0xffffffu);
+}
+__host__ __device__ constexpr unsigned job_gen(unsigned long long w) { return (unsigned)(w >> 48); }
+__host__ __device__ constexpr unsigned job_count(unsigned long long w) { return (unsigned)((w >> 24) & 0xffffffu); }
+__host__ __device__ constexpr unsigned job_next(unsigned long long w) { return (unsigned)(w & 0xffffffu); }
+constexpr unsigned kMaxJobItems = 1u << 23;   // far below the 24-bit fields, so over-claims cannot carry
+
+// Mutable per-system state (device).  Written only by a job's finish (one CTA,
+// while no item of the system is outstanding) and by SELECT (the only item of
+// its job); read by the items of the next job after they claim it.
+struct SysState {
+  unsigned long long word;   // current job
+  unsigned done;             // items of the current job completed
+  int type;                  // JobType of the current job
+  int status;                // CD_OK or the system's error code
+  int bad;                   // a residual diagonal fell below neg_tol in this step
+  int cur;                   // D[cur] is the current residual diagonal
+  int pslot;                 // pool slot of the current pivot
+  int converged;             // SELECT found max D < tau
+  int ngroups;               // ERI ket groups of the block
+  int64_t K, Kb;             // vectors done; first vector of the current block
+  int64_t prow;              // pivot row of the current step
+  double dp;                 // its residual diagonal
+  double dmax;               // max of D[cur] and its row (ties: lowest row)
+  int64_t idx;
+  int nitems[2];             // items of the two parts of a job
+  int gitems[2];             // gather items of the two update groups
+  int nb[2];                 // update groups (new slots, kept slots): columns
+  int64_t k0[2];             // and the first vector each still needs
+  int32_t uslot[2][kBMaxB];
+  int64_t urow[2][kBMaxB];
+  int64_t slot_row[kBMaxB];  // pool slot -> row (-1 = free)
+  int64_t slot_valid[kBMaxB];// vectors [0, slot_valid) are applied to the slot's column
+};
+
+// Immutable per-system descriptor (device; copied to shared memory per item).
+struct __align__(16) SysDesc {
+  int64_t n, ld, Mcap;
+  int N, O, Op, b;
+  double tau, neg_tol;
+  PairSet bra, ket;                 // screened bra shell pairs (by class), all shell pairs
+  int64_t cls[4], all_cls[4];
+  int ntile[3], nsplit_cap;
+  const int32_t* row_allsp;         // [n] shell pair (in ket) of each row
+  const int8_t* row_kc;             // [n] canonical components of each row
+  const int8_t* row_kd;
+  const int32_t* row_mu;            // [n] mu >= nu of each row
+  const int32_t* row_nu;
+  const int32_t* csr_off;           // [N+1] row list per basis function mu:
+  const int32_t* csr_nu;            //   partner nu and row r of every screened pair (mu nu)
+  const int32_t* csr_row;
+  const double* C;                  // [N][O] occupied coefficients
+  double* D0;                       // [ld] residual diagonals (double buffered)
+  double* D1;
+  double* pool;                     // [b][ld] candidate columns
+  double* L;                        // [Mcap][ld] vectors
+  int64_t* piv;                     // [Mcap] pivot rows
+  double* pivd;                     // [Mcap] their residual diagonals
+  double* Bg0;                      // [Mcap][b] gathered pivot rows (new slots)
+  double* Bg1;                      // [b][b] (kept slots)
+  KetGroup* groups;                 // [b]
+  double* part_val;                 // [ceil(n / kStepRows)] partial argmax
+  int64_t* part_idx;
+  double* dpk;                      // [ld] packed density
+  double* v;                        // [Mcap] v_P
+  double* Jp;                       // [ld] packed J
+  double* B;                        // [Mcap][N][Op] half-transformed vectors
+  double* Kpart;                    // [nsplit_cap][N][N] partial K tiles
+  double* J;                        // [N][N]
+  double* Kx;                       // [N][N]
+  SysState* st;
+};
+
+constexpr int kJobKinds = 16;
+struct BatchCtl {
+  unsigned done_sys;            // systems finished (converged or failed)
+  int abort;                    // stop claiming work
+  int timed_out;                // a CTA's wait for work ran out
+  int pad;
+  unsigned long long progress;  // items completed, all systems
+  unsigned long long kind_ns[kJobKinds];     // CTA time per item kind (incl. its job finish)
+  unsigned long long kind_items[kJobKinds];  // items per kind
+  unsigned long long idle_ns;                // CTA time spent looking for work
+};
+
+// ------------------------------------------------------------ helpers ----
+__device__ __forceinline__ long long globaltimer_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+template <class T>
+__device__ __forceinline__ T vload(const T* p) { return *(const volatile T*)p; }
+
+__device__ __forceinline__ bool better(double v1, int64_t i1, double v2, int64_t i2) {
+  return v1 > v2 || (v1 == v2 && i1 < i2);
+}
+__device__ __forceinline__ void warp_argmax(double& v, int64_t& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int64_t i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (better(v2, i2, v, i)) { v = v2; i = i2; }
+  }
+}
+// CTA argmax; result valid in every thread
+__device__ void cta_argmax(double& v, int64_t& i, double* sv, int64_t* si) {
+  warp_argmax(v, i);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) { sv[w] = v; si[w] = i; }
+  __syncthreads();
+  v = sv[0]; i = si[0];
+  for (int k = 1; k < kBT / 32; ++k)
+    if (better(sv[k], si[k], v, i)) { v = sv[k]; i = si[k]; }
+  __syncthreads();
+}
+__device__ double cta_sum(double x, double* sv) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sv[w] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int k = 0; k < kBT / 32; ++k) s += sv[k];
+  __syncthreads();
+  return s;
+}
+__device__ int cta_sum_int(int x, int* sv) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sv[w] = x;
+  __syncthreads();
+  int s = 0;
+  for (int k = 0; k < kBT / 32; ++k) s += sv[k];
+  __syncthreads();
+  return s;
+}
+__device__ __forceinline__ const double* dcur(const SysDesc& d, int cur) { return cur ? d.D1 : d.D0; }
+__device__ __forceinline__ double* dnext(const SysDesc& d, int cur) { return cur ? d.D0 : d.D1; }
+__device__ __forceinline__ unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// reduction scratch shared by the helpers
+struct Red {
+  double v[kBT / 32];
+  int64_t i[kBT / 32];
+  int n[kBT / 32];
+};
+
+// --------------------------------------------------------------- SELECT ----
+// Candidates of a new block: the b rows with the largest residual diagonals
+// >= tau, ordered by (D descending, row ascending); the exact top b of that
+// order.  Positive doubles compare like their bit patterns, so a radix select
+// over 12-bit digits of the bit pattern finds the bin of the b-th value; the
+// rows of that bin (at most kTieCap, or all of one value) are ranked directly.
+__device__ void select_item(const SysDesc& d, unsigned char* smem, Red* red, int64_t* s_cand, int* s_int) {
+  SysState* st = d.st;
+  const int tid = threadIdx.x;
+  const int64_t n = d.n;
+  const int cur = vload(&st->cur);
+  const double dmax = vload(&st->dmax);
+  const double tau = d.tau;
+  if (!(dmax >= tau)) {
+    if (tid == 0) st->converged = 1;
+    return;
+  }
+  const double* D = dcur(d, cur);
+  unsigned* hist = (unsigned*)smem;                           // [4096]
+  unsigned long long* tkey = (unsigned long long*)(smem + 16384);   // [kTieCap]
+  int64_t* trow = (int64_t*)(smem + 16384 + 8 * kTieCap);     // [kTieCap]
+  const int b = d.b;
+  int cnt = 0;
+  for (int64_t r = tid; r < n; r += kBT) cnt += (__ldcg(D + r) >= tau) ? 1 : 0;
+  cnt = cta_sum_int(cnt, red->n);
+  // s_int: 0 n_cand, 1 n_tie, 2 need, 3 sel bin, 4 fixed bits, 5 stop
+  unsigned long long prefix = 0;
+  int fixed = 0, need = b;
+  if (cnt > b) {
+    for (;;) {
+      const int dig = min(12, 64 - fixed);
+      const int shift = 64 - fixed - dig;
+      const unsigned nbin = 1u << dig;
+      for (unsigned k = tid; k < nbin; k += kBT) hist[k] = 0;
+      __syncthreads();
+      for (int64_t r = tid; r < n; r += kBT) {
+        const double x = __ldcg(D + r);
+        if (!(x >= tau)) continue;
+        const unsigned long long key = (unsigned long long)__double_as_longlong(x);
+        if (fixed > 0 && (key >> (64 - fixed)) != prefix) continue;
+        atomicAdd(&hist[(unsigned)((key >> shift) & (nbin - 1))], 1u);
+      }
+      __syncthreads();
+      // bin of the need-th largest: chunk sums (32 bins per thread), then one scan
+      const unsigned per = (nbin + kBT - 1) / kBT;
+      unsigned csum = 0;
+      for (unsigned k = tid * per; k < min(nbin, (tid + 1) * per); ++k) csum += hist[k];
+      unsigned* chunk = (unsigned*)(smem + 16384);  // tkey area is free during the passes
+      chunk[tid] = csum;
+      __syncthreads();
+      if (tid == 0) {
+        unsigned above = 0;
+        int c = kBT - 1;
+        for (; c > 0; --c) {
+          if (above + chunk[c] >= (unsigned)need) break;
+          above += chunk[c];
+        }
+        unsigned bin = min(nbin, (unsigned)(c + 1) * per);
+        unsigned sel = (unsigned)c * per;
+        for (unsigned k = bin; k-- > (unsigned)c * per;) {
+          if (above + hist[k] >= (unsigned)need) { sel = k; break; }
+          above += hist[k];
+        }
+        s_int[2] = need - (int)above;
+        s_int[3] = (int)sel;
+        s_int[5] = (hist[sel] <= (unsigned)kTieCap || fixed + dig == 64) ? 1 : 0;
+      }
+      __syncthreads();
+      need = s_int[2];
+      prefix = (prefix << dig) | (unsigned long long)s_int[3];
+      fixed += dig;
+      const int stop = s_int[5];
+      __syncthreads();
+      if (stop) break;
+    }
+  }
+  // collect: rows above the bin (all taken) and the bin's rows, in row order
+  if (tid == 0) { s_int[0] = 0; s_int[1] = 0; }
+  __syncthreads();
+  for (int64_t r0 = 0; r0 < n; r0 += kBT) {
+    const int64_t r = r0 + tid;
+    int kind = 0;   // 1 above, 2 in the bin
+    unsigned long long key = 0;
+    if (r < n) {
+      const double x = __ldcg(D + r);
+      if (x >= tau) {
+        key = (unsigned long long)__double_as_longlong(x);
+        if (cnt <= b) kind = 1;
+        else {
+          const unsigned long long hi = key >> (64 - fixed);
+          kind = hi > prefix ? 1 : (hi == prefix ? 2 : 0);
+        }
+      }
+    }
+    const unsigned ma = __ballot_sync(0xffffffffu, kind == 1);
+    const unsigned mt = __ballot_sync(0xffffffffu, kind == 2);
+    const int w = tid >> 5, lane = tid & 31;
+    if (lane == 0) { red->n[w] = __popc(ma) | (__popc(mt) << 8); }
+    __syncthreads();
+    int base_a = s_int[0], base_t = s_int[1];
+    for (int k = 0; k < w; ++k) { base_a += red->n[k] & 0xff; base_t += red->n[k] >> 8; }
+    const unsigned below = (1u << lane) - 1u;
+    if (kind == 1) s_cand[base_a + __popc(ma & below)] = r;
+    if (kind == 2) {
+      const int t = base_t + __popc(mt & below);
+      if (t < kTieCap) { tkey[t] = key; trow[t] = r; }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int ta = 0, tt = 0;
+      for (int k = 0; k < kBT / 32; ++k) { ta += red->n[k] & 0xff; tt += red->n[k] >> 8; }
+      s_int[0] += ta;
+      s_int[1] += tt;
+    }
+    __syncthreads();
+  }
+  if (cnt > b) {
+    const int nab = s_int[0];
+    const int nt = min(s_int[1], kTieCap);
+    for (int e = tid; e < nt; e += kBT) {
+      int rank = 0;
+      for (int f = 0; f < nt; ++f)
+        rank += (tkey[f] > tkey[e] || (tkey[f] == tkey[e] && trow[f] < trow[e])) ? 1 : 0;
+      if (rank < need) s_cand[nab + rank] = trow[e];
+    }
+    __syncthreads();
+    if (tid == 0) s_int[0] = nab + need;
+    __syncthreads();
+  }
+  const int nc = min(s_int[0], b);
+  // slots: free the ones no longer wanted, keep the others, new rows take free slots
+  if (tid == 0) {
+    volatile SysState* st = d.st;
+    // candidates in row order (deterministic slot assignment)
+    for (int i = 1; i < nc; ++i) {
+      const int64_t x = s_cand[i];
+      int j = i - 1;
+      while (j >= 0 && s_cand[j] > x) { s_cand[j + 1] = s_cand[j]; --j; }
+      s_cand[j + 1] = x;
+    }
+    const int64_t K = st->K;
+    bool kept[kBMaxB];
+    for (int s = 0; s < b; ++s) {
+      const int64_t r = st->slot_row[s];
+      bool want = false;
+      if (r >= 0)
+        for (int i = 0; i < nc; ++i) want = want || (s_cand[i] == r);
+      if (r >= 0 && !want) st->slot_row[s] = -1;
+      kept[s] = r >= 0 && want;
+    }
+    // update groups: new slots need vectors [0, K), kept ones [valid, K)
+    int nnew = 0, nkeep = 0;
+    int64_t kvalid = K;
+    KetDesc kd[kBMaxB];
+    int nk = 0;
+    for (int i = 0; i < nc; ++i) {
+      const int64_t r = s_cand[i];
+      int slot = -1;
+      for (int s = 0; s < b; ++s)
+        if (kept[s] && st->slot_row[s] == r) slot = s;
+      if (slot >= 0) continue;
+      for (int s = 0; s < b && slot < 0; ++s)
+        if (st->slot_row[s] < 0) slot = s;
+      if (slot < 0) break;   // cannot happen: at most b candidates, kept ones hold their slots
+      st->slot_row[slot] = r;
+      kept[slot] = false;
+      st->uslot[0][nnew] = slot;
+      st->urow[0][nnew] = r;
+      ++nnew;
+      KetDesc k;
+      k.sp = __ldg(d.row_allsp + r);
+      k.slot = slot;
+      k.kc = __ldg(d.row_kc + r);
+      k.kd = __ldg(d.row_kd + r);
+      if (k.sp < d.all_cls[1]) { k.lc = 0; k.ld = 0; }
+      else if (k.sp < d.all_cls[2]) { k.lc = 1; k.ld = 0; }
+      else { k.lc = 1; k.ld = 1; }
+      kd[nk++] = k;
+    }
+    for (int s = 0; s < b; ++s)
+      if (kept[s] && st->slot_valid[s] < K) {
+        st->uslot[1][nkeep] = s;
+        st->urow[1][nkeep] = st->slot_row[s];
+        kvalid = min(kvalid, st->slot_valid[s]);
+        ++nkeep;
+      }
+    st->nb[0] = K > 0 ? nnew : 0;
+    st->k0[0] = 0;
+    st->nb[1] = nkeep;
+    st->k0[1] = kvalid;
+    for (int s = 0; s < b; ++s)
+      if (st->slot_row[s] >= 0) st->slot_valid[s] = K;
+    // ket groups: same shell pair together (sorted by shell pair, kc, kd), up to
+    // 9 components for a (pp) shell pair and 3 otherwise
+    for (int i = 1; i < nk; ++i) {
+      const KetDesc x = kd[i];
+      int j = i - 1;
+      while (j >= 0 && (kd[j].sp > x.sp || (kd[j].sp == x.sp && (kd[j].kc > x.kc || (kd[j].kc == x.kc && kd[j].kd > x.kd))))) {
+        kd[j + 1] = kd[j];
+        --j;
+      }
+      kd[j + 1] = x;
+    }
+    int ng = 0;
+    for (int i = 0; i < nk;) {
+      const int cap = (kd[i].lc == 1 && kd[i].ld == 1) ? kMaxKetGroup : 3;
+      int j = i;
+      while (j < nk && kd[j].sp == kd[i].sp && j - i < cap) ++j;
+      KetGroup g;
+      memset(&g, 0, sizeof(g));
+      g.sp = kd[i].sp;
+      g.lc = kd[i].lc;
+      g.ld = kd[i].ld;
+      g.nc = (int8_t)(j - i);
+      for (int c = 0; c < j - i; ++c) {
+        g.kc[c] = kd[i + c].kc;
+        g.kd[c] = kd[i + c].kd;
+        g.slot[c] = kd[i + c].slot;
+      }
+      d.groups[ng++] = g;
+      i = j;
+    }
+    st->ngroups = ng;
+    st->Kb = K;
+    st->gitems[0] = st->nb[0] > 0 ? (int)ceil_div(K - st->k0[0], kGatherQ) : 0;
+    st->gitems[1] = st->nb[1] > 0 ? (int)ceil_div(K - st->k0[1], kGatherQ) : 0;
+    int64_t neri = 0;
+    for (int c = 0; c < 3; ++c) neri += (int64_t)d.ntile[c] * ng;
+    st->nitems[0] = st->gitems[0] + st->gitems[1];
+    st->nitems[1] = (int)neri;
+  }
+}
+
+// ----------------------------------------------------------------- COLS ----
+__device__ void gather_item(const SysDesc& d, unsigned it) {
+  SysState* st = d.st;
+  const int g0 = vload(&st->gitems[0]);
+  const int g = (int)it < g0 ? 0 : 1;
+  const unsigned chunk = g == 0 ? it : it - g0;
+  const int nb = vload(&st->nb[g]);
+  const int64_t k0 = vload(&st->k0[g]), K = vload(&st->K);
+  const int64_t q0 = k0 + (int64_t)chunk * kGatherQ;
+  const int64_t q1 = min(K, q0 + kGatherQ);
+  double* Bg = g ? d.Bg1 : d.Bg0;
+  const int64_t tot = (q1 - q0) * nb;
+  for (int64_t e = threadIdx.x; e < tot; e += kBT) {
+    const int64_t q = q0 + e / nb;
+    const int j = (int)(e % nb);
+    const int64_t row = vload(&st->urow[g][j]);
+    Bg[(q - k0) * nb + j] = __ldcg(d.L + q * d.ld + row);
+  }
+}
+
+__device__ void eri_item(const SysDesc& d, unsigned it, const double* boys, KetGroup* sg) {
+  SysState* st = d.st;
+  const int ng = vload(&st->ngroups);
+  int64_t j = (int64_t)it - vload(&st->nitems[0]);
+  int c = 2;
+  for (; c > 0; --c) {
+    const int64_t cnt = (int64_t)d.ntile[c] * ng;
+    if (j < cnt) break;
+    j -= cnt;
+  }
+  const int64_t tile = j / ng;
+  const int g = (int)(j % ng);
+  if (threadIdx.x < (int)(sizeof(KetGroup) / 16))
+    ((int4*)sg)[threadIdx.x] = __ldcg((const int4*)(d.groups + g) + threadIdx.x);
+  __syncthreads();
+  unsigned long long ops = 0;
+  if (c == 0) column_item<0, 0>(d.bra, nullptr, d.cls[0], d.cls[1], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
+  else if (c == 1) column_item<1, 0>(d.bra, nullptr, d.cls[1], d.cls[2], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
+  else column_item<1, 1>(d.bra, nullptr, d.cls[2], d.cls[3], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
+}
+
+// --------------------------------------------------------------- UPDATE ----
+// pool[slot_j][r] -= sum_{q in [k0, K)} L[q][r] Bg[q - k0][j] for 128 rows and
+// the nb <= 64 columns of one update group.  Thread (tx, ty) owns rows
+// tx + 16 i (i < 8) and columns 8 ty + c (c < 8).
+__device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) {
+  SysState* st = d.st;
+  const int n0 = vload(&st->nitems[0]);
+  const int g = (int)it < n0 ? 0 : 1;
+  const int64_t tile = g == 0 ? it : it - n0;
+  const int nb = vload(&st->nb[g]);
+  const int64_t k0 = vload(&st->k0[g]), K = vload(&st->K);
+  const int64_t n = d.n, ld = d.ld, r0 = tile * kRowTile;
+  const double* Bg = g ? d.Bg1 : d.Bg0;
+  double (*As)[kRowTile] = (double (*)[kRowTile])smem;                  // [16][128]
+  double (*Bs)[kBMaxB] = (double (*)[kBMaxB])(smem + 16 * kRowTile * 8);  // [16][64]
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[i][c] = 0.0;
+  for (int64_t kk = k0; kk < K; kk += 16) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + kBT * t;
+      const int k = e >> 6, rp = (e & 63) * 2;
+      const int64_t q = kk + k, r = r0 + rp;
+      double2 x = make_double2(0.0, 0.0);
+      if (q < K) {
+        const double* src = d.L + q * ld + r;
+        if (r + 1 < n) x = __ldcg((const double2*)src);
+        else if (r < n) x.x = __ldcg(src);
+      }
+      *(double2*)&As[k][rp] = x;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + kBT * t;
+      const int k = e >> 6, j = e & 63;
+      const int64_t q = kk + k;
+      Bs[k][j] = (q < K && j < nb) ? __ldcg(Bg + (q - k0) * nb + j) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      double a[8], bb[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[k][tx + 16 * i];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) bb[c] = Bs[k][ty * 8 + c];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[i][c] = fma(a[i], bb[c], acc[i][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = ty * 8 + c;
+    if (j >= nb) continue;
+    double* col = d.pool + (int64_t)vload(&st->uslot[g][j]) * ld;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int64_t r = r0 + tx + 16 * i;
+      if (r < n) col[r] = __ldcg(col + r) - acc[i][c];
+    }
+  }
+}
+
+// ----------------------------------------------------------------- STEP ----
+// L^K_r = (col_r - sum_{k in [Kb, K)} L^k_r L^k_p) / sqrt(D_p), D'_r = D_r - (L^K_r)^2
+// for 1024 rows; the item's argmax of D' goes to part_val / part_idx.
+__device__ void step_item(const SysDesc& d, unsigned it, unsigned char* smem, Red* red) {
+  SysState* st = d.st;
+  const int64_t K = vload(&st->K), Kb = vload(&st->Kb), prow = vload(&st->prow);
+  const int pslot = vload(&st->pslot), cur = vload(&st->cur);
+  const double dp = vload(&st->dp);
+  const int64_t n = d.n, ld = d.ld;
+  double* g = (double*)smem;
+  const int nk = (int)(K - Kb);
+  for (int k = threadIdx.x; k < nk; k += kBT) g[k] = __ldcg(d.L + (Kb + k) * ld + prow);
+  __syncthreads();
+  const int64_t r0 = (int64_t)it * kStepRows + threadIdx.x;
+  constexpr int R = kStepRows / kBT;
+  double acc[R];
+  const double* col = d.pool + (int64_t)pslot * ld;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int64_t r = r0 + (int64_t)j * kBT;
+    acc[j] = r < n ? __ldcg(col + r) : 0.0;
+  }
+  for (int k = 0; k < nk; ++k) {
+    const double gk = g[k];
+    const double* Lk = d.L + (Kb + k) * ld;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int64_t r = r0 + (int64_t)j * kBT;
+      if (r < n) acc[j] = fma(-__ldcg(Lk + r), gk, acc[j]);
+    }
+  }
+  const double inv = 1.0 / sqrt(dp);
+  const double* Din = dcur(d, cur);
+  double* Dout = dnext(d, cur);
+  double* Lout = d.L + K * ld;
+  double bv = -1.0e300;
+  int64_t bi = INT64_MAX;
+  int bad = 0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int64_t r = r0 + (int64_t)j * kBT;
+    if (r < n) {
+      const double vv = acc[j] * inv;
+      Lout[r] = vv;
+      const double dd = fma(-vv, vv, __ldcg(Din + r));
+      Dout[r] = dd;
+      bad |= dd < d.neg_tol;
+      if (better(dd, r, bv, bi)) { bv = dd; bi = r; }
+    }
+  }
+  cta_argmax(bv, bi, red->v, red->i);
+  if (bad) atomicOr(&d.st->bad, 1);
+  if (threadIdx.x == 0) {
+    d.part_val[it] = bv;
+    d.part_idx[it] = bi;
+  }
+}
+
+// ------------------------------------------------------------------- JK ----
+// d_r = D_{mu nu} (2 - delta_{mu nu}), D = 2 C C^T
+__device__ void dens_item(const SysDesc& d, unsigned it) {
+  const int64_t r0 = (int64_t)it * kStepRows;
+  for (int64_t r = r0 + threadIdx.x; r < min(d.n, r0 + kStepRows); r += kBT) {
+    const int mu = __ldg(d.row_mu + r), nu = __ldg(d.row_nu + r);
+    const double* cm = d.C + (int64_t)mu * d.O;
+    const double* cn = d.C + (int64_t)nu * d.O;
+    double s = 0.0;
+    for (int i = 0; i < d.O; ++i) s = fma(__ldg(cm + i), __ldg(cn + i), s);
+    d.dpk[r] = 2.0 * s * (mu == nu ? 1.0 : 2.0);
+  }
+}
+
+// B^P[mu][i] = sum_nu L^P_{mu nu} C[nu][i] for one vector P (warp per mu, lanes over i)
+__device__ void kb_item(const SysDesc& d, unsigned P) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const double* Lp = d.L + (int64_t)P * d.ld;
+  double* Bp = d.B + (int64_t)P * d.N * d.Op;
+  for (int mu = w; mu < d.N; mu += kBT / 32) {
+    const int e0 = __ldg(d.csr_off + mu), e1 = __ldg(d.csr_off + mu + 1);
+    for (int i0 = 0; i0 < d.Op; i0 += 32) {
+      const int i = i0 + lane;
+      double s = 0.0;
+      if (i < d.O)
+        for (int e = e0; e < e1; ++e) {
+          const double l = __ldcg(Lp + __ldg(d.csr_row + e));
+          s = fma(l, __ldg(d.C + (int64_t)__ldg(d.csr_nu + e) * d.O + i), s);
+        }
+      if (i < d.Op) Bp[(int64_t)mu * d.Op + i] = s;
+    }
+  }
+}
+
+// v_P = sum_r L^P_r d_r for kJvVec vectors
+__device__ void jv_item(const SysDesc& d, unsigned it, int64_t M, Red* red) {
+  for (int t = 0; t < kJvVec; ++t) {
+    const int64_t P = (int64_t)it * kJvVec + t;
+    if (P >= M) break;
+    const double* Lp = d.L + P * d.ld;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < d.n; r += kBT) s = fma(__ldcg(Lp + r), __ldcg(d.dpk + r), s);
+    s = cta_sum(s, red->v);
+    if (threadIdx.x == 0) d.v[P] = s;
+  }
+}
+
+__device__ __forceinline__ void tile_of(unsigned t, int& bi, int& bj) {
+  int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((i + 1) * (i + 2) / 2 <= (int)t) ++i;
+  while (i * (i + 1) / 2 > (int)t) --i;
+  bi = i;
+  bj = (int)t - i * (i + 1) / 2;
+}
+
+// Kpart[s][mu][nu] = sum_{P in split s} sum_i B^P[mu][i] B^P[nu][i] over one
+// 64 x 64 tile (block row bi >= block column bj).  Thread (tx, ty) owns
+// mu = tx + 16 a (a < 4) and nu = ty + 8 c (c < 8).
+__device__ void kt_item(const SysDesc& d, unsigned it, int64_t M, int ntiles, unsigned char* smem) {
+  const int s = (int)(it / ntiles);
+  int bi, bj;
+  tile_of(it % ntiles, bi, bj);
+  const int mu0 = bi * kKt, nu0 = bj * kKt, N = d.N, Op = d.Op;
+  double (*As)[kKt] = (double (*)[kKt])smem;               // [8][64]
+  double (*Bs)[kKt] = (double (*)[kKt])(smem + 8 * kKt * 8);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[a][c] = 0.0;
+  const int64_t P0 = (int64_t)s * kKtSplit, P1 = min(M, P0 + kKtSplit);
+  for (int64_t P = P0; P < P1; ++P) {
+    const double* Bp = d.B + P * N * Op;
+    for (int i0 = 0; i0 < Op; i0 += 8) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = tid + kBT * t;
+        const int ii = e & 7, m = e >> 3;
+        const int mu = mu0 + m, nu = nu0 + m;
+        As[ii][m] = mu < N ? __ldcg(Bp + (int64_t)mu * Op + i0 + ii) : 0.0;
+        Bs[ii][m] = nu < N ? __ldcg(Bp + (int64_t)nu * Op + i0 + ii) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        double a[4], bb[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[q] = As[k][tx + 16 * q];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) bb[c] = Bs[k][ty + 8 * c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[q][c] = fma(a[q], bb[c], acc[q][c]);
+      }
+      __syncthreads();
+    }
+  }
+  double* Kp = d.Kpart + (int64_t)s * N * N;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int mu = mu0 + tx + 16 * q;
+    if (mu >= N) continue;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int nu = nu0 + ty + 8 * c;
+      if (nu < N) Kp[(int64_t)mu * N + nu] = acc[q][c];
+    }
+  }
+}
+
+// J_r = sum_P L^P_r v_P for 1024 rows (v staged through shared memory)
+__device__ void jp_item(const SysDesc& d, unsigned it, int64_t M, unsigned char* smem) {
+  double* vs = (double*)smem;   // [1024]
+  const int64_t r0 = (int64_t)it * kStepRows + threadIdx.x;
+  constexpr int R = kStepRows / kBT;
+  double acc[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) acc[j] = 0.0;
+  for (int64_t P0 = 0; P0 < M; P0 += 1024) {
+    const int np = (int)min((int64_t)1024, M - P0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += kBT) vs[k] = __ldcg(d.v + P0 + k);
+    __syncthreads();
+    for (int k = 0; k < np; ++k) {
+      const double vk = vs[k];
+      const double* Lk = d.L + (P0 + k) * d.ld;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t r = r0 + (int64_t)j * kBT;
+        if (r < d.n) acc[j] = fma(__ldcg(Lk + r), vk, acc[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int64_t r = r0 + (int64_t)j * kBT;
+    if (r < d.n) d.Jp[r] = acc[j];
+  }
+}
+
+// K[mu][nu] = K[nu][mu] = 2 sum_s Kpart[s][mu][nu] over one tile
+__device__ void ksum_item(const SysDesc& d, unsigned t, int nsplit) {
+  int bi, bj;
+  tile_of(t, bi, bj);
+  const int N = d.N;
+  for (int e = threadIdx.x; e < kKt * kKt; e += kBT) {
+    const int mu = bi * kKt + e / kKt, nu = bj * kKt + e % kKt;
+    if (mu >= N || nu >= N) continue;
+    double s = 0.0;
+    for (int q = 0; q < nsplit; ++q) s += __ldcg(d.Kpart + ((int64_t)q * N + mu) * N + nu);
+    d.Kx[(int64_t)mu * N + nu] = 2.0 * s;
+    d.Kx[(int64_t)nu * N + mu] = 2.0 * s;
+  }
+}
+
+__device__ void junpack_item(const SysDesc& d, unsigned it) {
+  const int64_t r0 = (int64_t)it * kStepRows;
+  for (int64_t r = r0 + threadIdx.x; r < min(d.n, r0 + kStepRows); r += kBT) {
+    const int mu = __ldg(d.row_mu + r), nu = __ldg(d.row_nu + r);
+    const double x = __ldcg(d.Jp + r);
+    d.J[(int64_t)mu * d.N + nu] = x;
+    d.J[(int64_t)nu * d.N + mu] = x;
+  }
+}
+
+// -------------------------------------------------------------- finishes ----
+// Thread 0 only: publish the next job (parameters first, then the word).
+__device__ void publish(volatile SysState* st, int type, unsigned count) {
+  st->type = type;
+  st->done = 0;
+  __threadfence();
+  const unsigned long long w = st->word;
+  atomicExch((unsigned long long*)&st->word, job_word(job_gen(w) + 1, count, 0));
+}
+__device__ void end_system(volatile SysState* st, BatchCtl* ctl, int status) {
+  if (status != CD_OK) st->status = status;
+  publish(st, kJobNone, 0);
+  __threadfence();
+  atomicAdd(&ctl->done_sys, 1u);
+}
+
+__device__ __forceinline__ int ntiles_k(int N) { const int nb = (N + kKt - 1) / kKt; return nb * (nb + 1) / 2; }
+
+// Runs in thread 0: moves a system from the end of job `type` to its next
+// non-empty job (or ends it).
+__device__ void advance(const SysDesc& d, int type, BatchCtl* ctl) {
+  volatile SysState* st = d.st;
+  const unsigned nrow = ceil_div(d.n, kStepRows);
+  for (;;) {
+    const int64_t K = st->K;
+    switch (type) {
+      case kJobSelect: {
+        if (st->converged) { type = kJobConverged; break; }
+        const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
+        if (c > 0) { publish(st, kJobCols, c); return; }
+        type = kJobCols;
+        break;
+      }
+      case kJobCols: {
+        const unsigned t = ceil_div(d.n, kRowTile);
+        st->nitems[0] = (st->nb[0] > 0 && K > st->k0[0]) ? (int)t : 0;
+        st->nitems[1] = (st->nb[1] > 0 && K > st->k0[1]) ? (int)t : 0;
+        const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
+        if (c > 0) { publish(st, kJobUpdate, c); return; }
+        type = kJobUpdate;
+        break;
+      }
+      case kJobUpdate: {
+        // first step of the block: the pivot is the argmax (one of the candidates)
+        const int64_t p = st->idx;
+        int slot = -1;
+        for (int s = 0; s < d.b; ++s)
+          if (st->slot_row[s] == p) slot = s;
+        const double dp = __ldcg(dcur(d, st->cur) + p);
+        if (slot < 0 || !(dp > 0.0)) { end_system(st, ctl, slot < 0 ? CD_EINVAL : CD_ENOTPSD); return; }
+        st->prow = p;
+        st->pslot = slot;
+        st->dp = dp;
+        publish(st, kJobStep, nrow);
+        return;
+      }
+      case kJobConverged: {   // J/K build
+        const int64_t M = K;
+        st->nitems[0] = (int)nrow;
+        st->nitems[1] = (int)M;
+        const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
+        if (c > 0) { publish(st, kJobJk1, c); return; }
+        type = kJobJk1;
+        break;
+      }
+      case kJobJk1: {
+        const int64_t M = K;
+        const int nsplit = (int)ceil_div(M, kKtSplit);
+        st->nitems[0] = (int)ceil_div(M, kJvVec);
+        st->nitems[1] = nsplit * ntiles_k(d.N);
+        const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
+        if (c > 0) { publish(st, kJobJk2, c); return; }
+        type = kJobJk2;
+        break;
+      }
+      case kJobJk2: {
+        st->nitems[0] = (int)nrow;
+        st->nitems[1] = ntiles_k(d.N);
+        publish(st, kJobJk3, (unsigned)(st->nitems[0] + st->nitems[1]));
+        return;
+      }
+      case kJobJk3: {
+        if (nrow > 0) { publish(st, kJobJk4, nrow); return; }
+        type = kJobJk4;
+        break;
+      }
+      case kJobJk4:
+        end_system(st, ctl, CD_OK);
+        return;
+      default:
+        end_system(st, ctl, CD_EINVAL);
+        return;
+    }
+  }
+}
+
+// End of a pivot step (whole CTA): the step's argmax from the item partials,
+// the pivot recorded, then the next job.
+__device__ void finish_step(const SysDesc& d, BatchCtl* ctl, Red* red) {
+  volatile SysState* st = d.st;
+  const unsigned nit = ceil_div(d.n, kStepRows);
+  double bv = -1.0e300;
+  int64_t bi = INT64_MAX;
+  for (unsigned k = threadIdx.x; k < nit; k += kBT) {
+    const double v2 = __ldcg(d.part_val + k);
+    const int64_t i2 = __ldcg(d.part_idx + k);
+    if (better(v2, i2, bv, bi)) { bv = v2; bi = i2; }
+  }
+  cta_argmax(bv, bi, red->v, red->i);
+  if (threadIdx.x != 0) return;
+  const int64_t K = st->K;
+  d.piv[K] = st->prow;
+  d.pivd[K] = st->dp;
+  st->slot_row[st->pslot] = -1;
+  st->K = K + 1;
+  st->cur ^= 1;
+  st->dmax = bv;
+  st->idx = bi;
+  const int bad = st->bad;
+  st->bad = 0;
+  if (bad) { end_system(st, ctl, CD_ENOTPSD); return; }
+  if (!(bv >= d.tau)) { advance(d, kJobConverged, ctl); return; }
+  if (K + 1 >= d.Mcap) { end_system(st, ctl, CD_ENOMEM); return; }
+  int slot = -1;
+  for (int s = 0; s < d.b; ++s)
+    if (st->slot_row[s] == bi) slot = s;
+  if (slot < 0) { publish(st, kJobSelect, 1); return; }
+  const double dp = __ldcg(dcur(d, st->cur) + bi);
+  if (!(dp > 0.0)) { end_system(st, ctl, CD_ENOTPSD); return; }
+  st->prow = bi;
+  st->pslot = slot;
+  st->dp = dp;
+  publish(st, kJobStep, nit);
+}
+
+// ---------------------------------------------------------------- kernel ----
+__global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict__ sys, int n_sys, BatchCtl* ctl,
+                                                       const double* __restrict__ boys, long long wait_ns) {
+  __shared__ __align__(16) unsigned char smem[kSmemBytes];
+  __shared__ SysDesc sd;
+  __shared__ Red red;
+  __shared__ KetGroup sg;
+  __shared__ int64_t s_cand[kBMaxB + kBT];
+  __shared__ int s_int[8];
+  __shared__ int s_sys, s_last, s_type;
+  __shared__ unsigned s_item, s_count;
+  long long idle_since = -1, last_idle = 0;
+  unsigned long long seen = 0;
+  for (;;) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      int found = -1;
+      unsigned item = 0, count = 0;
+      int stop = 0;
+      if (lane == 0) stop = vload(&ctl->abort) || vload(&ctl->done_sys) >= (unsigned)n_sys;
+      stop = __shfl_sync(0xffffffffu, stop, 0);
+      if (!stop) {
+        for (int base = 0; base < n_sys && found < 0; base += 32) {
+          const int s = base + lane;
+          unsigned long long w = 0;
+          if (s < n_sys) w = vload(&sys[s].st->word);
+          const bool avail = s < n_sys && job_next(w) < job_count(w);
+          unsigned mask = __ballot_sync(0xffffffffu, avail);
+          while (mask && found < 0) {
+            const int l = __ffs(mask) - 1;
+            mask &= mask - 1;
+            unsigned long long old = 0;
+            if (lane == l) old = atomicAdd(&sys[base + l].st->word, 1ull);
+            old = __shfl_sync(0xffffffffu, old, l);
+            if (job_next(old) < job_count(old)) {
+              found = base + l;
+              item = job_next(old);
+              count = job_count(old);
+            }
+          }
+        }
+      }
+      if (lane == 0) {
+        s_sys = stop ? -2 : found;
+        s_item = item;
+        s_count = count;
+      }
+    }
+    __syncthreads();
+    const int s = s_sys;
+    if (s == -2) break;
+    if (s < 0) {
+      // no work: a bounded wait (no item completed anywhere for wait_ns -> give up)
+      if (threadIdx.x == 0) {
+        const unsigned long long p = vload(&ctl->progress);
+        const long long now = globaltimer_ns();
+        if (idle_since >= 0) atomicAdd(&ctl->idle_ns, (unsigned long long)(now - last_idle));
+        last_idle = now;
+        if (idle_since < 0 || p != seen) {
+          idle_since = now;
+          seen = p;
+        } else if (now - idle_since > wait_ns) {
+          atomicExch(&ctl->timed_out, 1);
+          atomicExch(&ctl->abort, 1);
+        }
+        __nanosleep(500);
+      }
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) idle_since = -1;
+    for (int k = threadIdx.x; k < (int)(sizeof(SysDesc) / 16); k += kBT)
+      ((int4*)&sd)[k] = __ldg((const int4*)(sys + s) + k);
+    __threadfence();
+    if (threadIdx.x == 0) s_type = vload(&sys[s].st->type);
+    __syncthreads();
+    const unsigned it = s_item;
+    const int type = s_type;
+    const SysState* st = sd.st;
+    const long long t_item = threadIdx.x == 0 ? globaltimer_ns() : 0;
+    int kind = type;   // item kind for the timing: the second part of a combined job counts as type + 8
+    if (threadIdx.x == 0 && (type == kJobCols || type == kJobJk1 || type == kJobJk2 || type == kJobJk3) &&
+        (int)it >= vload(&st->nitems[0]))
+      kind = type + 8;
+    switch (type) {
+      case kJobSelect: select_item(sd, smem, &red, s_cand, s_int); break;
+      case kJobCols:
+        if ((int)it < vload(&st->nitems[0])) gather_item(sd, it);
+        else eri_item(sd, it, boys, &sg);
+        break;
+      case kJobUpdate: update_item(sd, it, smem); break;
+      case kJobStep: step_item(sd, it, smem, &red); break;
+      case kJobJk1:
+        if ((int)it < vload(&st->nitems[0])) dens_item(sd, it);
+        else kb_item(sd, it - (unsigned)vload(&st->nitems[0]));
+        break;
+      case kJobJk2: {
+        const int n0 = vload(&st->nitems[0]);
+        if ((int)it < n0) jv_item(sd, it, vload(&st->K), &red);
+        else kt_item(sd, it - (unsigned)n0, vload(&st->K), ntiles_k(sd.N), smem);
+        break;
+      }
+      case kJobJk3: {
+        const int n0 = vload(&st->nitems[0]);
+        if ((int)it < n0) jp_item(sd, it, vload(&st->K), smem);
+        else ksum_item(sd, it - (unsigned)n0, (int)ceil_div(vload(&st->K), kKtSplit));
+        break;
+      }
+      case kJobJk4: junpack_item(sd, it); break;
+      default: break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned t = atomicAdd(&sd.st->done, 1u);
+      s_last = (t + 1 == s_count) ? 1 : 0;
+      atomicAdd(&ctl->progress, 1ull);
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (type == kJobStep) {
+        finish_step(sd, ctl, &red);
+      } else if (threadIdx.x == 0) {
+        advance(sd, type, ctl);
+      }
+    }
+    if (threadIdx.x == 0 && kind >= 0 && kind < kJobKinds) {
+      atomicAdd(&ctl->kind_ns[kind], (unsigned long long)(globaltimer_ns() - t_item));
+      atomicAdd(&ctl->kind_items[kind], 1ull);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ----
+namespace {
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+}  // namespace cd
+
+extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts,
+                                   const double* const* C_occ, const int32_t* n_occ, double* const* J,
+                                   double* const* K, int64_t* M_out, double* stats, void* stream) {
+  using namespace cd;
+  if (n_sys < 0 || (n_sys > 0 && (!bases || !opts || !C_occ || !n_occ || !J || !K))) {
+    set_error("cd_batch_persistent: bad argument");
+    return CD_EINVAL;
+  }
+  if (n_sys == 0) return CD_OK;
+  for (int i = 0; i < n_sys; ++i) {
+    const cd_opts_t& o = opts[i];
+    std::string why;
+    if (!(o.tau > 0.0) || !std::isfinite(o.tau)) why = "tau must be finite and > 0";
+    else if (o.block < 0 || o.block > kBMaxB) why = "block must be in [0, 64] (0 = 64)";
+    else if (o.vec_precision != CD_FP64) why = "vectors are FP64";
+    else if (o.algorithm != CD_ALG_FULL || o.forced_pivots || o.candidates || o.diag_shift != 0.0)
+      why = "only the fully pivoted decomposition (CD_ALG_FULL, no forced pivots, mask or shift)";
+    else if (o.max_vectors < 0) why = "max_vectors < 0";
+    else if (n_occ[i] <= 0 || !C_occ[i] || !J[i] || !K[i]) why = "n_occ, C_occ, J, K";
+    if (!why.empty()) {
+      set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + why);
+      return CD_EINVAL;
+    }
+  }
+  const double t0 = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  auto now_ms = []() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  };
+  int dev = 0;
+  CD_CUDA(cudaGetDevice(&dev));
+  cudaStream_t ust = (cudaStream_t)stream;
+  // ---- set-up of every system (screening, diagonal, pair records) on host workers
+  std::vector<cd_system_t*> systems(n_sys, nullptr);
+  std::vector<int> rcs(n_sys, CD_OK);
+  std::vector<std::string> msgs(n_sys);
+  {
+    const int nw = std::max(1, std::min<int>(n_sys, (int)std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+      cudaSetDevice(dev);
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) { cudaGetLastError(); st = nullptr; }
+      for (;;) {
+        const int i = next.fetch_add(1);
+        if (i >= n_sys) break;
+        const int rc = cd_system_create(&bases[i], opts[i].schwarz, st, &systems[i]);
+        rcs[i] = rc;
+        if (rc != CD_OK) msgs[i] = cd_last_error();
+      }
+      if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    };
+    std::vector<std::thread> th;
+    for (int w = 1; w < std::min(nw, 16); ++w) th.emplace_back(work);
+    work();
+    for (auto& t : th) t.join();
+  }
+  auto release_systems = [&]() {
+    for (auto* s : systems)
+      if (s) cd_system_free(s);
+  };
+  for (int i = 0; i < n_sys; ++i)
+    if (rcs[i] != CD_OK) {
+      release_systems();
+      set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + msgs[i]);
+      return rcs[i];
+    }
+  const double t_setup = now_ms();
+  // ---- sizes and one device allocation for every system's buffers
+  struct Plan {
+    int64_t n, ld, Mcap;
+    int N, O, Op, b, nsplit;
+    size_t off[24];
+    size_t bytes;
+    std::vector<int32_t> csr_off, csr_nu, csr_row, allsp;
+    std::vector<int8_t> kc, kd;
+    double dmax;
+    int64_t idx;
+  };
+  std::vector<Plan> plan(n_sys);
+  size_t total = 0;
+  size_t max_items = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    cd_system* s = systems[i];
+    Plan& p = plan[i];
+    p.n = s->n_rows;
+    p.ld = s->n_rows_pad;
+    p.N = s->hb.nbf;
+    p.O = n_occ[i];
+    p.Op = (p.O + 7) / 8 * 8;
+    p.b = opts[i].block ? opts[i].block : kBMaxB;
+    int64_t mcap = opts[i].max_vectors > 0 ? opts[i].max_vectors : (int64_t)8 * p.N;
+    p.Mcap = std::max<int64_t>(1, std::min<int64_t>(mcap, std::max<int64_t>(p.n, 1)));
+    p.nsplit = (int)((p.Mcap + kKtSplit - 1) / kKtSplit);
+    const int64_t nst = std::max<int64_t>(1, (p.n + kStepRows - 1) / kStepRows);
+    const size_t N2 = (size_t)p.N * p.N;
+    size_t sz[] = {
+        sizeof(double) * (size_t)p.ld,               // 0 D0
+        sizeof(double) * (size_t)p.ld,               // 1 D1
+        sizeof(double) * (size_t)p.b * p.ld,         // 2 pool
+        sizeof(double) * (size_t)p.Mcap * p.ld,      // 3 L
+        sizeof(int64_t) * (size_t)p.Mcap,            // 4 piv
+        sizeof(double) * (size_t)p.Mcap,             // 5 pivd
+        sizeof(double) * (size_t)p.Mcap * p.b,       // 6 Bg0
+        sizeof(double) * (size_t)p.b * p.b,          // 7 Bg1
+        sizeof(KetGroup) * (size_t)p.b,              // 8 groups
+        sizeof(double) * (size_t)nst,                // 9 part_val
+        sizeof(int64_t) * (size_t)nst,               // 10 part_idx
+        sizeof(double) * (size_t)p.ld,               // 11 dpk
+        sizeof(double) * (size_t)p.Mcap,             // 12 v
+        sizeof(double) * (size_t)p.ld,               // 13 Jp
+        sizeof(double) * (size_t)p.Mcap * p.N * p.Op,// 14 B
+        sizeof(double) * (size_t)p.nsplit * N2,      // 15 Kpart
+        sizeof(double) * N2,                         // 16 J
+        sizeof(double) * N2,                         // 17 K
+        sizeof(SysState),                            // 18 state
+        sizeof(double) * (size_t)p.N * p.O,          // 19 C
+        sizeof(int32_t) * (size_t)(p.N + 1),         // 20 csr_off
+        sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 21 csr_nu
+        sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 22 csr_row
+        sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n) + 2 * align256((size_t)std::max<int64_t>(1, p.n)),  // 23 allsp, kc, kd
+    };
+    size_t o = 0;
+    for (int k = 0; k < 24; ++k) {
+      p.off[k] = total + o;
+      o += align256(sz[k]);
+    }
+    p.bytes = o;
+    total += o;
+    // row list per basis function: (mu nu) under mu and, if mu != nu, under nu
+    p.csr_off.assign(p.N + 1, 0);
+    std::vector<int32_t> mu(p.n), nu(p.n);
+    for (int64_t r = 0; r < p.n; ++r) {
+      const int64_t pk = s->row_packed[r];
+      int64_t m = (int64_t)((std::sqrt(8.0 * (double)pk + 1.0) - 1.0) / 2.0);
+      while (m * (m + 1) / 2 > pk) --m;
+      while ((m + 1) * (m + 2) / 2 <= pk) ++m;
+      mu[r] = (int32_t)m;
+      nu[r] = (int32_t)(pk - m * (m + 1) / 2);
+      p.csr_off[mu[r] + 1]++;
+      if (mu[r] != nu[r]) p.csr_off[nu[r] + 1]++;
+    }
+    for (int k = 0; k < p.N; ++k) p.csr_off[k + 1] += p.csr_off[k];
+    p.csr_nu.assign(std::max<int32_t>(1, p.csr_off[p.N]), 0);
+    p.csr_row.assign(std::max<int32_t>(1, p.csr_off[p.N]), 0);
+    std::vector<int32_t> fill(p.csr_off.begin(), p.csr_off.end() - 1);
+    for (int64_t r = 0; r < p.n; ++r) {
+      int32_t e = fill[mu[r]]++;
+      p.csr_nu[e] = nu[r];
+      p.csr_row[e] = (int32_t)r;
+      if (mu[r] != nu[r]) {
+        e = fill[nu[r]]++;
+        p.csr_nu[e] = mu[r];
+        p.csr_row[e] = (int32_t)r;
+      }
+    }
+    p.dmax = -1.0;
+    p.idx = -1;
+    for (int64_t r = 0; r < p.n; ++r)
+      if (s->row_diag[r] > p.dmax) { p.dmax = s->row_diag[r]; p.idx = r; }
+    // largest job of the system (queue words hold 24-bit counts)
+    int64_t neri = 0;
+    for (int c = 0; c < 3; ++c) neri += (s->bra_class_off[c + 1] - s->bra_class_off[c] + 127) / 128 * p.b;
+    const int64_t nb_k = (p.N + kKt - 1) / kKt;
+    const int64_t jobs[] = {neri + 2 * ((p.Mcap + kGatherQ - 1) / kGatherQ), 2 * ((p.n + kRowTile - 1) / kRowTile),
+                            nst + p.Mcap, (p.Mcap + kJvVec - 1) / kJvVec + p.nsplit * nb_k * (nb_k + 1) / 2};
+    for (int64_t j : jobs) max_items = std::max<size_t>(max_items, (size_t)j);
+  }
+  if (max_items >= kMaxJobItems) {
+    release_systems();
+    set_error("cd_batch_persistent: a system needs more than 2^23 work items in one job");
+    return CD_EINVAL;
+  }
+  size_t freeb = 0, totb = 0;
+  CD_CUDA(cudaMemGetInfo(&freeb, &totb));
+  const double budget = opts[0].mem_budget_gb > 0 ? opts[0].mem_budget_gb * 1e9 : 0.9 * (double)freeb;
+  if ((double)total > budget) {
+    release_systems();
+    set_error("cd_batch_persistent: device memory for the batch (" + std::to_string(total / 1e9) +
+              " GB) exceeds the budget (" + std::to_string(budget / 1e9) + " GB)");
+    return CD_ENOMEM;
+  }
+  unsigned char* arena = nullptr;
+  if (cudaMalloc(&arena, total) != cudaSuccess) {
+    cudaGetLastError();
+    release_systems();
+    set_error("cd_batch_persistent: cudaMalloc of " + std::to_string(total) + " bytes failed");
+    return CD_ENOMEM;
+  }
+  SysDesc* desc_dev = nullptr;
+  BatchCtl* ctl_dev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = CD_OK;
+  std::vector<SysState> hst(n_sys);
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(desc_dev);
+    cudaFree(ctl_dev);
+    cudaFree(arena);
+    release_systems();
+  };
+  auto fail = [&](int code) {
+    cleanup();
+    return code;
+  };
+#define BP_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t _e = (call);                                                            \
+    if (_e != cudaSuccess) {                                                            \
+      cudaGetLastError();                                                               \
+      set_error(std::string("cd_batch_persistent: ") + cudaGetErrorString(_e) + " at " + \
+                std::to_string(__LINE__));                                              \
+      return fail(CD_ECUDA);                                                            \
+    }                                                                                   \
+  } while (0)
+  BP_CUDA(cudaMalloc(&desc_dev, sizeof(SysDesc) * n_sys));
+  BP_CUDA(cudaMalloc(&ctl_dev, sizeof(BatchCtl)));
+  BP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  BP_CUDA(cudaEventCreate(&e0));
+  BP_CUDA(cudaEventCreate(&e1));
+  BP_CUDA(cudaStreamSynchronize(ust));
+  // systems largest first: CTAs scan them in this order
+  std::vector<int> order(n_sys);
+  for (int i = 0; i < n_sys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)plan[a].n * plan[a].N > (double)plan[b].n * plan[b].N;
+  });
+  std::vector<SysDesc> hd(n_sys);
+  std::vector<const double*> boys_of(n_sys);
+  for (int k = 0; k < n_sys; ++k) {
+    const int i = order[k];
+    cd_system* s = systems[i];
+    Plan& p = plan[i];
+    auto at = [&](int slot) { return (void*)(arena + p.off[slot]); };
+    SysDesc& d = hd[k];
+    memset(&d, 0, sizeof(d));
+    d.n = p.n;
+    d.ld = p.ld;
+    d.Mcap = p.Mcap;
+    d.N = p.N;
+    d.O = p.O;
+    d.Op = p.Op;
+    d.b = p.b;
+    d.tau = opts[i].tau;
+    double d1max = 0.0;
+    for (double v : s->row_diag) d1max = std::max(d1max, v);
+    d.neg_tol = -1e-10 * d1max;
+    d.bra = s->bra;
+    d.ket = s->all;
+    for (int c = 0; c < 4; ++c) {
+      d.cls[c] = s->bra_class_off[c];
+      d.all_cls[c] = s->all_class_off[c];
+    }
+    for (int c = 0; c < 3; ++c) d.ntile[c] = (int)((d.cls[c + 1] - d.cls[c] + 127) / 128);
+    d.nsplit_cap = p.nsplit;
+    d.D0 = (double*)at(0);
+    d.D1 = (double*)at(1);
+    d.pool = (double*)at(2);
+    d.L = (double*)at(3);
+    d.piv = (int64_t*)at(4);
+    d.pivd = (double*)at(5);
+    d.Bg0 = (double*)at(6);
+    d.Bg1 = (double*)at(7);
+    d.groups = (KetGroup*)at(8);
+    d.part_val = (double*)at(9);
+    d.part_idx = (int64_t*)at(10);
+    d.dpk = (double*)at(11);
+    d.v = (double*)at(12);
+    d.Jp = (double*)at(13);
+    d.B = (double*)at(14);
+    d.Kpart = (double*)at(15);
+    d.J = (double*)at(16);
+    d.Kx = (double*)at(17);
+    d.st = (SysState*)at(18);
+    d.C = (const double*)at(19);
+    d.csr_off = (const int32_t*)at(20);
+    d.csr_nu = (const int32_t*)at(21);
+    d.csr_row = (const int32_t*)at(22);
+    unsigned char* rt = (unsigned char*)at(23);
+    d.row_allsp = (const int32_t*)rt;
+    d.row_kc = (const int8_t*)(rt + align256(sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n)));
+    d.row_kd = d.row_kc + align256((size_t)std::max<int64_t>(1, p.n));
+    d.row_mu = s->row_mu_dev;
+    d.row_nu = s->row_nu_dev;
+    boys_of[k] = s->boys;
+    // uploads
+    SysState h;
+    memset(&h, 0, sizeof(h));
+    h.word = job_word(1, 1, 0);
+    h.type = kJobSelect;
+    h.dmax = p.dmax;
+    h.idx = p.idx;
+    for (int x = 0; x < kBMaxB; ++x) h.slot_row[x] = -1;
+    BP_CUDA(cudaMemcpyAsync(d.st, &h, sizeof(h), cudaMemcpyHostToDevice, cs));
+    BP_CUDA(cudaMemcpyAsync(d.D0, s->diag_dev, sizeof(double) * p.ld, cudaMemcpyDeviceToDevice, cs));
+    BP_CUDA(cudaMemcpyAsync((void*)d.C, C_occ[i], sizeof(double) * (size_t)p.N * p.O, cudaMemcpyHostToDevice, cs));
+    BP_CUDA(cudaMemcpyAsync((void*)d.csr_off, p.csr_off.data(), sizeof(int32_t) * p.csr_off.size(), cudaMemcpyHostToDevice, cs));
+    BP_CUDA(cudaMemcpyAsync((void*)d.csr_nu, p.csr_nu.data(), sizeof(int32_t) * p.csr_nu.size(), cudaMemcpyHostToDevice, cs));
+    BP_CUDA(cudaMemcpyAsync((void*)d.csr_row, p.csr_row.data(), sizeof(int32_t) * p.csr_row.size(), cudaMemcpyHostToDevice, cs));
+    if (p.n > 0) {
+      BP_CUDA(cudaMemcpyAsync((void*)d.row_allsp, s->row_allsp.data(), sizeof(int32_t) * p.n, cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaMemcpyAsync((void*)d.row_kc, s->row_kc.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaMemcpyAsync((void*)d.row_kd, s->row_kd.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
+    }
+  }
+  for (int k = 1; k < n_sys; ++k)
+    if (boys_of[k] != boys_of[0]) {
+      set_error("cd_batch_persistent: systems on different Boys tables");
+      return fail(CD_EINVAL);
+    }
+  BP_CUDA(cudaMemcpyAsync(desc_dev, hd.data(), sizeof(SysDesc) * n_sys, cudaMemcpyHostToDevice, cs));
+  BP_CUDA(cudaStreamSynchronize(cs));
+  const double t_upload = now_ms();
+  // ---- the launch, recorded in a CUDA graph: clear J and the control block, one persistent kernel
+  int per_sm = 0, sms = 0;
+  BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBT, 0));
+  BP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, per_sm) * sms;
+  const long long wait_ns = (long long)device_wait_limit_ns();
+  BP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < n_sys; ++k)
+    cudaMemsetAsync(hd[k].J, 0, sizeof(double) * (size_t)hd[k].N * hd[k].N, cs);
+  cudaMemsetAsync(ctl_dev, 0, sizeof(BatchCtl), cs);
+  batch_kernel<<<grid, kBT, 0, cs>>>(desc_dev, n_sys, ctl_dev, boys_of[0], wait_ns);
+  BP_CUDA(cudaStreamEndCapture(cs, &graph));
+  BP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  BP_CUDA(cudaEventRecord(e0, cs));
+  BP_CUDA(cudaGraphLaunch(exec, cs));
+  count_launch();
+  BP_CUDA(cudaEventRecord(e1, cs));
+  BP_CUDA(cudaStreamSynchronize(cs));
+  float kms = 0.0f;
+  cudaEventElapsedTime(&kms, e0, e1);
+  BatchCtl hctl;
+  BP_CUDA(cudaMemcpy(&hctl, ctl_dev, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < n_sys; ++k) BP_CUDA(cudaMemcpy(&hst[k], hd[k].st, sizeof(SysState), cudaMemcpyDeviceToHost));
+  if (hctl.timed_out) {
+    set_error("cd_batch_persistent: a CTA's wait for work gave up after the wait limit with no item completed");
+    return fail(CD_ETIMEOUT);
+  }
+  for (int k = 0; k < n_sys; ++k) {
+    const int i = order[k];
+    if (hst[k].status != CD_OK || hst[k].type != kJobNone) {
+      const int code = hst[k].status != CD_OK ? hst[k].status : CD_ETIMEOUT;
+      std::string why = code == CD_ENOTPSD ? "matrix not PSD (pivot diagonal <= 0 or residual below -1e-10 max D)"
+                        : code == CD_ENOMEM ? "number of vectors exceeds max_vectors = " + std::to_string(plan[i].Mcap)
+                                            : "decomposition did not finish";
+      set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + why);
+      return fail(code);
+    }
+  }
+  for (int k = 0; k < n_sys; ++k) {
+    const int i = order[k];
+    const size_t N2 = (size_t)hd[k].N * hd[k].N;
+    BP_CUDA(cudaMemcpy(J[i], hd[k].J, sizeof(double) * N2, cudaMemcpyDeviceToHost));
+    BP_CUDA(cudaMemcpy(K[i], hd[k].Kx, sizeof(double) * N2, cudaMemcpyDeviceToHost));
+    if (M_out) M_out[i] = hst[k].K;
+  }
+  const double t_end = now_ms();
+  if (stats) {
+    stats[0] = t_setup - t0;       // system set-up (host workers)
+    stats[1] = t_upload - t_setup; // sizes, row lists, uploads
+    stats[2] = kms;                // the graph launch (one persistent kernel), device time
+    stats[3] = t_end - t_upload;   // launch, wait and read-back, host time
+    stats[4] = (double)grid;
+    stats[5] = (double)total;
+    // CTA-seconds per item kind: 1 select, 2 gather, 3 update, 4 step, 5 density, 6 v = L d,
+    // 7 J_p = L^T v, 8 J unpack, 10 ERI columns, 13 B = L C, 14 partial K tiles, 15 K sum; 16 idle
+    for (int k = 0; k < kJobKinds; ++k) stats[6 + k] = 0.0;
+    const int kinds[][2] = {{1, kJobSelect}, {2, kJobCols}, {3, kJobUpdate}, {4, kJobStep}, {5, kJobJk1},
+                            {6, kJobJk2}, {7, kJobJk3}, {8, kJobJk4}, {10, kJobCols + 8}, {13, kJobJk1 + 8},
+                            {14, kJobJk2 + 8}, {15, kJobJk3 + 8}};
+    for (auto& kk : kinds) stats[6 + kk[0]] = (double)hctl.kind_ns[kk[1]] * 1e-9;
+    stats[6 + 16] = (double)hctl.idle_ns * 1e-9;
+  }
+  cleanup();
+  return rc;
+#undef BP_CUDA
+}

@@ -479,6 +479,8 @@ int update_cta_registers(int* regs) {
   *regs = (kThreads / 32) * ((a.numRegs * 32 + 255) / 256 * 256);
   return CD_OK;
 }
+// the wall-clock limit of bounded device waits set by cd_set_wait_limit
+unsigned long long device_wait_limit_ns() { return wait_limit_ns(); }
 }  // namespace cd
 
 extern "C" int cd_set_wait_limit(double seconds, double* previous) {
