@@ -40,8 +40,9 @@ MUTANTS = [
     ("p primitive norm", "if (l[s] == 1) n *= sqrt(4.0 * a);", "if (l[s] == 1) n *= 4.0 * a;"),
     ("s primitive norm power", "double n = pow(2.0 * a / OR_PI, 0.75);", "double n = pow(2.0 * a / OR_PI, 0.5);"),
     ("p contraction overlap", "if (l[s] == 1) ov /= 2.0 * ab;", "if (l[s] == 1) ov /= ab;"),
-    ("cd update sign", "col -= L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + p];",
-     "col += L[(int64_t)J * npairs + r] * L[(int64_t)J * npairs + p];"),
+    # Eq. (subtr) in the oracle's default (row-chunked, J-outer) loop order
+    ("cd update sign", "for (int64_t r = r0; r < r1; ++r) out[r] -= LJ[r] * wj;",
+     "for (int64_t r = r0; r < r1; ++r) out[r] += LJ[r] * wj;"),
     ("cd divides by D not sqrt(D)", "double sq = sqrt(D[p]);", "double sq = D[p];"),
     ("cd diagonal update", "D[r] -= LK[r] * LK[r];", "D[r] -= 0.5 * LK[r] * LK[r];"),
 ]
