@@ -117,6 +117,7 @@ struct __align__(16) SysDesc {
   PairSet bra, ket;                 // screened bra shell pairs (by class), all shell pairs
   int64_t cls[4], all_cls[4];
   int ntile[3], nsplit_cap;
+  int64_t nnz;                      // entries of the row lists (2 n minus the diagonal pairs)
   const int32_t* row_allsp;         // [n] shell pair (in ket) of each row
   const int8_t* row_kc;             // [n] canonical components of each row
   const int8_t* row_kd;
@@ -156,6 +157,7 @@ struct BatchCtl {
   unsigned long long progress;  // items completed, all systems
   unsigned long long kind_ns[kJobKinds];     // CTA time per item kind (incl. its job finish)
   unsigned long long kind_items[kJobKinds];  // items per kind
+  unsigned long long kind_ops[kJobKinds];    // FP64-pipe operations per kind (one per FMA; ERI: executed)
   unsigned long long idle_ns;                // CTA time spent looking for work
 };
 
@@ -479,7 +481,8 @@ __device__ void gather_item(const SysDesc& d, unsigned it) {
   }
 }
 
-__device__ void eri_item(const SysDesc& d, unsigned it, const double* boys, KetGroup* sg) {
+__device__ void eri_item(const SysDesc& d, unsigned it, const double* boys, KetGroup* sg,
+                         unsigned long long* ops_out) {
   SysState* st = d.st;
   const int ng = vload(&st->ngroups);
   int64_t j = (int64_t)it - vload(&st->nitems[0]);
@@ -498,13 +501,18 @@ __device__ void eri_item(const SysDesc& d, unsigned it, const double* boys, KetG
   if (c == 0) column_item<0, 0>(d.bra, nullptr, d.cls[0], d.cls[1], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
   else if (c == 1) column_item<1, 0>(d.bra, nullptr, d.cls[1], d.cls[2], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
   else column_item<1, 1>(d.bra, nullptr, d.cls[2], d.cls[3], d.ket, sg, tile, 0, d.pool, d.ld, boys, ops);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ops += __shfl_xor_sync(0xffffffffu, ops, o);
+  if ((threadIdx.x & 31) == 0 && ops) atomicAdd(ops_out, ops);
 }
 
 // --------------------------------------------------------------- UPDATE ----
 // pool[slot_j][r] -= sum_{q in [k0, K)} L[q][r] Bg[q - k0][j] for 128 rows and
-// the nb <= 64 columns of one update group.  Thread (tx, ty) owns rows
-// tx + 16 i (i < 8) and columns 8 ty + c (c < 8).
-__device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) {
+// the nb <= NC columns of one update group (NC = 64, or 32 for narrow groups).
+// Thread (tx, ty) owns rows tx + 16 i (i < 8) and columns CPT ty + c (c < CPT).
+template <int NC>
+__device__ void update_tile(const SysDesc& d, unsigned it, unsigned char* smem) {
+  constexpr int CPT = NC / 8;
   SysState* st = d.st;
   const int n0 = vload(&st->nitems[0]);
   const int g = (int)it < n0 ? 0 : 1;
@@ -514,13 +522,13 @@ __device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) 
   const int64_t n = d.n, ld = d.ld, r0 = tile * kRowTile;
   const double* Bg = g ? d.Bg1 : d.Bg0;
   double (*As)[kRowTile] = (double (*)[kRowTile])smem;                  // [16][128]
-  double (*Bs)[kBMaxB] = (double (*)[kBMaxB])(smem + 16 * kRowTile * 8);  // [16][64]
+  double (*Bs)[NC] = (double (*)[NC])(smem + 16 * kRowTile * 8);  // [16][NC]
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[8][8];
+  double acc[8][CPT];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[i][c] = 0.0;
+    for (int c = 0; c < CPT; ++c) acc[i][c] = 0.0;
   for (int64_t kk = k0; kk < K; kk += 16) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -536,30 +544,30 @@ __device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) 
       *(double2*)&As[k][rp] = x;
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    for (int t = 0; t < NC / 8; ++t) {
       const int e = tid + kBT * t;
-      const int k = e >> 6, j = e & 63;
+      const int k = e / NC, j = e % NC;
       const int64_t q = kk + k;
       Bs[k][j] = (q < K && j < nb) ? __ldcg(Bg + (q - k0) * nb + j) : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      double a[8], bb[8];
+      double a[8], bb[CPT];
 #pragma unroll
       for (int i = 0; i < 8; ++i) a[i] = As[k][tx + 16 * i];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) bb[c] = Bs[k][ty * 8 + c];
+      for (int c = 0; c < CPT; ++c) bb[c] = Bs[k][ty * CPT + c];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[i][c] = fma(a[i], bb[c], acc[i][c]);
+        for (int c = 0; c < CPT; ++c) acc[i][c] = fma(a[i], bb[c], acc[i][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int j = ty * 8 + c;
+  for (int c = 0; c < CPT; ++c) {
+    const int j = ty * CPT + c;
     if (j >= nb) continue;
     double* col = d.pool + (int64_t)vload(&st->uslot[g][j]) * ld;
 #pragma unroll
@@ -568,6 +576,13 @@ __device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) 
       if (r < n) col[r] = __ldcg(col + r) - acc[i][c];
     }
   }
+}
+
+__device__ void update_item(const SysDesc& d, unsigned it, unsigned char* smem) {
+  const SysState* st = d.st;
+  const int g = (int)it < vload(&st->nitems[0]) ? 0 : 1;
+  if (vload(&st->nb[g]) <= 32) update_tile<32>(d, it, smem);
+  else update_tile<64>(d, it, smem);
 }
 
 // ----------------------------------------------------------------- STEP ----
@@ -930,6 +945,45 @@ __device__ void finish_step(const SysDesc& d, BatchCtl* ctl, Red* red) {
   publish(st, kJobStep, nit);
 }
 
+// FMAs of one item as the algorithm counts them (no tile padding), read before
+// the item runs (the job's parameters do not change while it is outstanding)
+__device__ unsigned long long item_work(const SysDesc& d, int type, int kind, unsigned it) {
+  const SysState* st = d.st;
+  const int64_t K = vload(&st->K);
+  if (type == kJobUpdate) {
+    const int n0 = vload(&st->nitems[0]);
+    const int g = (int)it < n0 ? 0 : 1;
+    const int64_t tile = g == 0 ? it : it - n0;
+    const int64_t rows = min((int64_t)kRowTile, d.n - tile * kRowTile);
+    return (unsigned long long)(rows * vload(&st->nb[g]) * (K - vload(&st->k0[g])));
+  }
+  if (type == kJobStep) {
+    const int64_t rows = min((int64_t)kStepRows, d.n - (int64_t)it * kStepRows);
+    return (unsigned long long)(rows * (K - vload(&st->Kb) + 1));
+  }
+  if (kind == kJobJk1 + 8) {   // B^P = L^P C: every screened pair twice (mu nu and nu mu), O each
+    return (unsigned long long)d.nnz * (unsigned long long)d.O;
+  }
+  if (kind == kJobJk2 + 8) {   // partial K tile: tile elements x vectors x O
+    const int ntl = ntiles_k(d.N);
+    const int s = (int)(it - (unsigned)vload(&st->nitems[0])) / ntl;
+    int bi, bj;
+    tile_of((it - (unsigned)vload(&st->nitems[0])) % ntl, bi, bj);
+    const int64_t nm = min(kKt, d.N - bi * kKt), nn = min(kKt, d.N - bj * kKt);
+    const int64_t np = min((int64_t)kKtSplit, K - (int64_t)s * kKtSplit);
+    return (unsigned long long)(nm * nn * np * d.O);
+  }
+  if (kind == kJobJk2) {       // v = L d
+    const int64_t nv = min((int64_t)kJvVec, K - (int64_t)it * kJvVec);
+    return (unsigned long long)(nv * d.n);
+  }
+  if (kind == kJobJk3) {       // J_p = L^T v
+    const int64_t rows = min((int64_t)kStepRows, d.n - (int64_t)it * kStepRows);
+    return (unsigned long long)(rows * K);
+  }
+  return 0;
+}
+
 // ---------------------------------------------------------------- kernel ----
 __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict__ sys, int n_sys, BatchCtl* ctl,
                                                        const double* __restrict__ boys, long long wait_ns) {
@@ -1011,14 +1065,17 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict
     const SysState* st = sd.st;
     const long long t_item = threadIdx.x == 0 ? globaltimer_ns() : 0;
     int kind = type;   // item kind for the timing: the second part of a combined job counts as type + 8
-    if (threadIdx.x == 0 && (type == kJobCols || type == kJobJk1 || type == kJobJk2 || type == kJobJk3) &&
-        (int)it >= vload(&st->nitems[0]))
-      kind = type + 8;
+    unsigned long long item_fma = 0;   // FMAs of the item (thread 0; algorithmic, no padding)
+    if (threadIdx.x == 0) {
+      if ((type == kJobCols || type == kJobJk1 || type == kJobJk2 || type == kJobJk3) && (int)it >= vload(&st->nitems[0]))
+        kind = type + 8;
+      item_fma = item_work(sd, type, kind, it);
+    }
     switch (type) {
       case kJobSelect: select_item(sd, smem, &red, s_cand, s_int); break;
       case kJobCols:
         if ((int)it < vload(&st->nitems[0])) gather_item(sd, it);
-        else eri_item(sd, it, boys, &sg);
+        else eri_item(sd, it, boys, &sg, &ctl->kind_ops[kJobCols + 8]);
         break;
       case kJobUpdate: update_item(sd, it, smem); break;
       case kJobStep: step_item(sd, it, smem, &red); break;
@@ -1060,6 +1117,7 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict
     if (threadIdx.x == 0 && kind >= 0 && kind < kJobKinds) {
       atomicAdd(&ctl->kind_ns[kind], (unsigned long long)(globaltimer_ns() - t_item));
       atomicAdd(&ctl->kind_items[kind], 1ull);
+      if (item_fma) atomicAdd(&ctl->kind_ops[kind], item_fma);
     }
     __syncthreads();
   }
@@ -1336,6 +1394,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     }
     for (int c = 0; c < 3; ++c) d.ntile[c] = (int)((d.cls[c + 1] - d.cls[c] + 127) / 128);
     d.nsplit_cap = p.nsplit;
+    d.nnz = p.csr_off[p.N];
     d.D0 = (double*)at(0);
     d.D1 = (double*)at(1);
     d.pool = (double*)at(2);
@@ -1455,6 +1514,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
                             {14, kJobJk2 + 8}, {15, kJobJk3 + 8}};
     for (auto& kk : kinds) stats[6 + kk[0]] = (double)hctl.kind_ns[kk[1]] * 1e-9;
     stats[6 + 16] = (double)hctl.idle_ns * 1e-9;
+    for (int k = 0; k < kJobKinds; ++k) stats[23 + k] = (double)hctl.kind_ops[k];
   }
   cleanup();
   return rc;
