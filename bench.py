@@ -60,6 +60,8 @@ def _args():
                     help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=48)
     ap.add_argument("--block", type=int, default=0, help="speculative column block b (0 = library default)")
+    ap.add_argument("--batch-only", type=int, default=0,
+                    help="batch64: run only the persistent batch on the first N systems, once (profiling)")
     ap.add_argument("--no-fp64-update", action="store_true",
                     help="skip the factorisation with the FP64 DFMA column update (its roofline entry)")
     return ap.parse_args()
@@ -507,6 +509,16 @@ def run_batch(args):
     if "persistent_blocks" not in table:
         table = autotune.tune_persistent(systems)
     pblocks = autotune.blocks_for(systems, table, "persistent_blocks")
+    if args.batch_only > 0:
+        # the N systems around the median basis size (a small case for profilers)
+        mid = sorted(range(len(systems)), key=lambda i: systems[i].n_basis)
+        c = len(mid) // 2
+        pick = sorted(mid[max(0, c - args.batch_only // 2):max(0, c - args.batch_only // 2) + args.batch_only])
+        sub = [systems[i] for i in pick]
+        pblocks = [pblocks[i] for i in pick]
+        _, _, Mb, info = cd.batch_persistent(sub, blocks=pblocks[:len(sub)])
+        print(json.dumps({"workload": "batch64[:%d]" % len(sub), "M": Mb, "info": info}), flush=True)
+        return 0
     clk = ClockSampler()
 
     def persistent():
