@@ -292,7 +292,7 @@ int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, 
  * 39 entries): [0] set-up ms, [1] upload ms, [2] device ms of the launch, [3]
  * host ms of the launch and read-back, [4] CTAs, [5] bytes reserved, [6 + k]
  * CTA-seconds spent in items of kind k (1 select, 2 gather, 3 update, 4 step,
- * 5 density, 6 v = L d, 7 J_p = L^T v, 8 J unpack, 10 ERI columns, 13 B = L C,
+ * 5 density, 6 v = L d, 7 J_p = L^T v, 8 J unpack, 9 slicing, 10 ERI columns, 13 B = L C,
  * 14 partial K tiles, 15 K sums), [22] CTA-seconds spent looking for work,
  * [23 + k] FP64-pipe operations of the items of kind k (one per FMA as the
  * algorithm counts them; for ERI columns the kernel's executed operations).  All device memory is

@@ -383,13 +383,15 @@ def batch_run(systems, jk_mode: int = CD_JK_FP64, workers: int = 0, blocks=None,
     return Js, Ks
 
 
-def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: float = 0.0, stream=None):
+def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: float = 0.0,
+                     update: int = CD_UPDATE_SLICE, stream=None):
     """Decompose and contract many independent systems in FP64 with one
     persistent kernel launch recorded in a CUDA graph (C ABI cd_batch_persistent).
 
     systems: sequence of synth.System-like objects (basis, C_occ, tau, schwarz).
     blocks: per-system block size b <= 64 (e.g. from the autotuner), or None (64).
     max_vectors: per-system vector capacity, or None (8 N).
+    update: CD_UPDATE_SLICE (exact 7-slice products on the tensor cores) or CD_UPDATE_FP64 (DFMA).
     Returns lists J, K of numpy arrays, the vector counts M and a dict of timings.
     """
     n = len(systems)
@@ -397,7 +399,7 @@ def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: floa
     bases = (cd_basis_t * n)(*[b.s for b in bargs])
     opts = (cd_opts_t * n)(*[make_opts(s.tau, s.schwarz, CD_FP64, int(blocks[i]) if blocks is not None else 0,
                                        int(max_vectors[i]) if max_vectors is not None else 0,
-                                       float(mem_budget_gb) if i == 0 else 0.0)[0]
+                                       float(mem_budget_gb) if i == 0 else 0.0, update=update)[0]
                              for i, s in enumerate(systems)])
     Cs = [np.ascontiguousarray(s.C_occ, dtype=np.float64) for s in systems]
     Js = [np.zeros((c.shape[0], c.shape[0])) for c in Cs]
@@ -414,7 +416,8 @@ def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: floa
             "launch_host_ms": float(stats[3]), "ctas": int(stats[4]), "bytes": float(stats[5]),
             "cta_s": {name: float(stats[6 + k]) for k, name in
                       [(1, "select"), (2, "gather"), (3, "update"), (4, "step"), (5, "density"), (6, "v"),
-                       (7, "jp"), (8, "j_unpack"), (10, "eri"), (13, "b"), (14, "k_tiles"), (15, "k_sum")]},
+                       (7, "jp"), (8, "j_unpack"), (9, "slice"), (10, "eri"), (13, "b"), (14, "k_tiles"),
+                       (15, "k_sum")]},
             "idle_cta_s": float(stats[22]),
             "fp64_ops": {name: float(stats[23 + k]) for k, name in
                          [(3, "update"), (4, "step"), (6, "v"), (7, "jp"), (10, "eri"), (13, "b"),

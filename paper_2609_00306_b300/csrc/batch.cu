@@ -46,12 +46,17 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
 #include <vector>
+#include <cuda_bf16.h>
 #include "internal.cuh"
 #include "eri_dev.cuh"
+#include "ozaki.cuh"
+#include "tc.cuh"
 
 namespace cd {
 unsigned long long device_wait_limit_ns();  // ozaki.cu (cd_set_wait_limit)
@@ -67,9 +72,19 @@ constexpr int kJvVec = 4;         // vectors per JV item
 constexpr int kKtSplit = 128;     // vectors per partial K tile
 constexpr int kKt = 64;           // K tile edge
 constexpr int kTieCap = 1024;     // tie-bin entries ranked directly by SELECT
-constexpr int kSmemBytes = 32768;
+constexpr int kSmemBytes = 32768;     // scratch of the FP64 items
+// exact-slice update items (tcgen05): A = 7 BF16 slices of 128 rows x 32 vectors,
+// B = 7 slices of 32 columns x 32 vectors, 64-byte swizzled rows
+constexpr int kTcSlices = 7, kTcBN = 32, kTcBK = 32;
+constexpr int kTcABytes = kTcSlices * 128 * kTcBK * 2;    // 57,344
+constexpr int kTcBBytes = kTcSlices * kTcBN * kTcBK * 2;  // 14,336
+constexpr int kTcF = 60;          // fixed-point fraction bits of the update sums
+constexpr int kTcChunk = 4;       // k-blocks per drain: 7 products x 128 k x 129^2 < 2^24 (exact FP32 sums)
+constexpr int kTcTmemCols = 256;  // 7 accumulator groups x 32 columns = 224 used
+constexpr int kDynSmem = (kTcABytes + kTcBBytes > kSmemBytes ? kTcABytes + kTcBBytes : kSmemBytes) + 1024;
 
 enum JobType : int { kJobNone = 0, kJobSelect, kJobCols, kJobUpdate, kJobStep, kJobJk1, kJobJk2, kJobJk3, kJobJk4,
+                     kJobSlice = 9 /* tensor-core mode: the finished block's vectors into the slice store */,
                      kJobConverged = 100 /* pseudo job: the decomposition has converged */ };
 
 __host__ __device__ constexpr unsigned long long job_word(unsigned gen, unsigned count, unsigned next) {
@@ -93,6 +108,7 @@ struct SysState {
   int cur;                   // D[cur] is the current residual diagonal
   int pslot;                 // pool slot of the current pivot
   int converged;             // SELECT found max D < tau
+  int after_slice;           // job after a SLICE job: kJobSelect or kJobConverged
   int ngroups;               // ERI ket groups of the block
   int64_t K, Kb;             // vectors done; first vector of the current block
   int64_t prow;              // pivot row of the current step
@@ -109,6 +125,8 @@ struct SysState {
   int64_t slot_valid[kBMaxB];// vectors [0, slot_valid) are applied to the slot's column
 };
 
+static_assert(sizeof(KetGroup) % 16 == 0, "ket groups are copied in 16-byte words");
+
 // Immutable per-system descriptor (device; copied to shared memory per item).
 struct __align__(16) SysDesc {
   int64_t n, ld, Mcap;
@@ -118,6 +136,11 @@ struct __align__(16) SysDesc {
   int64_t cls[4], all_cls[4];
   int ntile[3], nsplit_cap;
   int64_t nnz;                      // entries of the row lists (2 n minus the diagonal pairs)
+  int tc;                           // column update: 1 = exact 7-slice BF16 products on the tensor cores, 0 = DFMA
+  int pad0;
+  const int32_t* erow;              // [n] row exponents: |L^K_r| <= sqrt(D^1_r) < 2^erow[r]
+  __nv_bfloat16* Bsl;               // [2][7][64][bpitch] slices of the gathered pivot rows (tc)
+  int64_t bpitch;
   const int32_t* row_allsp;         // [n] shell pair (in ket) of each row
   const int8_t* row_kc;             // [n] canonical components of each row
   const int8_t* row_kd;
@@ -126,11 +149,13 @@ struct __align__(16) SysDesc {
   const int32_t* csr_off;           // [N+1] row list per basis function mu:
   const int32_t* csr_nu;            //   partner nu and row r of every screened pair (mu nu)
   const int32_t* csr_row;
-  const double* C;                  // [N][O] occupied coefficients
+  const double* C;                  // [N][Op] occupied coefficients (rows zero-padded to Op)
   double* D0;                       // [ld] residual diagonals (double buffered)
   double* D1;
   double* pool;                     // [b][ld] candidate columns
-  double* L;                        // [Mcap][ld] vectors
+  double* L;                        // [Mcap][ld] vectors (DFMA mode; NULL with tc)
+  __nv_bfloat16* Ls;                // tc: vectors as 7 BF16 slices, [ceil(Mcap/32)][7][n][32] (zeroed)
+  double* Lblk;                     // tc: the current block's vectors in FP64, [kBMaxB][ld]
   int64_t* piv;                     // [Mcap] pivot rows
   double* pivd;                     // [Mcap] their residual diagonals
   double* Bg0;                      // [Mcap][b] gathered pivot rows (new slots)
@@ -153,12 +178,13 @@ struct BatchCtl {
   unsigned done_sys;            // systems finished (converged or failed)
   int abort;                    // stop claiming work
   int timed_out;                // a CTA's wait for work ran out
-  int pad;
+  int tc_err;                   // a bounded tensor-core (MMA completion) wait gave up
   unsigned long long progress;  // items completed, all systems
   unsigned long long kind_ns[kJobKinds];     // CTA time per item kind (incl. its job finish)
   unsigned long long kind_items[kJobKinds];  // items per kind
   unsigned long long kind_ops[kJobKinds];    // FP64-pipe operations per kind (one per FMA; ERI: executed)
   unsigned long long idle_ns;                // CTA time spent looking for work
+  unsigned long long tc_ns[4];               // tensor-core update items: operand copies, MMA issue + wait, drain, result
 };
 
 // ------------------------------------------------------------ helpers ----
@@ -452,8 +478,12 @@ __device__ void select_item(const SysDesc& d, unsigned char* smem, Red* red, int
     }
     st->ngroups = ng;
     st->Kb = K;
-    st->gitems[0] = st->nb[0] > 0 ? (int)ceil_div(K - st->k0[0], kGatherQ) : 0;
-    st->gitems[1] = st->nb[1] > 0 ? (int)ceil_div(K - st->k0[1], kGatherQ) : 0;
+    for (int g = 0; g < 2; ++g) {
+      // DFMA: vectors [k0, K); tensor cores: the whole 32-vector blocks that hold them
+      const int64_t lo = d.tc ? st->k0[g] / kTcBK * kTcBK : st->k0[g];
+      const int64_t hi = d.tc ? (K + kTcBK - 1) / kTcBK * kTcBK : K;
+      st->gitems[g] = st->nb[g] > 0 ? (int)ceil_div(hi - lo, kGatherQ) : 0;
+    }
     int64_t neri = 0;
     for (int c = 0; c < 3; ++c) neri += (int64_t)d.ntile[c] * ng;
     st->nitems[0] = st->gitems[0] + st->gitems[1];
@@ -479,6 +509,179 @@ __device__ void gather_item(const SysDesc& d, unsigned it) {
     const int64_t row = vload(&st->urow[g][j]);
     Bg[(q - k0) * nb + j] = __ldcg(d.L + q * d.ld + row);
   }
+}
+
+// 16-byte global -> shared copy that bypasses registers (src_bytes = 0: zero fill)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(sdst)), "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// element (q, r) of slice t in the chunked slice store
+__device__ __forceinline__ int64_t ls_index(int64_t n, int64_t q, int t, int64_t r) {
+  return (((q / kTcBK) * kTcSlices + t) * n + r) * kTcBK + q % kTcBK;
+}
+
+// Slices of the gathered pivot rows for the tensor-core update: group g, column
+// j, vector q in the 32-vector blocks covering [k0, K): the 7 slices of
+// L[q][row_j] from the slice store (zero outside [k0, K)), Bsl[g][s][j][q - kbase].
+__device__ void gather_tc_item(const SysDesc& d, unsigned it) {
+  SysState* st = d.st;
+  const int g0 = vload(&st->gitems[0]);
+  const int g = (int)it < g0 ? 0 : 1;
+  const unsigned chunk = g == 0 ? it : it - g0;
+  const int nb = vload(&st->nb[g]);
+  const int64_t k0 = vload(&st->k0[g]), K = vload(&st->K);
+  const int64_t kbase = k0 / kTcBK * kTcBK, kpad = (K + kTcBK - 1) / kTcBK * kTcBK;
+  const int64_t q0 = kbase + (int64_t)chunk * kGatherQ;
+  const int64_t nq = min(kpad, q0 + kGatherQ) - q0;
+  __nv_bfloat16* B = d.Bsl + (int64_t)g * kTcSlices * 64 * d.bpitch;
+  const int64_t tot = nq * nb;
+  for (int64_t e = threadIdx.x; e < tot; e += kBT) {
+    const int j = (int)(e / nq);
+    const int64_t q = q0 + e % nq;
+    const int64_t row = vload(&st->urow[g][j]);
+    const bool in = q >= k0 && q < K;
+#pragma unroll
+    for (int t = 0; t < kTcSlices; ++t)
+      B[((int64_t)t * 64 + j) * d.bpitch + (q - kbase)] =
+          in ? __ldcg(d.Ls + ls_index(d.n, q, t, row)) : __float2bfloat16_rn(0.0f);
+  }
+}
+
+// Column update on the tensor cores, exact 7-slice products (the same
+// arithmetic as the single-system sliced update): 128 rows x 32 columns of one
+// update group over its vectors [k0, K).  Per block of 32 vectors every thread
+// copies its row of the 7 slice planes into A (64-byte swizzled rows: the
+// 16-byte chunk c of row r sits at chunk c ^ ((r >> 1) & 3)), the CTA copies
+// the 32 columns' slices into B, and thread 0 issues one MMA per A slice s
+// against the stacked B slices 0..6-s (N = 32 (7 - s)), so that the product
+// (s, t) lands in accumulator group s + t.  Every 4 blocks the 7 groups are
+// drained from tensor memory into 64-bit fixed-point sums (thread = row); at
+// the end col -= 2^(e_r + e_c - 60) * sum.
+__device__ bool update_tc_item(const SysDesc& d, unsigned it, unsigned char* smem, uint32_t tmem, uint64_t* mbar,
+                               uint32_t& mphase, int* s_fail, BatchCtl* ctl, long long wait_ns) {
+  SysState* st = d.st;
+  const int n0 = vload(&st->nitems[0]);
+  const int g = (int)it < n0 ? 0 : 1;
+  const int64_t li = g == 0 ? it : it - n0;
+  const int nb = vload(&st->nb[g]);
+  const int ctn = (nb + kTcBN - 1) / kTcBN;
+  const int64_t rt = li / ctn;
+  const int ct = (int)(li % ctn);
+  const int64_t k0 = vload(&st->k0[g]), K = vload(&st->K);
+  const int64_t n = d.n, ld = d.ld, r0 = rt * 128;
+  const int tid = threadIdx.x, w = tid >> 5;
+  const int64_t r = r0 + tid;
+  const int er = r < n ? __ldg(d.erow + r) : 0;
+  const int kb0 = (int)(k0 / kTcBK), kb1 = (int)((K + kTcBK - 1) / kTcBK);
+  (void)ld;
+  const int64_t kbase = (int64_t)kb0 * kTcBK;
+  unsigned char* A = smem;
+  unsigned char* Bm = smem + kTcABytes;
+  const __nv_bfloat16* Bg = d.Bsl + (int64_t)g * kTcSlices * 64 * d.bpitch;
+  const int sw = (tid >> 1) & 3;
+  long long run[kTcBN];
+#pragma unroll
+  for (int c = 0; c < kTcBN; ++c) run[c] = 0;
+  if (tid == 0) *s_fail = 0;
+  long long tt[4] = {0, 0, 0, 0};
+  long long tprev = tid == 0 ? globaltimer_ns() : 0;
+  auto mark = [&](int k) {
+    if (tid == 0) {
+      const long long t = globaltimer_ns();
+      tt[k] += t - tprev;
+      tprev = t;
+    }
+  };
+  for (int kb = kb0; kb < kb1; kb += kTcChunk) {
+    const int kbe = min(kb1, kb + kTcChunk);
+    for (int b = kb; b < kbe; ++b) {
+      // A: this thread's row of the 7 slice planes of vector block b (64 bytes each),
+      // B: 7 slices x 32 columns x 32 vectors of the gathered slices; all copies
+      // in flight at once (cp.async), rows past n and columns past nb zero-filled
+#pragma unroll
+      for (int t = 0; t < kTcSlices; ++t) {
+        const __nv_bfloat16* src = d.Ls + (((int64_t)b * kTcSlices + t) * n + (r < n ? r : 0)) * kTcBK;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          cp_async16(A + t * (128 * 64) + tid * 64 + ((c ^ sw) * 16), src + c * 8, r < n ? 16 : 0);
+      }
+      for (int t = tid; t < kTcSlices * kTcBN * 4; t += kBT) {
+        const int sl = t / (kTcBN * 4), jj = (t / 4) % kTcBN, c = t % 4;
+        const int j = ct * kTcBN + jj;
+        const __nv_bfloat16* src = Bg + ((int64_t)sl * 64 + (j < nb ? j : 0)) * d.bpitch + ((int64_t)b * kTcBK - kbase) + c * 8;
+        cp_async16(Bm + sl * (kTcBN * 64) + jj * 64 + ((c ^ ((jj >> 1) & 3)) * 16), src, j < nb ? 16 : 0);
+      }
+      cp_async_wait_all();
+      tc::fence_proxy_async();
+      __syncthreads();
+      mark(0);
+      if (tid == 0) {
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(Bm);
+#pragma unroll
+        for (int sa = 0; sa < kTcSlices; ++sa) {
+          const int nt = kTcSlices - sa;
+          const uint32_t idesc = tc::idesc_bf16_f32_n(128, nt * kTcBN);
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 16; ++kk)
+            tc::umma_bf16(tmem + (uint32_t)(sa * kTcBN), sdesc_k_sw64(a0 + sa * (128 * 64) + kk * 32),
+                          sdesc_k_sw64(b0 + kk * 32), idesc, (b == kb && sa == 0 && kk == 0) ? 0u : 1u);
+        }
+        tc::umma_commit(mbar);
+      }
+      if (tid == 0) {
+        volatile int ab = 0;
+        if (!tc::mbar_wait(mbar, mphase, &ab, &ctl->tc_err, 1, (unsigned long long)wait_ns)) {
+          tc::mbar_settle(mbar, mphase);
+          *s_fail = 1;
+          atomicExch(&ctl->abort, 1);
+        }
+        mphase ^= 1u;
+      }
+      __syncthreads();
+      mark(1);
+      if (*(volatile int*)s_fail) return false;
+    }
+    // drain the 7 groups into the fixed-point sums (thread = TMEM lane = tile row)
+    tc::tc_fence_after();
+    const uint32_t acc = tmem + ((uint32_t)(w * 32) << 16);
+#pragma unroll
+    for (int gq = 0; gq < kTcSlices; ++gq) {
+      const int sh = kTcF - 8 * (gq + 2) + 2;
+#pragma unroll
+      for (int cb = 0; cb < kTcBN / 16; ++cb) {
+        uint32_t v[16];
+        tc::tmem_ld16(acc + (uint32_t)(gq * kTcBN + cb * 16), v);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const long long iv = exact_float_to_ll(__uint_as_float(v[c]));
+          run[cb * 16 + c] += sh >= 0 ? (iv << sh) : ((iv + (1ll << (-sh - 1))) >> (-sh));
+        }
+      }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    mark(2);
+  }
+  if (r < n) {
+#pragma unroll
+    for (int c = 0; c < kTcBN; ++c) {
+      const int j = ct * kTcBN + c;
+      if (j >= nb) continue;
+      double* col = d.pool + (int64_t)vload(&st->uslot[g][j]) * ld;
+      const int ec = __ldg(d.erow + vload(&st->urow[g][j]));
+      col[r] = __ldcg(col + r) - ldexp((double)run[c], er + ec - kTcF);
+    }
+  }
+  __syncthreads();
+  mark(3);
+  if (tid == 0)
+    for (int k = 0; k < 4; ++k) atomicAdd(&ctl->tc_ns[k], (unsigned long long)tt[k]);
+  return true;
 }
 
 __device__ void eri_item(const SysDesc& d, unsigned it, const double* boys, KetGroup* sg,
@@ -596,7 +799,9 @@ __device__ void step_item(const SysDesc& d, unsigned it, unsigned char* smem, Re
   const int64_t n = d.n, ld = d.ld;
   double* g = (double*)smem;
   const int nk = (int)(K - Kb);
-  for (int k = threadIdx.x; k < nk; k += kBT) g[k] = __ldcg(d.L + (Kb + k) * ld + prow);
+  // the block's earlier vectors: rows Kb.. of L, or the FP64 block buffer (tensor-core mode)
+  const double* Lb = d.tc ? d.Lblk : d.L + Kb * ld;
+  for (int k = threadIdx.x; k < nk; k += kBT) g[k] = __ldcg(Lb + k * ld + prow);
   __syncthreads();
   const int64_t r0 = (int64_t)it * kStepRows + threadIdx.x;
   constexpr int R = kStepRows / kBT;
@@ -609,7 +814,7 @@ __device__ void step_item(const SysDesc& d, unsigned it, unsigned char* smem, Re
   }
   for (int k = 0; k < nk; ++k) {
     const double gk = g[k];
-    const double* Lk = d.L + (Kb + k) * ld;
+    const double* Lk = Lb + k * ld;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int64_t r = r0 + (int64_t)j * kBT;
@@ -619,7 +824,7 @@ __device__ void step_item(const SysDesc& d, unsigned it, unsigned char* smem, Re
   const double inv = 1.0 / sqrt(dp);
   const double* Din = dcur(d, cur);
   double* Dout = dnext(d, cur);
-  double* Lout = d.L + K * ld;
+  double* Lout = d.tc ? d.Lblk + (K - Kb) * ld : d.L + K * ld;
   double bv = -1.0e300;
   int64_t bi = INT64_MAX;
   int bad = 0;
@@ -643,14 +848,65 @@ __device__ void step_item(const SysDesc& d, unsigned it, unsigned char* smem, Re
   }
 }
 
+// ---------------------------------------------------------------- SLICE ----
+// Tensor-core mode, after a block: its vectors [Kb, K) (FP64 block buffer) as
+// 7 BF16 slices in the store, round(L 2^(55 - e_r)) in balanced base-256 digits
+// (the representation of the single-system sliced update), 1024 rows per item,
+// 8 vectors per 16-byte store (partial groups keep the neighbouring blocks' values).
+__device__ void slice_item(const SysDesc& d, unsigned it) {
+  const SysState* st = d.st;
+  const int64_t K = vload(&st->K), Kb = vload(&st->Kb), n = d.n;
+  const int64_t r0 = (int64_t)it * kStepRows;
+  for (int64_t r = r0 + threadIdx.x; r < min(n, r0 + kStepRows); r += kBT) {
+    const int er = __ldg(d.erow + r);
+    for (int64_t q8 = Kb / 8 * 8; q8 < K; q8 += 8) {
+      unsigned short h[kTcSlices][8];
+      const bool full = q8 >= Kb && q8 + 8 <= K;
+      if (!full) {
+#pragma unroll
+        for (int t = 0; t < kTcSlices; ++t) {
+          const uint4 v = __ldcg((const uint4*)(d.Ls + ls_index(n, q8, t, r)));
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            h[t][2 * m] = (unsigned short)(w[m] & 0xffffu);
+            h[t][2 * m + 1] = (unsigned short)(w[m] >> 16);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int64_t q = q8 + e;
+        if (q < Kb || q >= K) continue;
+        float a[kTcSlices];
+        fixed_digits<kTcSlices>(scaled_double_to_ll(__ldcg(d.Lblk + (q - Kb) * d.ld + r), 8 * kTcSlices - 1 - er), a);
+#pragma unroll
+        for (int t = 0; t < kTcSlices; ++t) {
+          const __nv_bfloat16 bv = __float2bfloat16_rn(a[t]);
+          h[t][e] = *(const unsigned short*)&bv;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kTcSlices; ++t) {
+        uint4 v;
+        v.x = (uint32_t)h[t][0] | ((uint32_t)h[t][1] << 16);
+        v.y = (uint32_t)h[t][2] | ((uint32_t)h[t][3] << 16);
+        v.z = (uint32_t)h[t][4] | ((uint32_t)h[t][5] << 16);
+        v.w = (uint32_t)h[t][6] | ((uint32_t)h[t][7] << 16);
+        *(uint4*)(d.Ls + ls_index(n, q8, t, r)) = v;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------- JK ----
 // d_r = D_{mu nu} (2 - delta_{mu nu}), D = 2 C C^T
 __device__ void dens_item(const SysDesc& d, unsigned it) {
   const int64_t r0 = (int64_t)it * kStepRows;
   for (int64_t r = r0 + threadIdx.x; r < min(d.n, r0 + kStepRows); r += kBT) {
     const int mu = __ldg(d.row_mu + r), nu = __ldg(d.row_nu + r);
-    const double* cm = d.C + (int64_t)mu * d.O;
-    const double* cn = d.C + (int64_t)nu * d.O;
+    const double* cm = d.C + (int64_t)mu * d.Op;
+    const double* cn = d.C + (int64_t)nu * d.Op;
     double s = 0.0;
     for (int i = 0; i < d.O; ++i) s = fma(__ldg(cm + i), __ldg(cn + i), s);
     d.dpk[r] = 2.0 * s * (mu == nu ? 1.0 : 2.0);
@@ -660,7 +916,7 @@ __device__ void dens_item(const SysDesc& d, unsigned it) {
 // B^P[mu][i] = sum_nu L^P_{mu nu} C[nu][i] for one vector P (warp per mu, lanes over i)
 __device__ void kb_item(const SysDesc& d, unsigned P) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const double* Lp = d.L + (int64_t)P * d.ld;
+  const double* Lp = d.L + (int64_t)P * d.ld;   // DFMA mode (the slice store has kb_tc_item)
   double* Bp = d.B + (int64_t)P * d.N * d.Op;
   for (int mu = w; mu < d.N; mu += kBT / 32) {
     const int e0 = __ldg(d.csr_off + mu), e1 = __ldg(d.csr_off + mu + 1);
@@ -670,9 +926,50 @@ __device__ void kb_item(const SysDesc& d, unsigned P) {
       if (i < d.O)
         for (int e = e0; e < e1; ++e) {
           const double l = __ldcg(Lp + __ldg(d.csr_row + e));
-          s = fma(l, __ldg(d.C + (int64_t)__ldg(d.csr_nu + e) * d.O + i), s);
+          s = fma(l, __ldg(d.C + (int64_t)__ldg(d.csr_nu + e) * d.Op + i), s);
         }
       if (i < d.Op) Bp[(int64_t)mu * d.Op + i] = s;
+    }
+  }
+}
+
+// tensor-core mode: B^P[mu][i] = sum_nu L^P_{mu nu} C[nu][i] for the 32 vectors
+// of slice chunk c (lane = vector: each row's 7 slice rows are read as 64-byte
+// rows across the warp) and 8 basis functions mu (2 per warp), i in passes of 24
+__device__ void kb_tc_item(const SysDesc& d, unsigned it, int64_t M) {
+  const int nmu = (d.N + 7) / 8;
+  const int64_t c = it / nmu;
+  const int mb = (int)(it % nmu);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t P = c * 32 + lane;
+  for (int mu = mb * 8 + w; mu < min(d.N, mb * 8 + 8); mu += kBT / 32) {
+    const int e0 = __ldg(d.csr_off + mu), e1 = __ldg(d.csr_off + mu + 1);
+    for (int i0 = 0; i0 < d.Op; i0 += 24) {
+      double acc[24];
+#pragma unroll
+      for (int q = 0; q < 24; ++q) acc[q] = 0.0;
+      for (int e = e0; e < e1; ++e) {
+        const int32_t row = __ldg(d.csr_row + e), nu = __ldg(d.csr_nu + e);
+        long long v = 0;
+#pragma unroll
+        for (int t = 0; t < kTcSlices; ++t)
+          v = v * 256 + (long long)(int)__bfloat162float(__ldcg(d.Ls + ((c * kTcSlices + t) * d.n + row) * kTcBK + lane));
+        const double x = ldexp((double)v, __ldg(d.erow + row) - (8 * kTcSlices - 1));
+        // C rows are zero-padded to Op (a multiple of 8), so 24 columns from i0 are in the row
+        const double2* cr = (const double2*)(d.C + (int64_t)nu * d.Op + i0);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          const double2 c2 = __ldg(cr + q);
+          acc[2 * q] = fma(x, c2.x, acc[2 * q]);
+          acc[2 * q + 1] = fma(x, c2.y, acc[2 * q + 1]);
+        }
+      }
+      if (P < M) {
+        double* Bp = d.B + ((int64_t)P * d.N + mu) * d.Op + i0;
+#pragma unroll
+        for (int q = 0; q < 24; ++q)
+          if (i0 + q < d.Op) Bp[q] = acc[q];
+      }
     }
   }
 }
@@ -687,6 +984,87 @@ __device__ void jv_item(const SysDesc& d, unsigned it, int64_t M, Red* red) {
     for (int64_t r = threadIdx.x; r < d.n; r += kBT) s = fma(__ldcg(Lp + r), __ldcg(d.dpk + r), s);
     s = cta_sum(s, red->v);
     if (threadIdx.x == 0) d.v[P] = s;
+  }
+}
+
+// the 8 integers round(L^P_r 2^(55 - e_r)) of vectors 32 c + 8 g8 .. + 7 of row r
+__device__ __forceinline__ void ls_ints8(const __nv_bfloat16* __restrict__ Ls, int64_t n, int64_t c, int g8, int64_t r,
+                                         long long (&v)[8]) {
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = 0;
+#pragma unroll
+  for (int t = 0; t < kTcSlices; ++t) {
+    const uint4 w4 = __ldcg((const uint4*)(Ls + ((c * kTcSlices + t) * n + r) * kTcBK + g8 * 8));
+    const uint32_t w[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const unsigned short lo = (unsigned short)(w[m] & 0xffffu), hi = (unsigned short)(w[m] >> 16);
+      v[2 * m] = v[2 * m] * 256 + (long long)(int)__bfloat162float(*(const __nv_bfloat16*)&lo);
+      v[2 * m + 1] = v[2 * m + 1] * 256 + (long long)(int)__bfloat162float(*(const __nv_bfloat16*)&hi);
+    }
+  }
+}
+
+// tensor-core mode: v_P = sum_r L^P_r d_r for the 32 vectors of slice chunk `it`
+// (every row's 7 x 64-byte slice rows read once), reduced over the CTA in shared memory
+__device__ void jv_tc_item(const SysDesc& d, unsigned it, int64_t M, unsigned char* smem) {
+  double acc[32];
+#pragma unroll
+  for (int e = 0; e < 32; ++e) acc[e] = 0.0;
+  for (int64_t r = threadIdx.x; r < d.n; r += kBT) {
+    const double sc = ldexp(__ldcg(d.dpk + r), __ldg(d.erow + r) - (8 * kTcSlices - 1));
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+      long long v[8];
+      ls_ints8(d.Ls, d.n, it, g8, r, v);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[g8 * 8 + e] = fma((double)v[e], sc, acc[g8 * 8 + e]);
+    }
+  }
+  double* red = (double*)smem;   // [32][kBT]
+#pragma unroll
+  for (int e = 0; e < 32; ++e) red[e * kBT + threadIdx.x] = acc[e];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int64_t P = (int64_t)it * 32 + threadIdx.x;
+    double sum = 0.0;
+    for (int k = 0; k < kBT; ++k) sum += red[threadIdx.x * kBT + k];
+    if (P < M) d.v[P] = sum;
+  }
+}
+
+// tensor-core mode: J_r = sum_P L^P_r v_P for 1024 rows from the slice store
+__device__ void jp_tc_item(const SysDesc& d, unsigned it, int64_t M, unsigned char* smem) {
+  double* vs = (double*)smem;   // [1024]
+  const int64_t r0 = (int64_t)it * kStepRows + threadIdx.x;
+  constexpr int R = kStepRows / kBT;
+  double acc[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) acc[j] = 0.0;
+  for (int64_t P0 = 0; P0 < M; P0 += 1024) {
+    const int np = (int)min((int64_t)1024, M - P0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < 1024; k += kBT) vs[k] = k < np ? __ldcg(d.v + P0 + k) : 0.0;
+    __syncthreads();
+    for (int c = 0; c < (np + 31) / 32; ++c) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t r = r0 + (int64_t)j * kBT;
+        if (r >= d.n) continue;
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          long long v[8];
+          ls_ints8(d.Ls, d.n, P0 / 32 + c, g8, r, v);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[j] = fma((double)v[e], vs[c * 32 + g8 * 8 + e], acc[j]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int64_t r = r0 + (int64_t)j * kBT;
+    if (r < d.n) d.Jp[r] = ldexp(acc[j], __ldg(d.erow + r) - (8 * kTcSlices - 1));
   }
 }
 
@@ -845,8 +1223,10 @@ __device__ void advance(const SysDesc& d, int type, BatchCtl* ctl) {
       }
       case kJobCols: {
         const unsigned t = ceil_div(d.n, kRowTile);
-        st->nitems[0] = (st->nb[0] > 0 && K > st->k0[0]) ? (int)t : 0;
-        st->nitems[1] = (st->nb[1] > 0 && K > st->k0[1]) ? (int)t : 0;
+        for (int g = 0; g < 2; ++g) {
+          const int ctn = d.tc ? (st->nb[g] + kTcBN - 1) / kTcBN : 1;   // tensor cores: 32-column tiles
+          st->nitems[g] = (st->nb[g] > 0 && K > st->k0[g]) ? (int)t * ctn : 0;
+        }
         const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
         if (c > 0) { publish(st, kJobUpdate, c); return; }
         type = kJobUpdate;
@@ -869,7 +1249,7 @@ __device__ void advance(const SysDesc& d, int type, BatchCtl* ctl) {
       case kJobConverged: {   // J/K build
         const int64_t M = K;
         st->nitems[0] = (int)nrow;
-        st->nitems[1] = (int)M;
+        st->nitems[1] = d.tc ? (int)(ceil_div(M, 32) * ((d.N + 7) / 8)) : (int)M;
         const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
         if (c > 0) { publish(st, kJobJk1, c); return; }
         type = kJobJk1;
@@ -878,7 +1258,7 @@ __device__ void advance(const SysDesc& d, int type, BatchCtl* ctl) {
       case kJobJk1: {
         const int64_t M = K;
         const int nsplit = (int)ceil_div(M, kKtSplit);
-        st->nitems[0] = (int)ceil_div(M, kJvVec);
+        st->nitems[0] = (int)ceil_div(M, d.tc ? 32 : kJvVec);
         st->nitems[1] = nsplit * ntiles_k(d.N);
         const unsigned c = (unsigned)(st->nitems[0] + st->nitems[1]);
         if (c > 0) { publish(st, kJobJk2, c); return; }
@@ -899,6 +1279,10 @@ __device__ void advance(const SysDesc& d, int type, BatchCtl* ctl) {
       case kJobJk4:
         end_system(st, ctl, CD_OK);
         return;
+      case kJobSlice:
+        if (st->after_slice == kJobSelect) { publish(st, kJobSelect, 1); return; }
+        type = kJobConverged;
+        break;
       default:
         end_system(st, ctl, CD_EINVAL);
         return;
@@ -931,12 +1315,20 @@ __device__ void finish_step(const SysDesc& d, BatchCtl* ctl, Red* red) {
   const int bad = st->bad;
   st->bad = 0;
   if (bad) { end_system(st, ctl, CD_ENOTPSD); return; }
-  if (!(bv >= d.tau)) { advance(d, kJobConverged, ctl); return; }
+  if (!(bv >= d.tau)) {
+    if (d.tc) { st->after_slice = kJobConverged; publish(st, kJobSlice, nit); }
+    else advance(d, kJobConverged, ctl);
+    return;
+  }
   if (K + 1 >= d.Mcap) { end_system(st, ctl, CD_ENOMEM); return; }
   int slot = -1;
   for (int s = 0; s < d.b; ++s)
     if (st->slot_row[s] == bi) slot = s;
-  if (slot < 0) { publish(st, kJobSelect, 1); return; }
+  if (slot < 0) {
+    if (d.tc) { st->after_slice = kJobSelect; publish(st, kJobSlice, nit); }
+    else publish(st, kJobSelect, 1);
+    return;
+  }
   const double dp = __ldcg(dcur(d, st->cur) + bi);
   if (!(dp > 0.0)) { end_system(st, ctl, CD_ENOTPSD); return; }
   st->prow = bi;
@@ -953,15 +1345,31 @@ __device__ unsigned long long item_work(const SysDesc& d, int type, int kind, un
   if (type == kJobUpdate) {
     const int n0 = vload(&st->nitems[0]);
     const int g = (int)it < n0 ? 0 : 1;
-    const int64_t tile = g == 0 ? it : it - n0;
+    const int64_t li = g == 0 ? it : it - n0;
+    const int nb = vload(&st->nb[g]);
+    int64_t tile = li, cols = nb;
+    if (d.tc) {
+      const int ctn = (nb + kTcBN - 1) / kTcBN;
+      tile = li / ctn;
+      cols = min((int64_t)kTcBN, (int64_t)nb - (li % ctn) * kTcBN);
+    }
     const int64_t rows = min((int64_t)kRowTile, d.n - tile * kRowTile);
-    return (unsigned long long)(rows * vload(&st->nb[g]) * (K - vload(&st->k0[g])));
+    return (unsigned long long)(rows * cols * (K - vload(&st->k0[g])));
   }
   if (type == kJobStep) {
     const int64_t rows = min((int64_t)kStepRows, d.n - (int64_t)it * kStepRows);
     return (unsigned long long)(rows * (K - vload(&st->Kb) + 1));
   }
   if (kind == kJobJk1 + 8) {   // B^P = L^P C: every screened pair twice (mu nu and nu mu), O each
+    if (d.tc) {
+      const unsigned j = it - (unsigned)vload(&st->nitems[0]);
+      const int nmu = (d.N + 7) / 8;
+      const int64_t c = j / nmu;
+      const int mb = (int)(j % nmu);
+      const int64_t nv = min((int64_t)32, K - c * 32);
+      const int64_t deg = __ldg(d.csr_off + min(d.N, mb * 8 + 8)) - __ldg(d.csr_off + mb * 8);
+      return (unsigned long long)(nv * deg * d.O);
+    }
     return (unsigned long long)d.nnz * (unsigned long long)d.O;
   }
   if (kind == kJobJk2 + 8) {   // partial K tile: tile elements x vectors x O
@@ -974,7 +1382,8 @@ __device__ unsigned long long item_work(const SysDesc& d, int type, int kind, un
     return (unsigned long long)(nm * nn * np * d.O);
   }
   if (kind == kJobJk2) {       // v = L d
-    const int64_t nv = min((int64_t)kJvVec, K - (int64_t)it * kJvVec);
+    const int64_t per = d.tc ? 32 : kJvVec;
+    const int64_t nv = min(per, K - (int64_t)it * per);
     return (unsigned long long)(nv * d.n);
   }
   if (kind == kJobJk3) {       // J_p = L^T v
@@ -985,18 +1394,43 @@ __device__ unsigned long long item_work(const SysDesc& d, int type, int kind, un
 }
 
 // ---------------------------------------------------------------- kernel ----
+// TC = true: the build with the tensor-core update items.  A kernel that contains
+// tcgen05 instructions is resident at one CTA per SM, so the FP64-only build
+// (TC = false, two CTAs per SM) serves batches whose systems all use the DFMA update.
+template <bool TC>
 __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict__ sys, int n_sys, BatchCtl* ctl,
                                                        const double* __restrict__ boys, long long wait_ns) {
-  __shared__ __align__(16) unsigned char smem[kSmemBytes];
+  constexpr int use_tc = TC ? 1 : 0;
+  // item scratch (dynamic, 1024-byte aligned for the swizzled tensor-core operands)
+  extern __shared__ __align__(1024) unsigned char dsmem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)dsmem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ SysDesc sd;
+  __shared__ __align__(8) uint64_t s_mbar;   // MMA completion of the tensor-core update items
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_tcfail;
   __shared__ Red red;
-  __shared__ KetGroup sg;
+  __shared__ __align__(16) KetGroup sg;   // filled with 16-byte copies
   __shared__ int64_t s_cand[kBMaxB + kBT];
   __shared__ int s_int[8];
   __shared__ int s_sys, s_last, s_type;
   __shared__ unsigned s_item, s_count;
   long long idle_since = -1, last_idle = 0;
   unsigned long long seen = 0;
+  uint32_t mphase = 0;   // thread 0: parity of the next MMA-completion phase
+  // tensor memory for the update accumulators: 256 columns per CTA (two CTAs per SM),
+  // held for the whole launch
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&s_mbar, 1);
+    tc::fence_mbar_init();
+    s_tcfail = 0;
+  }
+  if constexpr (TC) {
+    if (threadIdx.x < 32) tc::tmem_alloc<kTcTmemCols>(&s_tmem);
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  if constexpr (TC) tc::tc_fence_after();
+  const uint32_t tmem = use_tc ? s_tmem : 0u;
   for (;;) {
     if (threadIdx.x < 32) {
       const int lane = threadIdx.x;
@@ -1074,28 +1508,46 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict
     switch (type) {
       case kJobSelect: select_item(sd, smem, &red, s_cand, s_int); break;
       case kJobCols:
-        if ((int)it < vload(&st->nitems[0])) gather_item(sd, it);
+        if ((int)it < vload(&st->nitems[0])) {
+          if (sd.tc) gather_tc_item(sd, it);
+          else gather_item(sd, it);
+        }
         else eri_item(sd, it, boys, &sg, &ctl->kind_ops[kJobCols + 8]);
         break;
-      case kJobUpdate: update_item(sd, it, smem); break;
+      case kJobUpdate:
+        if constexpr (TC) {
+          if (sd.tc) update_tc_item(sd, it, smem, tmem, &s_mbar, mphase, &s_tcfail, ctl, wait_ns);
+          else update_item(sd, it, smem);
+        } else {
+          update_item(sd, it, smem);
+        }
+        break;
       case kJobStep: step_item(sd, it, smem, &red); break;
       case kJobJk1:
         if ((int)it < vload(&st->nitems[0])) dens_item(sd, it);
+        else if (sd.tc) kb_tc_item(sd, it - (unsigned)vload(&st->nitems[0]), vload(&st->K));
         else kb_item(sd, it - (unsigned)vload(&st->nitems[0]));
         break;
       case kJobJk2: {
         const int n0 = vload(&st->nitems[0]);
-        if ((int)it < n0) jv_item(sd, it, vload(&st->K), &red);
+        if ((int)it < n0) {
+          if (sd.tc) jv_tc_item(sd, it, vload(&st->K), smem);
+          else jv_item(sd, it, vload(&st->K), &red);
+        }
         else kt_item(sd, it - (unsigned)n0, vload(&st->K), ntiles_k(sd.N), smem);
         break;
       }
       case kJobJk3: {
         const int n0 = vload(&st->nitems[0]);
-        if ((int)it < n0) jp_item(sd, it, vload(&st->K), smem);
+        if ((int)it < n0) {
+          if (sd.tc) jp_tc_item(sd, it, vload(&st->K), smem);
+          else jp_item(sd, it, vload(&st->K), smem);
+        }
         else ksum_item(sd, it - (unsigned)n0, (int)ceil_div(vload(&st->K), kKtSplit));
         break;
       }
       case kJobJk4: junpack_item(sd, it); break;
+      case kJobSlice: slice_item(sd, it); break;
       default: break;
     }
     __syncthreads();
@@ -1120,6 +1572,14 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(const SysDesc* __restrict
       if (item_fma) atomicAdd(&ctl->kind_ops[kind], item_fma);
     }
     __syncthreads();
+  }
+  if constexpr (TC) tc::tc_fence_before();
+  __syncthreads();
+  if constexpr (TC) {
+    if (threadIdx.x < 32) {
+      tc::tc_fence_after();
+      tc::tmem_dealloc<kTcTmemCols>(tmem);
+    }
   }
 }
 
@@ -1151,6 +1611,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     else if (o.algorithm != CD_ALG_FULL || o.forced_pivots || o.candidates || o.diag_shift != 0.0)
       why = "only the fully pivoted decomposition (CD_ALG_FULL, no forced pivots, mask or shift)";
     else if (o.max_vectors < 0) why = "max_vectors < 0";
+    else if (o.update != CD_UPDATE_SLICE && o.update != CD_UPDATE_FP64) why = "bad update mode";
     else if (n_occ[i] <= 0 || !C_occ[i] || !J[i] || !K[i]) why = "n_occ, C_occ, J, K";
     if (!why.empty()) {
       set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + why);
@@ -1204,7 +1665,8 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
   struct Plan {
     int64_t n, ld, Mcap;
     int N, O, Op, b, nsplit;
-    size_t off[24];
+    size_t off[28];
+    int64_t bpitch;
     size_t bytes;
     std::vector<int32_t> csr_off, csr_nu, csr_row, allsp;
     std::vector<int8_t> kc, kd;
@@ -1232,7 +1694,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
         sizeof(double) * (size_t)p.ld,               // 0 D0
         sizeof(double) * (size_t)p.ld,               // 1 D1
         sizeof(double) * (size_t)p.b * p.ld,         // 2 pool
-        sizeof(double) * (size_t)p.Mcap * p.ld,      // 3 L
+        opts[i].update == CD_UPDATE_SLICE ? (size_t)16 : sizeof(double) * (size_t)p.Mcap * p.ld,   // 3 L (DFMA)
         sizeof(int64_t) * (size_t)p.Mcap,            // 4 piv
         sizeof(double) * (size_t)p.Mcap,             // 5 pivd
         sizeof(double) * (size_t)p.Mcap * p.b,       // 6 Bg0
@@ -1248,14 +1710,22 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
         sizeof(double) * N2,                         // 16 J
         sizeof(double) * N2,                         // 17 K
         sizeof(SysState),                            // 18 state
-        sizeof(double) * (size_t)p.N * p.O,          // 19 C
+        sizeof(double) * (size_t)p.N * p.Op + 256,   // 19 C (rows padded to Op, + room for the last 24-column read)
         sizeof(int32_t) * (size_t)(p.N + 1),         // 20 csr_off
         sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 21 csr_nu
         sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 22 csr_row
         sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n) + 2 * align256((size_t)std::max<int64_t>(1, p.n)),  // 23 allsp, kc, kd
+        sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n),                     // 24 erow
+        opts[i].update == CD_UPDATE_SLICE ? (size_t)2 * kTcSlices * 64 * (size_t)((p.Mcap + 2 * kTcBK) / kTcBK * kTcBK) * 2
+                                          : (size_t)16,                          // 25 pivot-row slices
+        opts[i].update == CD_UPDATE_SLICE
+            ? (size_t)((p.Mcap + kTcBK - 1) / kTcBK) * kTcSlices * (size_t)std::max<int64_t>(1, p.n) * kTcBK * 2
+            : (size_t)16,                                                        // 26 slice store
+        opts[i].update == CD_UPDATE_SLICE ? sizeof(double) * (size_t)kBMaxB * p.ld : (size_t)16,   // 27 block buffer
     };
+    p.bpitch = (p.Mcap + 2 * kTcBK) / kTcBK * kTcBK;
     size_t o = 0;
-    for (int k = 0; k < 24; ++k) {
+    for (int k = 0; k < 28; ++k) {
       p.off[k] = total + o;
       o += align256(sz[k]);
     }
@@ -1424,6 +1894,23 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     d.row_kd = d.row_kc + align256((size_t)std::max<int64_t>(1, p.n));
     d.row_mu = s->row_mu_dev;
     d.row_nu = s->row_nu_dev;
+    d.tc = opts[i].update == CD_UPDATE_SLICE ? 1 : 0;
+    d.erow = (const int32_t*)at(24);
+    d.Bsl = (__nv_bfloat16*)at(25);
+    d.bpitch = p.bpitch;
+    d.Ls = (__nv_bfloat16*)at(26);
+    d.Lblk = (double*)at(27);
+    if (d.tc) d.L = nullptr;
+    {
+      // row exponents: sqrt(D^1_r) < 2^e_r (frexp), so every |L^K_r| / 2^e_r <= 1
+      std::vector<int32_t> er(std::max<int64_t>(1, p.n), 0);
+      for (int64_t r = 0; r < p.n; ++r) {
+        int ex = 0;
+        if (s->row_diag[r] > 0.0) std::frexp(std::sqrt(s->row_diag[r]), &ex);
+        er[r] = ex;
+      }
+      BP_CUDA(cudaMemcpyAsync((void*)d.erow, er.data(), sizeof(int32_t) * er.size(), cudaMemcpyHostToDevice, cs));
+    }
     boys_of[k] = s->boys;
     // uploads
     SysState h;
@@ -1435,7 +1922,13 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     for (int x = 0; x < kBMaxB; ++x) h.slot_row[x] = -1;
     BP_CUDA(cudaMemcpyAsync(d.st, &h, sizeof(h), cudaMemcpyHostToDevice, cs));
     BP_CUDA(cudaMemcpyAsync(d.D0, s->diag_dev, sizeof(double) * p.ld, cudaMemcpyDeviceToDevice, cs));
-    BP_CUDA(cudaMemcpyAsync((void*)d.C, C_occ[i], sizeof(double) * (size_t)p.N * p.O, cudaMemcpyHostToDevice, cs));
+    {
+      std::vector<double> cp((size_t)p.N * p.Op + 32, 0.0);
+      for (int mu = 0; mu < p.N; ++mu)
+        for (int k = 0; k < p.O; ++k) cp[(size_t)mu * p.Op + k] = C_occ[i][(size_t)mu * p.O + k];
+      BP_CUDA(cudaMemcpyAsync((void*)d.C, cp.data(), sizeof(double) * cp.size(), cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaStreamSynchronize(cs));   // cp is a temporary
+    }
     BP_CUDA(cudaMemcpyAsync((void*)d.csr_off, p.csr_off.data(), sizeof(int32_t) * p.csr_off.size(), cudaMemcpyHostToDevice, cs));
     BP_CUDA(cudaMemcpyAsync((void*)d.csr_nu, p.csr_nu.data(), sizeof(int32_t) * p.csr_nu.size(), cudaMemcpyHostToDevice, cs));
     BP_CUDA(cudaMemcpyAsync((void*)d.csr_row, p.csr_row.data(), sizeof(int32_t) * p.csr_row.size(), cudaMemcpyHostToDevice, cs));
@@ -1454,16 +1947,31 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
   BP_CUDA(cudaStreamSynchronize(cs));
   const double t_upload = now_ms();
   // ---- the launch, recorded in a CUDA graph: clear J and the control block, one persistent kernel
+  int use_tc = 0;
+  for (int k = 0; k < n_sys; ++k) use_tc |= hd[k].tc;
+  auto kfn = use_tc ? batch_kernel<true> : batch_kernel<false>;
   int per_sm = 0, sms = 0;
-  BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBT, 0));
+  BP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem));
+  BP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBT, kDynSmem));
   BP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = std::max(1, per_sm) * sms;
+  // at most two CTAs per SM (each would hold half of the SM's tensor memory)
+  const int grid = std::max(1, std::min(per_sm, 2)) * sms;
+  if (getenv("CDERI_DEBUG"))
+    fprintf(stderr, "[cderi] batch_kernel<%s>: %d CTAs per SM, grid %d\n", use_tc ? "tensor-core update" : "FP64",
+            per_sm, grid);
   const long long wait_ns = (long long)device_wait_limit_ns();
   BP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < n_sys; ++k)
+  for (int k = 0; k < n_sys; ++k) {
     cudaMemsetAsync(hd[k].J, 0, sizeof(double) * (size_t)hd[k].N * hd[k].N, cs);
+    // the slice store starts at zero: the last 32-vector block of a system is read whole by the update
+    if (hd[k].tc)
+      cudaMemsetAsync(hd[k].Ls, 0,
+                      (size_t)((hd[k].Mcap + kTcBK - 1) / kTcBK) * kTcSlices * (size_t)std::max<int64_t>(1, hd[k].n) *
+                          kTcBK * 2, cs);
+  }
   cudaMemsetAsync(ctl_dev, 0, sizeof(BatchCtl), cs);
-  batch_kernel<<<grid, kBT, 0, cs>>>(desc_dev, n_sys, ctl_dev, boys_of[0], wait_ns);
+  kfn<<<grid, kBT, kDynSmem, cs>>>(desc_dev, n_sys, ctl_dev, boys_of[0], wait_ns);
   BP_CUDA(cudaStreamEndCapture(cs, &graph));
   BP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   BP_CUDA(cudaEventRecord(e0, cs));
@@ -1476,6 +1984,10 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
   BatchCtl hctl;
   BP_CUDA(cudaMemcpy(&hctl, ctl_dev, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
   for (int k = 0; k < n_sys; ++k) BP_CUDA(cudaMemcpy(&hst[k], hd[k].st, sizeof(SysState), cudaMemcpyDeviceToHost));
+  if (hctl.tc_err) {
+    set_error("cd_batch_persistent: a bounded tensor-core wait gave up (MMA completion)");
+    return fail(CD_ETIMEOUT);
+  }
   if (hctl.timed_out) {
     set_error("cd_batch_persistent: a CTA's wait for work gave up after the wait limit with no item completed");
     return fail(CD_ETIMEOUT);
@@ -1510,10 +2022,13 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     // 7 J_p = L^T v, 8 J unpack, 10 ERI columns, 13 B = L C, 14 partial K tiles, 15 K sum; 16 idle
     for (int k = 0; k < kJobKinds; ++k) stats[6 + k] = 0.0;
     const int kinds[][2] = {{1, kJobSelect}, {2, kJobCols}, {3, kJobUpdate}, {4, kJobStep}, {5, kJobJk1},
-                            {6, kJobJk2}, {7, kJobJk3}, {8, kJobJk4}, {10, kJobCols + 8}, {13, kJobJk1 + 8},
-                            {14, kJobJk2 + 8}, {15, kJobJk3 + 8}};
+                            {6, kJobJk2}, {7, kJobJk3}, {8, kJobJk4}, {9, kJobSlice}, {10, kJobCols + 8},
+                            {13, kJobJk1 + 8}, {14, kJobJk2 + 8}, {15, kJobJk3 + 8}};
     for (auto& kk : kinds) stats[6 + kk[0]] = (double)hctl.kind_ns[kk[1]] * 1e-9;
     stats[6 + 16] = (double)hctl.idle_ns * 1e-9;
+    if (getenv("CDERI_DEBUG"))
+      fprintf(stderr, "[cderi] tensor-core update items, thread-0 seconds: copies %.2f, MMA %.2f, drain %.2f, result %.2f\n",
+              hctl.tc_ns[0] * 1e-9, hctl.tc_ns[1] * 1e-9, hctl.tc_ns[2] * 1e-9, hctl.tc_ns[3] * 1e-9);
     for (int k = 0; k < kJobKinds; ++k) stats[23 + k] = (double)hctl.kind_ops[k];
   }
   cleanup();

@@ -23,31 +23,6 @@ namespace {
 constexpr int BM = 128, BK = 32;
 constexpr int kThreads = 192;
 
-// 64-byte swizzled K-major descriptor: rows of 32 bf16 (64 B), 8-row groups 512 B apart
-__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                   // leading byte offset (unused: swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
-  d |= (uint64_t)1 << 46;                   // version
-  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
-  return d;
-}
-
-// An FP32 accumulator value that is an exact integer with |x| <= 2^24, as a
-// 64-bit integer, using only FP32 adds/FMAs and integer adds: x = 4096 h + l
-// with h = round(x / 4096) (|h| <= 4096) and |l| <= 2048, each turned into an
-// int by the 1.5 * 2^23 mantissa trick.  (A direct float -> int64 conversion
-// executes on the FP64 pipe of this GPU, which would bound the drain.)
-__device__ __forceinline__ long long exact_float_to_ll(float x) {
-  constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
-  const float h = __fadd_rn(__fmaf_rn(x, 1.0f / 4096.0f, kMagic), -kMagic);
-  const float l = __fmaf_rn(-h, 4096.0f, x);
-  const int hi = __float_as_int(__fadd_rn(h, kMagic)) - 0x4B400000;
-  const int lo = __float_as_int(__fadd_rn(l, kMagic)) - 0x4B400000;
-  return ((long long)hi << 12) + (long long)lo;
-}
-
 template <int SA, int SB, int KEEP, int BN, int STAGES>
 struct Cfg {
   static constexpr int G = KEEP - 1;                       // accumulator groups (s+t = 2..KEEP)

@@ -35,11 +35,12 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-@pytest.mark.parametrize("block", [0, 16])
-def test_persistent_equals_single_calls(block):
+@pytest.mark.parametrize("block,update", [(0, "slice"), (16, "slice"), (48, "slice"), (0, "fp64"), (16, "fp64")])
+def test_persistent_equals_single_calls(block, update):
     import paper_2609_00306_b300 as cd
     systems = _uneven_batch()
-    Jb, Kb, Mb, info = cd.batch_persistent(systems, blocks=[block] * len(systems))
+    upd = cd.CD_UPDATE_SLICE if update == "slice" else cd.CD_UPDATE_FP64
+    Jb, Kb, Mb, info = cd.batch_persistent(systems, blocks=[block] * len(systems), update=upd)
     assert info["ctas"] > 0 and info["launch_device_ms"] > 0
     for s, J, K, M in zip(systems, Jb, Kb, Mb):
         f = cd.cd_eri_factor(s.basis, s.tau, s.schwarz, update=cd.CD_UPDATE_FP64)
@@ -51,11 +52,13 @@ def test_persistent_equals_single_calls(block):
         f.free()
 
 
-def test_persistent_vs_oracle():
+@pytest.mark.parametrize("update", ["slice", "fp64"])
+def test_persistent_vs_oracle(update):
     import paper_2609_00306_b300 as cd
     systems = _uneven_batch()
     pick = [1, 5]
-    Jb, Kb, Mb, _ = cd.batch_persistent([systems[i] for i in pick])
+    upd = cd.CD_UPDATE_SLICE if update == "slice" else cd.CD_UPDATE_FP64
+    Jb, Kb, Mb, _ = cd.batch_persistent([systems[i] for i in pick], update=upd)
     for k, i in enumerate(pick):
         s = systems[i]
         o = oracle.Oracle(s.basis)
