@@ -521,8 +521,8 @@ def run_batch(args):
         return 0
     clk = ClockSampler()
 
-    def persistent():
-        return cd.batch_persistent(systems, blocks=pblocks)
+    def persistent(update=cd.CD_UPDATE_SLICE):
+        return cd.batch_persistent(systems, blocks=pblocks, update=update)
 
     def sequential_fp64():
         out = []
@@ -545,6 +545,10 @@ def run_batch(args):
             infos.append(info)
     clocks = clk.summary()
     t0 = time.perf_counter()
+    _, _, Mf, info_f = persistent(cd.CD_UPDATE_FP64)
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
     seq = sequential_fp64()
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
@@ -555,40 +559,54 @@ def run_batch(args):
     t_stream = time.perf_counter() - t0
     errK = max(float(np.max(np.abs(K - k1)) / np.max(np.abs(k1))) for K, (j1, k1, m1) in zip(Kb, seq))
     errJ = max(float(np.max(np.abs(J - j1)) / np.max(np.abs(j1))) for J, (j1, k1, m1) in zip(Jb, seq))
-    same_M = all(int(m) == int(m1) for m, (j1, k1, m1) in zip(Mb, seq))
+    same_M = all(int(m) == int(m1) for m, (j1, k1, m1) in zip(Mb, seq)) and list(Mf) == list(Mb)
     v = float(np.mean(tb))
     info = infos[-1]
     dev_s = info["launch_device_ms"] * 1e-3
-    ops = sum(info["fp64_ops"].values())
     peak_fp64_ops = 148 * 2 * 2.032e9 / 1e12
+    bf16_sust = float(_measured_peaks().get("bf16_tflops_sustained") or 1358.8)
+
+    def sm_s(inf, kind):   # SM-seconds of one item kind (CTA-seconds / CTAs per SM)
+        return inf["cta_s"][kind] / (inf["ctas"] / 148.0)
+
+    eri_ach = info["fp64_ops"]["eri"] / sm_s(info, "eri") * 148 / 1e12
+    upd_fma = info["fp64_ops"]["update"]
+    upd_ach = 2.0 * 28 * upd_fma / sm_s(info, "update") * 148 / 1e12
+    ops_f = sum(info_f["fp64_ops"].values())
+    dev_f = info_f["launch_device_ms"] * 1e-3
     h2d = int(sum(s.C_occ.size * 8 for s in systems))
     d2h = int(sum(2 * s.n_basis ** 2 * 8 for s in systems))
-    out = {"metric": "64-system batch: screening + CD + J/K wall seconds (N=60-600 s+p, FP64)", "value": v,
-           "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": v * 1e3,
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded lattice s+p systems)",
+    out = {"metric": "64-system batch: screening + CD + J/K wall seconds (N=60-600 s+p, FP64-equivalent)",
+           "value": v, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup),
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+bf16x7 update", "data": "synthetic (seeded lattice s+p systems)",
            "config": {"workload": "batch64", "systems": len(systems),
                       "n_basis_total": int(sum(s.n_basis for s in systems)),
-                      "path": "cd_batch_persistent: one persistent kernel launch in a CUDA graph",
+                      "path": "cd_batch_persistent: one persistent kernel launch in a CUDA graph; column update as "
+                              "exact 7-slice BF16 products on the tensor cores, everything else FP64",
                       "blocks": table.get("persistent_blocks"),
-                      "l2": "inputs (vectors, ~70 GB over the batch) larger than L2"},
+                      "l2": "inputs (vectors, ~120 GB of slices over the batch) larger than L2"},
            "breakdown_s": {"setup": info["setup_ms"] * 1e-3, "upload": info["upload_ms"] * 1e-3,
                            "launch_device": dev_s},
            "cta_s": info["cta_s"], "idle_cta_s": info["idle_cta_s"], "ctas": info["ctas"],
            "reserved_gb": info["bytes"] / 1e9,
-           "roofline": {"kernel": "batch_kernel (persistent: ERI columns, DFMA update, pivot steps, J/K)",
-                        "bound": "alu", "achieved": ops / dev_s / 1e12, "peak": peak_fp64_ops,
-                        "unit": "T FP64 ops/s", "frac": ops / dev_s / 1e12 / peak_fp64_ops, "traffic": None,
-                        "work": "one FP64-pipe operation per FMA as the algorithm counts it (ERI: executed "
-                                "operations); per kind in fp64_ops",
+           "roofline": {"kernel": "batch_kernel ERI-column items (the largest share of the launch)", "bound": "alu",
+                        "achieved": eri_ach, "peak": peak_fp64_ops, "unit": "T FP64 ops/s",
+                        "frac": eri_ach / peak_fp64_ops, "traffic": None,
+                        "share_of_launch": sm_s(info, "eri") / (dev_s * 148),
+                        "how": "executed FP64-pipe operations / SM-seconds in ERI items x 148 SMs",
                         "peak_source": "FP64 pipe: 148 SMs x 2 operations/clk x 2.032 GHz (unit counts and clock)"},
-           "roofline_update": {"kernel": "update items (DFMA, 128 x 64 tiles)", "bound": "alu",
-                               "achieved": info["fp64_ops"]["update"] / (info["cta_s"]["update"] / 2) / 1e12 * 148,
-                               "peak": peak_fp64_ops, "unit": "T FP64 ops/s",
-                               "frac": info["fp64_ops"]["update"] / (info["cta_s"]["update"] / 2) / 1e12 * 148
-                               / peak_fp64_ops,
-                               "how": "FMAs / (CTA-seconds in update items / 2 CTAs per SM) x 148 SMs"},
+           "roofline_update": {"kernel": "batch_kernel tensor-core update items (28 BF16 slice products per FMA)",
+                               "bound": "tensor", "achieved": upd_ach, "peak": bf16_sust, "unit": "TFLOP/s",
+                               "frac": upd_ach / bf16_sust, "fp64_equivalent_tflops": 2.0 * upd_fma /
+                               sm_s(info, "update") * 148 / 1e12,
+                               "share_of_launch": sm_s(info, "update") / (dev_s * 148),
+                               "peak_source": "MEASURED_PEAKS.json bf16 (sustained) - of measured"},
            "fp64_ops": info["fp64_ops"],
+           "persistent_fp64_update_s": t_fp64,
+           "roofline_fp64_build": {"kernel": "batch_kernel<FP64> (DFMA update)", "bound": "alu",
+                                   "achieved": ops_f / dev_f / 1e12, "peak": peak_fp64_ops, "unit": "T FP64 ops/s",
+                                   "frac": ops_f / dev_f / 1e12 / peak_fp64_ops},
            "gpu_launches": 1,
            "clocks": clocks,
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
