@@ -1955,6 +1955,19 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
   BP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   BP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kBT, kDynSmem));
   BP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (use_tc && per_sm >= 1) {
+    // the occupancy calculator reports one CTA per SM for any kernel with tcgen05
+    // instructions; registers (2 x 128 x 256) and shared memory (2 x 77 KB) allow
+    // two, each holding half of the SM's tensor memory.  A CTA that is not
+    // resident at once only starts after another exits and then finds no work.
+    cudaFuncAttributes fa;
+    BP_CUDA(cudaFuncGetAttributes(&fa, kfn));
+    int smem_sm = 0;
+    BP_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int by_regs = 65536 / (kBT * ((fa.numRegs + 7) / 8 * 8));
+    const int by_smem = smem_sm / (int)(kDynSmem + fa.sharedSizeBytes + 1024);
+    per_sm = std::max(per_sm, std::min(by_regs, by_smem));
+  }
   // at most two CTAs per SM (each would hold half of the SM's tensor memory)
   const int grid = std::max(1, std::min(per_sm, 2)) * sms;
   if (getenv("CDERI_DEBUG"))
