@@ -251,11 +251,22 @@ const double* boys_table_device(int* rc) {
   if (cudaGetDevice(&dev) != cudaSuccess) { *rc = CD_ECUDA; set_error("cudaGetDevice failed"); return nullptr; }
   auto it = tables.find(dev);
   if (it != tables.end()) { *rc = CD_OK; return it->second; }
-  std::vector<double> h((size_t)kBoysPoints * kBoysCols);
+  std::vector<double> h((size_t)kBoysTableSize);
   for (int k = 0; k < kBoysPoints; ++k) {
     const long double T = (long double)k * (long double)kBoysStep;
-    for (int m = 0; m < kBoysFcols; ++m) h[(size_t)k * kBoysCols + m] = (double)boys_series(m, T);
+    long double F[kBoysFcols];
+    for (int m = 0; m < kBoysFcols; ++m) {
+      F[m] = boys_series(m, T);
+      h[(size_t)k * kBoysCols + m] = (double)F[m];
+    }
     h[(size_t)k * kBoysCols + kBoysFcols] = (double)expl(-T);
+    for (int L = 0; L <= kBoysMaxM; ++L) {
+      long double fact = 1.0L;
+      for (int j = 0; j < kBoysTaylor; ++j) {
+        if (j > 0) fact *= (long double)j;
+        h[(size_t)kBoysCoefOff + ((size_t)L * kBoysPoints + k) * kBoysTaylor + j] = (double)(F[L + j] / fact);
+      }
+    }
   }
   double* d = nullptr;
   if (cudaMalloc(&d, sizeof(double) * h.size()) != cudaSuccess ||

@@ -27,10 +27,11 @@ __device__ __forceinline__ void boys_fm(double T, double (&F)[L + 1], const doub
     const int k = __double2int_rn(T * (1.0 / kBoysStep));
     const double d = (double)k * kBoysStep - T;  // F_L(T) = sum_j F_{L+j}(T_k) d^j / j!
     const double* __restrict__ row = tab + k * kBoysCols;
-    const double* __restrict__ r = row + L;
-    double f = __ldg(r + kBoysTaylor - 1);
+    // Horner sum of the pre-divided coefficients F_{L+j}(T_k) / j!
+    const double* __restrict__ c = tab + kBoysCoefOff + (L * kBoysPoints + k) * kBoysTaylor;
+    double f = __ldg(c + kBoysTaylor - 1);
 #pragma unroll
-    for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, d * (1.0 / (j + 1)), __ldg(r + j));
+    for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, d, __ldg(c + j));
     F[L] = f;
     if constexpr (L > 0) {
       // exp(-T) = exp(-T_k) exp(d), exp(d) by Horner with constant coefficients 1/j!
@@ -294,7 +295,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
 
 // FP64-pipe operations (DFMA, DMUL, DADD, FP64 conversions) per primitive
 // quartet, counted from the code above, for the roofline of this kernel:
-//   set-up 22; Boys tabulated branch 19 (+ 10 + 2L for L > 0), asymptotic
+//   set-up 22; Boys tabulated branch 12 (+ 10 + 2L for L > 0), asymptotic
 //   branch 12 + 2L, both + (L+1) for S0; bra recurrence 4 + 6L (p) and
 //   1 + 18(L-1) more (d); ket: 5, level 1 per distinct kc FK x (2 | 9 | 33),
 //   per component NE adds (ket ss), NE adds (level 1 only) or 6 | 19 | 67 (pp).
@@ -341,7 +342,7 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     }
     const unsigned long long nq = (unsigned long long)(__ldg(bra.pp_off + sb + 1) - __ldg(bra.pp_off + sb)) *
                                   (unsigned long long)(__ldg(ket.pp_off + kg.sp + 1) - __ldg(ket.pp_off + kg.sp));
-    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (19 + (L > 0 ? 10 + 2 * L : 0)) +
+    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (12 + (L > 0 ? 10 + 2 * L : 0)) +
            (nq - n_table) * (12 + 2 * L);
   }
   const int32_t* rw = bra.row + 9 * sb;

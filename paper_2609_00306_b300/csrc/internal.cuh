@@ -88,6 +88,11 @@ constexpr double kBoysTmax = 60.0;
 constexpr int kBoysPoints = 602;
 constexpr int kBoysFcols = kBoysMaxM + kBoysTaylor + 1;  // F_0..F_12
 constexpr int kBoysCols = kBoysFcols + 1;                // + exp(-T_k)
+// After the kBoysPoints x kBoysCols main table: for each L = 0..kBoysMaxM the
+// Taylor coefficients of F_L about every grid point, c[L][k][j] = F_{L+j}(T_k) / j!
+// (j < kBoysTaylor), so that F_L(T_k - d) is a plain Horner sum in d
+constexpr int kBoysCoefOff = kBoysPoints * kBoysCols;
+constexpr int kBoysTableSize = kBoysCoefOff + (kBoysMaxM + 1) * kBoysPoints * kBoysTaylor;
 // bra primitive pairs with |Kp| below this are dropped.  The contribution of
 // one such primitive pair to a contracted integral was measured on the N = 2000
 // lattice system (30,000 dropped pairs with |Kp| in [1e-24, 1e-18) against
