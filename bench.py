@@ -60,6 +60,9 @@ def _args():
                     help="comma list of J/K modes timed separately after the step (default: all)")
     ap.add_argument("--cpu-sample-steps", type=int, default=48)
     ap.add_argument("--block", type=int, default=0, help="speculative column block b (0 = library default)")
+    ap.add_argument("--validate-cpu-baseline", action="store_true",
+                    help="host only: the cpu_baseline projection of --workload against the full oracle run "
+                         "stored in tests/golden/<workload>_oracle.txt (no GPU)")
     ap.add_argument("--batch-only", type=int, default=0,
                     help="batch64: run only the persistent batch on the first N systems, once (profiling)")
     ap.add_argument("--no-fp64-update", action="store_true",
@@ -617,8 +620,34 @@ def run_batch(args):
     return 0
 
 
+def validate_cpu_baseline(args):
+    """The projection of oracle_sample against the full oracle run of the same
+    workload (timings stored by tests/golden/make_golden.py on this host)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.txt")
+    full = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                full[k.strip()] = v.strip()
+    M = int(full["M"])
+    s = synth.make_workload(args.workload)
+    proj = oracle_sample(s, M, args.cpu_sample_steps)
+    meas = {"cd_s": float(full["t_screen_s"]) + float(full["t_cd_s"]), "j_ms": float(full["t_j_s"]) * 1e3,
+            "k_ms": float(full["t_k_s"]) * 1e3}
+    out = {"workload": args.workload, "M": M, "threads": full.get("omp_threads"),
+           "projected": {k: proj[k] for k in ("cd_s", "j_ms", "k_ms")},
+           "measured_full_run": meas,
+           "projected_over_measured": {k: proj[k] / meas[k] for k in meas},
+           "sample_wall_s": proj["sample_wall_s"], "sample": proj["sample"]}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.validate_cpu_baseline:
+        return validate_cpu_baseline(args)
     if args.workload == "batch64" and args.impl == "ours":
         return run_batch(args)
     rank = int(os.environ.get("RANK", 0))

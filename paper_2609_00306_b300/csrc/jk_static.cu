@@ -2,9 +2,8 @@
 // memory.
 //
 // Some callers cannot call cudaMalloc: code running inside a memory pool or
-// arena that owns all device memory, a host application whose allocator must
-// not be bypassed, or a stream whose work is being recorded where allocation
-// calls are not allowed.  cd_jk_coulomb_static computes the same J as
+// arena that owns all device memory, or a host application whose allocator
+// must not be bypassed.  cd_jk_coulomb_static computes the same J as
 // cd_jk(..., CD_JK_FP64 | CD_JK_DEVICE | CD_JK_ONLY_J) but takes its scratch
 // (the packed density, the projected density v_P and the packed J) from one
 // file-scope __device__ array of fixed size instead of allocating it.  Every

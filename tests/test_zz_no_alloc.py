@@ -1,6 +1,6 @@
 """cd_jk_coulomb_static: the Coulomb build for callers that cannot allocate
-device memory (an arena that owns the device memory, or work recorded where
-allocation calls are not allowed).  It takes its scratch from a static device
+device memory (an arena that owns the device memory, or a host allocator that
+must not be bypassed).  It takes its scratch from a static device
 array instead of cudaMalloc.  Checked against the allocating cd_jk on two
 calls in a row (the scratch keeps the previous call's contents, so the second
 call shows that everything that must start at zero is cleared).  Collected
