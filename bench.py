@@ -63,6 +63,9 @@ def _args():
     ap.add_argument("--validate-cpu-baseline", action="store_true",
                     help="host only: the cpu_baseline projection of --workload against the full oracle run "
                          "stored in tests/golden/<workload>_oracle.txt (no GPU)")
+    ap.add_argument("--update-shape", default="",
+                    help="M,K: time one exact 7-slice product of the column-update shape (M rows x K vectors "
+                         "against 64 columns) through cd_slice_matmul, for profilers")
     ap.add_argument("--batch-only", type=int, default=0,
                     help="batch64: run only the persistent batch on the first N systems, once (profiling)")
     ap.add_argument("--no-fp64-update", action="store_true",
@@ -644,8 +647,35 @@ def validate_cpu_baseline(args):
     return 0
 
 
+def run_update_shape(args):
+    """One exact 7-slice product with the shape of a column-update launch of the
+    N = 2000 decomposition (rows x vectors against 64 pivot columns)."""
+    import torch
+    import paper_2609_00306_b300 as cd
+    from paper_2609_00306_b300 import build
+    build.build()
+    m, k = (int(x) for x in args.update_shape.split(","))
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = torch.randn(m, k, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.randn(64, k, dtype=torch.float64, device="cuda", generator=g)
+    cd.slice_matmul(X, Y, 7)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = cd.slice_matmul(X, Y, 7)
+    e1.record()
+    torch.cuda.synchronize()
+    ref = X[:256] @ Y.T
+    err = float((out[:256] - ref).abs().max() / ref.abs().max())
+    print(json.dumps({"update_shape": [m, k, 64], "ms": e0.elapsed_time(e1), "max_rel_err_first_rows": err}),
+          flush=True)
+    return 0
+
+
 def main():
     args = _args()
+    if args.update_shape:
+        return run_update_shape(args)
     if args.validate_cpu_baseline:
         return validate_cpu_baseline(args)
     if args.workload == "batch64" and args.impl == "ours":
