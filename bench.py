@@ -126,18 +126,20 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------- CPU oracle ---
-def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 4096, sub_steps: int = 600):
+def oracle_sample(system, M_full: int, k_steps: int, stream_vectors: int = 64):
     """Time the CPU oracle on a bounded sample of the workload and project it.
 
-    Sample (all on the same N=2000 system, oracle as it stands):
+    Sample (all on the same system, oracle as it stands):
       1. the Schwarz screening pass (diagonal of every pair);
       2. the first k pivot steps over all rows: per-step cost a (one ERI
          column over all rows, the update is negligible at small K);
-      3. the decomposition restricted to the first `sub_rows` rows, up to
-         `sub_steps` steps (K of them), timed whole, minus the time of the same
-         K ERI columns alone: the remainder is the update, sum_k b' k =
-         b' K^2 / 2, giving the update cost b' per vector per step, scaled by
-         rows / sub_rows;
+      3. the update term.  Step K of the decomposition also subtracts K stored
+         vectors from the new column over all rows (Eq. (subtr)): a stream over
+         K x rows x 8 bytes that is far larger than the host caches at the
+         sizes that matter.  Its cost per vector per step, b, is the time of
+         the same stream on this host: one matrix-vector product over
+         `stream_vectors` vectors of all rows (every host thread), divided by
+         their number;
       4. the J/K contraction of 2 vectors (per-vector cost c).
     Projection to one full step: t_screen + M a + b M^2 / 2 + M c, with M the
     vector count of the full decomposition.
@@ -153,16 +155,16 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 4096, sub_s
     t = time.perf_counter()
     r = o.cd(rows, system.tau, max_steps=k_steps)
     a = (time.perf_counter() - t) / k_steps
-    sub = rows[:min(sub_rows, n)]
+    Ls = np.full((stream_vectors, n), 1.0 / 3.0)
+    w = np.full(stream_vectors, 0.5)
+    col = w @ Ls                                     # warm-up pass
     t = time.perf_counter()
-    rs = o.cd(sub, system.tau, max_steps=sub_steps)
-    T_cd = time.perf_counter() - t
-    K_sub = max(rs.M, 1)
-    t = time.perf_counter()
-    o.eri_matrix(sub, sub[rs.piv])            # the same K_sub ERI columns alone
-    T_eri = time.perf_counter() - t
-    b_sub = max(0.0, 2.0 * (T_cd - T_eri) / K_sub ** 2)
-    b = b_sub * n / sub.shape[0]
+    reps = 3
+    for _ in range(reps):
+        col = w @ Ls
+    b = (time.perf_counter() - t) / reps / stream_vectors
+    del Ls, col
+    K_sub, T_cd, T_eri, k1 = stream_vectors, b * stream_vectors, 0.0, 0
     t = time.perf_counter()
     oracle.jk_from_vectors(r.L[:2], rows, system.C_occ, want_k=False)
     cJ = (time.perf_counter() - t) / 2.0
@@ -177,9 +179,9 @@ def oracle_sample(system, M_full: int, k_steps: int, sub_rows: int = 4096, sub_s
         "value": proj, "unit": "s", "cores": cores, "kind": "oracle",
         "cd_s": cd_s, "j_ms": M_full * cJ * 1e3, "k_ms": M_full * cK * 1e3, "projected": True,
         "sample": (f"oracle on {name}: screening ({t_screen:.2f}s), first {k_steps} pivot steps over "
-                   f"all {n} rows (a={a:.3g}s/step), {K_sub} steps on the first {sub.shape[0]} rows "
-                   f"({T_cd:.2f}s, of which its ERI columns alone {T_eri:.2f}s: update b={b:.3g}s per vector "
-                   f"per step after scaling), J and K of 2 vectors (cJ={cJ:.3g}s, cK={cK:.3g}s each); "
+                   f"all {n} rows (a={a:.3g}s/step), update stream over {K_sub} vectors of all rows "
+                   f"({T_cd * 1e3:.1f} ms per pass: b={b:.3g}s per vector per step), "
+                   f"J and K of 2 vectors (cJ={cJ:.3g}s, cK={cK:.3g}s each); "
                    f"projected to M={M_full}: CD = t_screen + M a + b M^2/2, J = M cJ, K = M cK; "
                    f"sample wall {sample_s:.1f}s"),
         "sample_wall_s": sample_s,
