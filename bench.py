@@ -722,7 +722,12 @@ def run_reference(args):
                             "sample": vals[0]["sample"], "projected": True,
                             "cd_s": float(np.mean([r["cd_s"] for r in vals])),
                             "j_ms": float(np.mean([r["j_ms"] for r in vals])),
-                            "k_ms": float(np.mean([r["k_ms"] for r in vals]))},
+                            "k_ms": float(np.mean([r["k_ms"] for r in vals])),
+                            "sample_wall_s": float(np.mean([r["sample_wall_s"] for r in vals])),
+                            "note": "value is the projection of one full step from the timed sample (each "
+                                    "step runs only the sample, about sample_wall_s of host time); against "
+                                    "full oracle runs the projection came within -30%/+35% "
+                                    "(bench.py --validate-cpu-baseline)"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
