@@ -1,7 +1,7 @@
 """Batch of independent systems in one persistent kernel launch
 (cd_batch_persistent): every system's vector count and J/K equal those of a
 plain single-system FP64 call (same recursion, Sec. 2; J/K of Sec. 4.1 summed
-in another order), two systems are checked against the CPU oracle, and the
+in another order), all seven are checked against the CPU oracle, and the
 error paths (M = 0, vector capacity, bad arguments, the bounded wait for
 work) return their codes without disturbing the device."""
 import numpy as np
@@ -54,9 +54,10 @@ def test_persistent_equals_single_calls(block, update):
 
 @pytest.mark.parametrize("update", ["slice", "fp64"])
 def test_persistent_vs_oracle(update):
+    # all seven uneven systems (N = 16-96, tau 1e-4 / 1e-5) against the oracle's decomposition and J/K
     import paper_2609_00306_b300 as cd
     systems = _uneven_batch()
-    pick = [1, 5]
+    pick = list(range(len(systems)))
     upd = cd.CD_UPDATE_SLICE if update == "slice" else cd.CD_UPDATE_FP64
     Jb, Kb, Mb, _ = cd.batch_persistent([systems[i] for i in pick], update=upd)
     for k, i in enumerate(pick):
