@@ -4,7 +4,9 @@
 // Every system runs the fully pivoted decomposition of Sec. 2 in the blocked
 // form of the single-system path (b candidate columns computed and brought up
 // to date together, then pivot steps while the global argmax of the residual
-// diagonal stays among them) and then the J/K build of Sec. 4.1, all in FP64.
+// diagonal stays among them) and then the J/K build of Sec. 4.1.  Everything is
+// FP64 except, in the default tensor-core build, the column update, which is
+// the exact 7-slice BF16 product of the single-system path (FP64-equivalent).
 // A system's work is a sequence of jobs, each a set of independent items:
 //
 //   SELECT  1 item: the b largest residual diagonals >= tau (ties: lowest row)
@@ -12,16 +14,21 @@
 //           patterns); pool slots of columns still wanted are kept, the new
 //           rows get ket groups
 //   COLS    the pivot rows of the existing vectors gathered for the update
-//           (256 vectors per item), and the ERI columns of the new candidates
-//           (kernel a: 128 bra shell pairs x one ket group per item)
+//           (256 vectors per item; their slices in the tensor-core build), and
+//           the ERI columns of the new candidates (kernel a: 128 bra shell
+//           pairs x one ket group per item)
 //   UPDATE  col -= L Lp^T over the vectors not yet applied, Eq. (subtr): 128
-//           rows x <= 64 columns per item, register-tiled DFMA
+//           rows x 32 columns per item on the tensor cores (tcgen05, operands
+//           copied to shared memory with cp.async), or 128 x <= 64 DFMA tiles
 //   STEP    one pivot step, Eq. (subtr) in-block terms and Eq. (diag), over
 //           1024 rows per item, each item leaving its partial argmax
-//   JK1     d = packed density (1024 rows per item); B^P = L^P C (one vector
-//           per item, through a row list per basis function)
-//   JK2     v = L d (4 vectors per item); partial K tiles sum_P B^P B^P^T
-//           (64 x 64 tile x 128 vectors per item)
+//   SLICE   tensor-core build, after a block: its vectors (an FP64 block
+//           buffer) written once into the BF16 slice store
+//   JK1     d = packed density (1024 rows per item); B^P = L^P C (through a
+//           row list per basis function; 32 vectors x 8 basis functions per
+//           item from the slice store, or one vector per item)
+//   JK2     v = L d; partial K tiles sum_P B^P B^P^T (64 x 64 tile x 128
+//           vectors per item)
 //   JK3     J_p = L^T v (1024 rows per item); K tiles = 2 x the sum of partials
 //   JK4     J unpacked to N x N
 //
@@ -40,8 +47,9 @@
 // Memory is reserved per system before the launch (vectors for max_vectors,
 // default 8 N, plus the K intermediates); a system that needs more vectors
 // stops with CD_ENOMEM.  Loads of data that change during the launch (residual
-// diagonals, columns, gathered rows, job state) bypass L1 (ld.global.cg or
-// volatile): another SM may have rewritten them since this SM last cached them.
+// diagonals, columns, gathered rows, slices, job state) bypass L1
+// (ld.global.cg, cp.async.cg or volatile): another SM may have rewritten them
+// since this SM last cached them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
