@@ -943,7 +943,38 @@ __device__ void kb_item(const SysDesc& d, unsigned P) {
 
 // tensor-core mode: B^P[mu][i] = sum_nu L^P_{mu nu} C[nu][i] for the 32 vectors
 // of slice chunk c (lane = vector: each row's 7 slice rows are read as 64-byte
-// rows across the warp) and 8 basis functions mu (2 per warp), i in passes of 24
+// rows across the warp) and 8 basis functions mu (2 per warp); all columns i in
+// one pass when the padded occupied count is at most 72, else passes of 24
+template <int NI>
+__device__ __forceinline__ void kb_tc_mu(const SysDesc& d, int64_t c, int mu, int i0, int lane, int64_t P, int64_t M) {
+  const int e0 = __ldg(d.csr_off + mu), e1 = __ldg(d.csr_off + mu + 1);
+  double acc[NI];
+#pragma unroll
+  for (int q = 0; q < NI; ++q) acc[q] = 0.0;
+  for (int e = e0; e < e1; ++e) {
+    const int32_t row = __ldg(d.csr_row + e), nu = __ldg(d.csr_nu + e);
+    long long v = 0;
+#pragma unroll
+    for (int t = 0; t < kTcSlices; ++t)
+      v = v * 256 + (long long)(int)__bfloat162float(__ldcg(d.Ls + ((c * kTcSlices + t) * d.n + row) * kTcBK + lane));
+    const double x = ldexp((double)v, __ldg(d.erow + row) - (8 * kTcSlices - 1));
+    // C rows are zero-padded to Op (a multiple of 8), so NI columns from i0 are in the array
+    const double2* cr = (const double2*)(d.C + (int64_t)nu * d.Op + i0);
+#pragma unroll
+    for (int q = 0; q < NI / 2; ++q) {
+      const double2 c2 = __ldg(cr + q);
+      acc[2 * q] = fma(x, c2.x, acc[2 * q]);
+      acc[2 * q + 1] = fma(x, c2.y, acc[2 * q + 1]);
+    }
+  }
+  if (P < M) {
+    double* Bp = d.B + ((int64_t)P * d.N + mu) * d.Op + i0;
+#pragma unroll
+    for (int q = 0; q < NI; ++q)
+      if (i0 + q < d.Op) Bp[q] = acc[q];
+  }
+}
+
 __device__ void kb_tc_item(const SysDesc& d, unsigned it, int64_t M) {
   const int nmu = (d.N + 7) / 8;
   const int64_t c = it / nmu;
@@ -951,33 +982,11 @@ __device__ void kb_tc_item(const SysDesc& d, unsigned it, int64_t M) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t P = c * 32 + lane;
   for (int mu = mb * 8 + w; mu < min(d.N, mb * 8 + 8); mu += kBT / 32) {
-    const int e0 = __ldg(d.csr_off + mu), e1 = __ldg(d.csr_off + mu + 1);
-    for (int i0 = 0; i0 < d.Op; i0 += 24) {
-      double acc[24];
-#pragma unroll
-      for (int q = 0; q < 24; ++q) acc[q] = 0.0;
-      for (int e = e0; e < e1; ++e) {
-        const int32_t row = __ldg(d.csr_row + e), nu = __ldg(d.csr_nu + e);
-        long long v = 0;
-#pragma unroll
-        for (int t = 0; t < kTcSlices; ++t)
-          v = v * 256 + (long long)(int)__bfloat162float(__ldcg(d.Ls + ((c * kTcSlices + t) * d.n + row) * kTcBK + lane));
-        const double x = ldexp((double)v, __ldg(d.erow + row) - (8 * kTcSlices - 1));
-        // C rows are zero-padded to Op (a multiple of 8), so 24 columns from i0 are in the row
-        const double2* cr = (const double2*)(d.C + (int64_t)nu * d.Op + i0);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-          const double2 c2 = __ldg(cr + q);
-          acc[2 * q] = fma(x, c2.x, acc[2 * q]);
-          acc[2 * q + 1] = fma(x, c2.y, acc[2 * q + 1]);
-        }
-      }
-      if (P < M) {
-        double* Bp = d.B + ((int64_t)P * d.N + mu) * d.Op + i0;
-#pragma unroll
-        for (int q = 0; q < 24; ++q)
-          if (i0 + q < d.Op) Bp[q] = acc[q];
-      }
+    if (d.Op <= 72) {
+      // every column in one pass: each entry's 7 slice reads and its rebuild are done once
+      kb_tc_mu<72>(d, c, mu, 0, lane, P, M);
+    } else {
+      for (int i0 = 0; i0 < d.Op; i0 += 24) kb_tc_mu<24>(d, c, mu, i0, lane, P, M);
     }
   }
 }
@@ -1718,7 +1727,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
         sizeof(double) * N2,                         // 16 J
         sizeof(double) * N2,                         // 17 K
         sizeof(SysState),                            // 18 state
-        sizeof(double) * (size_t)p.N * p.Op + 256,   // 19 C (rows padded to Op, + room for the last 24-column read)
+        sizeof(double) * ((size_t)p.N * p.Op + 80),   // 19 C (rows padded to Op, + room for the last 72-column read)
         sizeof(int32_t) * (size_t)(p.N + 1),         // 20 csr_off
         sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 21 csr_nu
         sizeof(int32_t) * (size_t)std::max<int64_t>(1, 2 * p.n),   // 22 csr_row
@@ -1931,7 +1940,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     BP_CUDA(cudaMemcpyAsync(d.st, &h, sizeof(h), cudaMemcpyHostToDevice, cs));
     BP_CUDA(cudaMemcpyAsync(d.D0, s->diag_dev, sizeof(double) * p.ld, cudaMemcpyDeviceToDevice, cs));
     {
-      std::vector<double> cp((size_t)p.N * p.Op + 32, 0.0);
+      std::vector<double> cp((size_t)p.N * p.Op + 80, 0.0);
       for (int mu = 0; mu < p.N; ++mu)
         for (int k = 0; k < p.O; ++k) cp[(size_t)mu * p.Op + k] = C_occ[i][(size_t)mu * p.O + k];
       BP_CUDA(cudaMemcpyAsync((void*)d.C, cp.data(), sizeof(double) * cp.size(), cudaMemcpyHostToDevice, cs));
