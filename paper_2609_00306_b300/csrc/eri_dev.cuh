@@ -33,7 +33,14 @@ __device__ __forceinline__ void boys_fm(double T, double (&F)[L + 1], const doub
 #pragma unroll
     for (int j = kBoysTaylor - 2; j >= 0; --j) f = fma(f, d, __ldg(c + j));
     F[L] = f;
-    if constexpr (L > 0) {
+    if constexpr (L == 1) {
+      // F_0 by its own Horner sum: cheaper than exp(-T) and one downward step
+      const double* __restrict__ c0 = tab + kBoysCoefOff + k * kBoysTaylor;
+      double f0 = __ldg(c0 + kBoysTaylor - 1);
+#pragma unroll
+      for (int j = kBoysTaylor - 2; j >= 0; --j) f0 = fma(f0, d, __ldg(c0 + j));
+      F[0] = f0;
+    } else if constexpr (L > 1) {
       // exp(-T) = exp(-T_k) exp(d), exp(d) by Horner with constant coefficients 1/j!
       constexpr double inv_fact[kExpTaylor] = {1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720,
                                                1.0 / 5040, 1.0 / 40320};
@@ -295,7 +302,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
 
 // FP64-pipe operations (DFMA, DMUL, DADD, FP64 conversions) per primitive
 // quartet, counted from the code above, for the roofline of this kernel:
-//   set-up 22; Boys tabulated branch 12 (+ 10 + 2L for L > 0), asymptotic
+//   set-up 22; Boys tabulated branch 12 (+ 7 for L = 1, + 10 + 2L for L > 1), asymptotic
 //   branch 12 + 2L, both + (L+1) for S0; bra recurrence 4 + 6L (p) and
 //   1 + 18(L-1) more (d); ket: 5, level 1 per distinct kc FK x (2 | 9 | 33),
 //   per component NE adds (ket ss), NE adds (level 1 only) or 6 | 19 | 67 (pp).
@@ -342,7 +349,7 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     }
     const unsigned long long nq = (unsigned long long)(__ldg(bra.pp_off + sb + 1) - __ldg(bra.pp_off + sb)) *
                                   (unsigned long long)(__ldg(ket.pp_off + kg.sp + 1) - __ldg(ket.pp_off + kg.sp));
-    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (12 + (L > 0 ? 10 + 2 * L : 0)) +
+    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (12 + (L == 1 ? 7 : (L > 1 ? 10 + 2 * L : 0))) +
            (nq - n_table) * (12 + 2 * L);
   }
   const int32_t* rw = bra.row + 9 * sb;
