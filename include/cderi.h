@@ -275,18 +275,22 @@ int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, 
                  const int32_t* n_occ, double* const* J, double* const* K, int32_t jk_mode, int32_t workers,
                  void* stream);
 
-/* The same computation (no paper counterpart either) in FP64 throughout, with
- * the decompositions and J/K builds of all systems in ONE persistent kernel
- * launch recorded in a CUDA graph.  Per system: the fully pivoted
- * decomposition of Sec. 2 (blocked, b = opts[i].block <= 64, 0 = 64; ERI
- * columns, DFMA column update, pivot steps on the device), then J and K of
- * Sec. 4.1 with D = 2 C_occ C_occ^T.  Set-up (screening, diagonal) runs first
- * on host workers.  Work items (a block's ERI columns, update tiles, the rows
+/* The same computation (no paper counterpart either), FP64 and FP64-equivalent,
+ * with the decompositions and J/K builds of all systems in ONE persistent
+ * kernel launch recorded in a CUDA graph.  Per system: the fully pivoted
+ * decomposition of Sec. 2 (blocked, b = opts[i].block <= 64, 0 = 64; FP64 ERI
+ * columns and pivot steps on the device; the column update of Eq. (subtr) as
+ * exact 7-slice BF16 products on the tensor cores, opts[i].update =
+ * CD_UPDATE_SLICE, the default, with the vectors kept as slices, or as FP64
+ * DFMA tiles, CD_UPDATE_FP64; a batch with any CD_UPDATE_SLICE system runs
+ * the tensor-core build for all), then J and K of Sec. 4.1 in FP64 with
+ * D = 2 C_occ C_occ^T.  Set-up (screening, diagonal) runs first on host
+ * workers.  Work items (a block's ERI columns, update tiles, the rows
  * of a pivot step, J/K tiles) are claimed by the CTAs from per-system job
  * words; the CTA that completes a job's last item publishes the next job.
  * Inputs: bases, opts (tau, schwarz, block, max_vectors: vector capacity per
- * system, 0 = 8 N; opts[0].mem_budget_gb caps the whole batch, 0 = 90% of
- * free memory; CD_ALG_FULL only, no forced pivots, mask or shift), C_occ[i]
+ * system, 0 = 8 N; update; opts[0].mem_budget_gb caps the whole batch, 0 =
+ * 90% of free memory; CD_ALG_FULL only, no forced pivots, mask or shift), C_occ[i]
  * host [N_i][n_occ[i]] row-major.  Outputs (host, caller-owned): J[i], K[i]
  * [N_i][N_i]; M_out[i] the vector counts (may be NULL); stats (may be NULL,
  * 39 entries): [0] set-up ms, [1] upload ms, [2] device ms of the launch, [3]
