@@ -289,21 +289,25 @@ int cd_batch_run(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts, 
  * of a pivot step, J/K tiles) are claimed by the CTAs from per-system job
  * words; the CTA that completes a job's last item publishes the next job.
  * Inputs: bases, opts (tau, schwarz, block, max_vectors: vector capacity per
- * system, 0 = 8 N; update; opts[0].mem_budget_gb caps the whole batch, 0 =
+ * system, 0 = 8 N; update; opts[0].mem_budget_gb caps the device buffer of a wave, 0 =
  * 90% of free memory; CD_ALG_FULL only, no forced pivots, mask or shift), C_occ[i]
  * host [N_i][n_occ[i]] row-major.  Outputs (host, caller-owned): J[i], K[i]
  * [N_i][N_i]; M_out[i] the vector counts (may be NULL); stats (may be NULL,
- * 39 entries): [0] set-up ms, [1] upload ms, [2] device ms of the launch, [3]
- * host ms of the launch and read-back, [4] CTAs, [5] bytes reserved, [6 + k]
+ * 40 entries): [0] set-up ms, [1] upload ms, [2] device ms of the launches, [3]
+ * host ms of the launches and read-back, [4] CTAs, [5] bytes reserved, [6 + k]
  * CTA-seconds spent in items of kind k (1 select, 2 gather, 3 update, 4 step,
  * 5 density, 6 v = L d, 7 J_p = L^T v, 8 J unpack, 9 slicing, 10 ERI columns, 13 B = L C,
  * 14 partial K tiles, 15 K sums), [22] CTA-seconds spent looking for work,
  * [23 + k] FP64-pipe operations of the items of kind k (one per FMA as the
- * algorithm counts them; for ERI columns the kernel's executed operations).  All device memory is
+ * algorithm counts them; for ERI columns the kernel's executed operations),
+ * [39] waves.  Waves: when the buffers of all systems together exceed the
+ * budget, the systems (largest first) go into the first wave that still fits
+ * it, and the waves run one after another, each as its own graph launch on one
+ * device buffer the size of the largest wave.  All device memory is
  * allocated for the call and freed before it returns; `stream` is waited for
  * before the work starts.  Errors: CD_EINVAL (arguments, names the system),
- * CD_ENOMEM (batch over the budget, or a system needing more than its
- * max_vectors), CD_ENOTPSD, CD_ETIMEOUT (a CTA waited longer than the wait
+ * CD_ENOMEM (one system alone over the budget, or a system needing more than
+ * its max_vectors), CD_ENOTPSD, CD_ETIMEOUT (a CTA waited longer than the wait
  * limit of cd_set_wait_limit with no item completed anywhere; the launch
  * then stops cleanly), CD_ECUDA. */
 int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const cd_opts_t* opts,

@@ -407,7 +407,7 @@ def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: floa
     PArr = ctypes.c_void_p * n
     occ = np.array([c.shape[1] for c in Cs], dtype=np.int32)
     M = np.zeros(n, dtype=np.int64)
-    stats = np.zeros(39)
+    stats = np.zeros(40)
     _check(load().cd_batch_persistent(n, ctypes.byref(bases), ctypes.byref(opts),
                                       PArr(*[c.ctypes.data for c in Cs]), _p(occ),
                                       PArr(*[j.ctypes.data for j in Js]), PArr(*[k.ctypes.data for k in Ks]),
@@ -418,7 +418,7 @@ def batch_persistent(systems, blocks=None, max_vectors=None, mem_budget_gb: floa
                       [(1, "select"), (2, "gather"), (3, "update"), (4, "step"), (5, "density"), (6, "v"),
                        (7, "jp"), (8, "j_unpack"), (9, "slice"), (10, "eri"), (13, "b"), (14, "k_tiles"),
                        (15, "k_sum")]},
-            "idle_cta_s": float(stats[22]),
+            "idle_cta_s": float(stats[22]), "waves": int(stats[39]),
             "fp64_ops": {name: float(stats[23 + k]) for k, name in
                          [(3, "update"), (4, "step"), (6, "v"), (7, "jp"), (10, "eri"), (13, "b"),
                           (14, "k_tiles")]}}

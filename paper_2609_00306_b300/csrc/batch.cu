@@ -1678,7 +1678,7 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
       return rcs[i];
     }
   const double t_setup = now_ms();
-  // ---- sizes and one device allocation for every system's buffers
+  // ---- sizes of every system's buffers (offsets relative to the system's base)
   struct Plan {
     int64_t n, ld, Mcap;
     int N, O, Op, b, nsplit;
@@ -1691,7 +1691,6 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     int64_t idx;
   };
   std::vector<Plan> plan(n_sys);
-  size_t total = 0;
   size_t max_items = 0;
   for (int i = 0; i < n_sys; ++i) {
     cd_system* s = systems[i];
@@ -1743,11 +1742,10 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     p.bpitch = (p.Mcap + 2 * kTcBK) / kTcBK * kTcBK;
     size_t o = 0;
     for (int k = 0; k < 28; ++k) {
-      p.off[k] = total + o;
+      p.off[k] = o;
       o += align256(sz[k]);
     }
     p.bytes = o;
-    total += o;
     // row list per basis function: (mu nu) under mu and, if mu != nu, under nu
     p.csr_off.assign(p.N + 1, 0);
     std::vector<int32_t> mu(p.n), nu(p.n);
@@ -1792,33 +1790,61 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
     set_error("cd_batch_persistent: a system needs more than 2^23 work items in one job");
     return CD_EINVAL;
   }
+  for (int i = 1; i < n_sys; ++i)
+    if (systems[i]->boys != systems[0]->boys) {
+      release_systems();
+      set_error("cd_batch_persistent: systems on different Boys tables");
+      return CD_EINVAL;
+    }
+  // ---- waves: systems largest first (CTAs scan them in this order), each put
+  // into the first wave whose buffers still fit the budget; one launch per wave
   size_t freeb = 0, totb = 0;
   CD_CUDA(cudaMemGetInfo(&freeb, &totb));
   const double budget = opts[0].mem_budget_gb > 0 ? opts[0].mem_budget_gb * 1e9 : 0.9 * (double)freeb;
-  if ((double)total > budget) {
-    release_systems();
-    set_error("cd_batch_persistent: device memory for the batch (" + std::to_string(total / 1e9) +
-              " GB) exceeds the budget (" + std::to_string(budget / 1e9) + " GB)");
-    return CD_ENOMEM;
+  std::vector<int> order(n_sys);
+  for (int i = 0; i < n_sys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)plan[a].n * plan[a].N > (double)plan[b].n * plan[b].N;
+  });
+  std::vector<std::vector<int>> waves;
+  std::vector<size_t> wave_bytes;
+  for (int i : order) {
+    if ((double)plan[i].bytes > budget) {
+      release_systems();
+      set_error("cd_batch_persistent: system " + std::to_string(i) + ": its device memory (" +
+                std::to_string(plan[i].bytes / 1e9) + " GB) exceeds the budget (" + std::to_string(budget / 1e9) +
+                " GB)");
+      return CD_ENOMEM;
+    }
+    size_t w = 0;
+    while (w < waves.size() && (double)(wave_bytes[w] + plan[i].bytes) > budget) ++w;
+    if (w == waves.size()) {
+      waves.emplace_back();
+      wave_bytes.push_back(0);
+    }
+    waves[w].push_back(i);
+    wave_bytes[w] += plan[i].bytes;
+  }
+  size_t max_wave = 0, max_sys = 0;
+  for (size_t w = 0; w < waves.size(); ++w) {
+    max_wave = std::max(max_wave, wave_bytes[w]);
+    max_sys = std::max(max_sys, waves[w].size());
   }
   unsigned char* arena = nullptr;
-  if (cudaMalloc(&arena, total) != cudaSuccess) {
-    cudaGetLastError();
-    release_systems();
-    set_error("cd_batch_persistent: cudaMalloc of " + std::to_string(total) + " bytes failed");
-    return CD_ENOMEM;
-  }
   SysDesc* desc_dev = nullptr;
   BatchCtl* ctl_dev = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int rc = CD_OK;
-  std::vector<SysState> hst(n_sys);
-  auto cleanup = [&]() {
+  auto free_wave = [&]() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  };
+  auto cleanup = [&]() {
+    free_wave();
     if (cs) cudaStreamDestroy(cs);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -1841,131 +1867,22 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
       return fail(CD_ECUDA);                                                            \
     }                                                                                   \
   } while (0)
-  BP_CUDA(cudaMalloc(&desc_dev, sizeof(SysDesc) * n_sys));
+  // one arena the size of the largest wave, reused by every wave
+  if (cudaMalloc(&arena, max_wave) != cudaSuccess) {
+    cudaGetLastError();
+    arena = nullptr;
+    set_error("cd_batch_persistent: cudaMalloc of " + std::to_string(max_wave) + " bytes failed");
+    return fail(CD_ENOMEM);
+  }
+  BP_CUDA(cudaMalloc(&desc_dev, sizeof(SysDesc) * max_sys));
   BP_CUDA(cudaMalloc(&ctl_dev, sizeof(BatchCtl)));
   BP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   BP_CUDA(cudaEventCreate(&e0));
   BP_CUDA(cudaEventCreate(&e1));
   BP_CUDA(cudaStreamSynchronize(ust));
-  // systems largest first: CTAs scan them in this order
-  std::vector<int> order(n_sys);
-  for (int i = 0; i < n_sys; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-    return (double)plan[a].n * plan[a].N > (double)plan[b].n * plan[b].N;
-  });
-  std::vector<SysDesc> hd(n_sys);
-  std::vector<const double*> boys_of(n_sys);
-  for (int k = 0; k < n_sys; ++k) {
-    const int i = order[k];
-    cd_system* s = systems[i];
-    Plan& p = plan[i];
-    auto at = [&](int slot) { return (void*)(arena + p.off[slot]); };
-    SysDesc& d = hd[k];
-    memset(&d, 0, sizeof(d));
-    d.n = p.n;
-    d.ld = p.ld;
-    d.Mcap = p.Mcap;
-    d.N = p.N;
-    d.O = p.O;
-    d.Op = p.Op;
-    d.b = p.b;
-    d.tau = opts[i].tau;
-    double d1max = 0.0;
-    for (double v : s->row_diag) d1max = std::max(d1max, v);
-    d.neg_tol = -1e-10 * d1max;
-    d.bra = s->bra;
-    d.ket = s->all;
-    for (int c = 0; c < 4; ++c) {
-      d.cls[c] = s->bra_class_off[c];
-      d.all_cls[c] = s->all_class_off[c];
-    }
-    for (int c = 0; c < 3; ++c) d.ntile[c] = (int)((d.cls[c + 1] - d.cls[c] + 127) / 128);
-    d.nsplit_cap = p.nsplit;
-    d.nnz = p.csr_off[p.N];
-    d.D0 = (double*)at(0);
-    d.D1 = (double*)at(1);
-    d.pool = (double*)at(2);
-    d.L = (double*)at(3);
-    d.piv = (int64_t*)at(4);
-    d.pivd = (double*)at(5);
-    d.Bg0 = (double*)at(6);
-    d.Bg1 = (double*)at(7);
-    d.groups = (KetGroup*)at(8);
-    d.part_val = (double*)at(9);
-    d.part_idx = (int64_t*)at(10);
-    d.dpk = (double*)at(11);
-    d.v = (double*)at(12);
-    d.Jp = (double*)at(13);
-    d.B = (double*)at(14);
-    d.Kpart = (double*)at(15);
-    d.J = (double*)at(16);
-    d.Kx = (double*)at(17);
-    d.st = (SysState*)at(18);
-    d.C = (const double*)at(19);
-    d.csr_off = (const int32_t*)at(20);
-    d.csr_nu = (const int32_t*)at(21);
-    d.csr_row = (const int32_t*)at(22);
-    unsigned char* rt = (unsigned char*)at(23);
-    d.row_allsp = (const int32_t*)rt;
-    d.row_kc = (const int8_t*)(rt + align256(sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n)));
-    d.row_kd = d.row_kc + align256((size_t)std::max<int64_t>(1, p.n));
-    d.row_mu = s->row_mu_dev;
-    d.row_nu = s->row_nu_dev;
-    d.tc = opts[i].update == CD_UPDATE_SLICE ? 1 : 0;
-    d.erow = (const int32_t*)at(24);
-    d.Bsl = (__nv_bfloat16*)at(25);
-    d.bpitch = p.bpitch;
-    d.Ls = (__nv_bfloat16*)at(26);
-    d.Lblk = (double*)at(27);
-    if (d.tc) d.L = nullptr;
-    {
-      // row exponents: sqrt(D^1_r) < 2^e_r (frexp), so every |L^K_r| / 2^e_r <= 1
-      std::vector<int32_t> er(std::max<int64_t>(1, p.n), 0);
-      for (int64_t r = 0; r < p.n; ++r) {
-        int ex = 0;
-        if (s->row_diag[r] > 0.0) std::frexp(std::sqrt(s->row_diag[r]), &ex);
-        er[r] = ex;
-      }
-      BP_CUDA(cudaMemcpyAsync((void*)d.erow, er.data(), sizeof(int32_t) * er.size(), cudaMemcpyHostToDevice, cs));
-    }
-    boys_of[k] = s->boys;
-    // uploads
-    SysState h;
-    memset(&h, 0, sizeof(h));
-    h.word = job_word(1, 1, 0);
-    h.type = kJobSelect;
-    h.dmax = p.dmax;
-    h.idx = p.idx;
-    for (int x = 0; x < kBMaxB; ++x) h.slot_row[x] = -1;
-    BP_CUDA(cudaMemcpyAsync(d.st, &h, sizeof(h), cudaMemcpyHostToDevice, cs));
-    BP_CUDA(cudaMemcpyAsync(d.D0, s->diag_dev, sizeof(double) * p.ld, cudaMemcpyDeviceToDevice, cs));
-    {
-      std::vector<double> cp((size_t)p.N * p.Op + 80, 0.0);
-      for (int mu = 0; mu < p.N; ++mu)
-        for (int k = 0; k < p.O; ++k) cp[(size_t)mu * p.Op + k] = C_occ[i][(size_t)mu * p.O + k];
-      BP_CUDA(cudaMemcpyAsync((void*)d.C, cp.data(), sizeof(double) * cp.size(), cudaMemcpyHostToDevice, cs));
-      BP_CUDA(cudaStreamSynchronize(cs));   // cp is a temporary
-    }
-    BP_CUDA(cudaMemcpyAsync((void*)d.csr_off, p.csr_off.data(), sizeof(int32_t) * p.csr_off.size(), cudaMemcpyHostToDevice, cs));
-    BP_CUDA(cudaMemcpyAsync((void*)d.csr_nu, p.csr_nu.data(), sizeof(int32_t) * p.csr_nu.size(), cudaMemcpyHostToDevice, cs));
-    BP_CUDA(cudaMemcpyAsync((void*)d.csr_row, p.csr_row.data(), sizeof(int32_t) * p.csr_row.size(), cudaMemcpyHostToDevice, cs));
-    if (p.n > 0) {
-      BP_CUDA(cudaMemcpyAsync((void*)d.row_allsp, s->row_allsp.data(), sizeof(int32_t) * p.n, cudaMemcpyHostToDevice, cs));
-      BP_CUDA(cudaMemcpyAsync((void*)d.row_kc, s->row_kc.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
-      BP_CUDA(cudaMemcpyAsync((void*)d.row_kd, s->row_kd.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
-    }
-  }
-  for (int k = 1; k < n_sys; ++k)
-    if (boys_of[k] != boys_of[0]) {
-      set_error("cd_batch_persistent: systems on different Boys tables");
-      return fail(CD_EINVAL);
-    }
-  BP_CUDA(cudaMemcpyAsync(desc_dev, hd.data(), sizeof(SysDesc) * n_sys, cudaMemcpyHostToDevice, cs));
-  BP_CUDA(cudaStreamSynchronize(cs));
-  const double t_upload = now_ms();
-  // ---- the launch, recorded in a CUDA graph: clear J and the control block, one persistent kernel
+  // the kernel build and its grid: the tensor-core build if any system wants it
   int use_tc = 0;
-  for (int k = 0; k < n_sys; ++k) use_tc |= hd[k].tc;
+  for (int i = 0; i < n_sys; ++i) use_tc |= opts[i].update == CD_UPDATE_SLICE ? 1 : 0;
   auto kfn = use_tc ? batch_kernel<true> : batch_kernel<false>;
   int per_sm = 0, sms = 0;
   BP_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, kDynSmem));
@@ -1988,80 +1905,208 @@ extern "C" int cd_batch_persistent(int32_t n_sys, const cd_basis_t* bases, const
   // at most two CTAs per SM (each would hold half of the SM's tensor memory)
   const int grid = std::max(1, std::min(per_sm, 2)) * sms;
   if (getenv("CDERI_DEBUG"))
-    fprintf(stderr, "[cderi] batch_kernel<%s>: %d CTAs per SM, grid %d\n", use_tc ? "tensor-core update" : "FP64",
-            per_sm, grid);
+    fprintf(stderr, "[cderi] batch_kernel<%s>: %d CTAs per SM, grid %d, %zu wave(s)\n",
+            use_tc ? "tensor-core update" : "FP64", per_sm, grid, waves.size());
   const long long wait_ns = (long long)device_wait_limit_ns();
-  BP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < n_sys; ++k) {
-    cudaMemsetAsync(hd[k].J, 0, sizeof(double) * (size_t)hd[k].N * hd[k].N, cs);
-    // the slice store starts at zero: the last 32-vector block of a system is read whole by the update
-    if (hd[k].tc)
-      cudaMemsetAsync(hd[k].Ls, 0,
-                      (size_t)((hd[k].Mcap + kTcBK - 1) / kTcBK) * kTcSlices * (size_t)std::max<int64_t>(1, hd[k].n) *
-                          kTcBK * 2, cs);
-  }
-  cudaMemsetAsync(ctl_dev, 0, sizeof(BatchCtl), cs);
-  kfn<<<grid, kBT, kDynSmem, cs>>>(desc_dev, n_sys, ctl_dev, boys_of[0], wait_ns);
-  BP_CUDA(cudaStreamEndCapture(cs, &graph));
-  BP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-  BP_CUDA(cudaEventRecord(e0, cs));
-  BP_CUDA(cudaGraphLaunch(exec, cs));
-  count_launch();
-  BP_CUDA(cudaEventRecord(e1, cs));
-  BP_CUDA(cudaStreamSynchronize(cs));
-  float kms = 0.0f;
-  cudaEventElapsedTime(&kms, e0, e1);
-  BatchCtl hctl;
-  BP_CUDA(cudaMemcpy(&hctl, ctl_dev, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
-  for (int k = 0; k < n_sys; ++k) BP_CUDA(cudaMemcpy(&hst[k], hd[k].st, sizeof(SysState), cudaMemcpyDeviceToHost));
-  if (hctl.tc_err) {
-    set_error("cd_batch_persistent: a bounded tensor-core wait gave up (MMA completion)");
-    return fail(CD_ETIMEOUT);
-  }
-  if (hctl.timed_out) {
-    set_error("cd_batch_persistent: a CTA's wait for work gave up after the wait limit with no item completed");
-    return fail(CD_ETIMEOUT);
-  }
-  for (int k = 0; k < n_sys; ++k) {
-    const int i = order[k];
-    if (hst[k].status != CD_OK || hst[k].type != kJobNone) {
-      const int code = hst[k].status != CD_OK ? hst[k].status : CD_ETIMEOUT;
-      std::string why = code == CD_ENOTPSD ? "matrix not PSD (pivot diagonal <= 0 or residual below -1e-10 max D)"
-                        : code == CD_ENOMEM ? "number of vectors exceeds max_vectors = " + std::to_string(plan[i].Mcap)
-                                            : "decomposition did not finish";
-      set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + why);
-      return fail(code);
+  double upload_ms = 0.0, launch_host_ms = 0.0, device_ms = 0.0;
+  BatchCtl sum;
+  memset(&sum, 0, sizeof(sum));
+  for (size_t w = 0; w < waves.size(); ++w) {
+    const std::vector<int>& members = waves[w];
+    const int nw = (int)members.size();
+    const double tw0 = now_ms();
+    std::vector<SysDesc> hd(nw);
+    size_t base = 0;
+    for (int k = 0; k < nw; ++k) {
+      const int i = members[k];
+      cd_system* s = systems[i];
+      Plan& p = plan[i];
+      unsigned char* sys_base = arena + base;
+      base += p.bytes;
+      auto at = [&](int slot) { return (void*)(sys_base + p.off[slot]); };
+      SysDesc& d = hd[k];
+      memset(&d, 0, sizeof(d));
+      d.n = p.n;
+      d.ld = p.ld;
+      d.Mcap = p.Mcap;
+      d.N = p.N;
+      d.O = p.O;
+      d.Op = p.Op;
+      d.b = p.b;
+      d.tau = opts[i].tau;
+      double d1max = 0.0;
+      for (double v : s->row_diag) d1max = std::max(d1max, v);
+      d.neg_tol = -1e-10 * d1max;
+      d.bra = s->bra;
+      d.ket = s->all;
+      for (int c = 0; c < 4; ++c) {
+        d.cls[c] = s->bra_class_off[c];
+        d.all_cls[c] = s->all_class_off[c];
+      }
+      for (int c = 0; c < 3; ++c) d.ntile[c] = (int)((d.cls[c + 1] - d.cls[c] + 127) / 128);
+      d.nsplit_cap = p.nsplit;
+      d.nnz = p.csr_off[p.N];
+      d.D0 = (double*)at(0);
+      d.D1 = (double*)at(1);
+      d.pool = (double*)at(2);
+      d.L = (double*)at(3);
+      d.piv = (int64_t*)at(4);
+      d.pivd = (double*)at(5);
+      d.Bg0 = (double*)at(6);
+      d.Bg1 = (double*)at(7);
+      d.groups = (KetGroup*)at(8);
+      d.part_val = (double*)at(9);
+      d.part_idx = (int64_t*)at(10);
+      d.dpk = (double*)at(11);
+      d.v = (double*)at(12);
+      d.Jp = (double*)at(13);
+      d.B = (double*)at(14);
+      d.Kpart = (double*)at(15);
+      d.J = (double*)at(16);
+      d.Kx = (double*)at(17);
+      d.st = (SysState*)at(18);
+      d.C = (const double*)at(19);
+      d.csr_off = (const int32_t*)at(20);
+      d.csr_nu = (const int32_t*)at(21);
+      d.csr_row = (const int32_t*)at(22);
+      unsigned char* rt = (unsigned char*)at(23);
+      d.row_allsp = (const int32_t*)rt;
+      d.row_kc = (const int8_t*)(rt + align256(sizeof(int32_t) * (size_t)std::max<int64_t>(1, p.n)));
+      d.row_kd = d.row_kc + align256((size_t)std::max<int64_t>(1, p.n));
+      d.row_mu = s->row_mu_dev;
+      d.row_nu = s->row_nu_dev;
+      d.tc = opts[i].update == CD_UPDATE_SLICE ? 1 : 0;
+      d.erow = (const int32_t*)at(24);
+      d.Bsl = (__nv_bfloat16*)at(25);
+      d.bpitch = p.bpitch;
+      d.Ls = (__nv_bfloat16*)at(26);
+      d.Lblk = (double*)at(27);
+      if (d.tc) d.L = nullptr;
+      {
+        // row exponents: sqrt(D^1_r) < 2^e_r (frexp), so every |L^K_r| / 2^e_r <= 1
+        std::vector<int32_t> er(std::max<int64_t>(1, p.n), 0);
+        for (int64_t r = 0; r < p.n; ++r) {
+          int ex = 0;
+          if (s->row_diag[r] > 0.0) std::frexp(std::sqrt(s->row_diag[r]), &ex);
+          er[r] = ex;
+        }
+        BP_CUDA(cudaMemcpyAsync((void*)d.erow, er.data(), sizeof(int32_t) * er.size(), cudaMemcpyHostToDevice, cs));
+        BP_CUDA(cudaStreamSynchronize(cs));   // er is a temporary
+      }
+      // uploads
+      SysState h;
+      memset(&h, 0, sizeof(h));
+      h.word = job_word(1, 1, 0);
+      h.type = kJobSelect;
+      h.dmax = p.dmax;
+      h.idx = p.idx;
+      for (int x = 0; x < kBMaxB; ++x) h.slot_row[x] = -1;
+      BP_CUDA(cudaMemcpyAsync(d.st, &h, sizeof(h), cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaMemcpyAsync(d.D0, s->diag_dev, sizeof(double) * p.ld, cudaMemcpyDeviceToDevice, cs));
+      {
+        std::vector<double> cp((size_t)p.N * p.Op + 80, 0.0);
+        for (int mu = 0; mu < p.N; ++mu)
+          for (int k2 = 0; k2 < p.O; ++k2) cp[(size_t)mu * p.Op + k2] = C_occ[i][(size_t)mu * p.O + k2];
+        BP_CUDA(cudaMemcpyAsync((void*)d.C, cp.data(), sizeof(double) * cp.size(), cudaMemcpyHostToDevice, cs));
+        BP_CUDA(cudaStreamSynchronize(cs));   // cp and h are temporaries
+      }
+      BP_CUDA(cudaMemcpyAsync((void*)d.csr_off, p.csr_off.data(), sizeof(int32_t) * p.csr_off.size(), cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaMemcpyAsync((void*)d.csr_nu, p.csr_nu.data(), sizeof(int32_t) * p.csr_nu.size(), cudaMemcpyHostToDevice, cs));
+      BP_CUDA(cudaMemcpyAsync((void*)d.csr_row, p.csr_row.data(), sizeof(int32_t) * p.csr_row.size(), cudaMemcpyHostToDevice, cs));
+      if (p.n > 0) {
+        BP_CUDA(cudaMemcpyAsync((void*)d.row_allsp, s->row_allsp.data(), sizeof(int32_t) * p.n, cudaMemcpyHostToDevice, cs));
+        BP_CUDA(cudaMemcpyAsync((void*)d.row_kc, s->row_kc.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
+        BP_CUDA(cudaMemcpyAsync((void*)d.row_kd, s->row_kd.data(), (size_t)p.n, cudaMemcpyHostToDevice, cs));
+      }
     }
+    BP_CUDA(cudaMemcpyAsync(desc_dev, hd.data(), sizeof(SysDesc) * nw, cudaMemcpyHostToDevice, cs));
+    BP_CUDA(cudaStreamSynchronize(cs));
+    const double tw1 = now_ms();
+    upload_ms += tw1 - tw0;
+    // ---- the launch, recorded in a CUDA graph: clear J, the slice store and the
+    // control block, one persistent kernel
+    BP_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < nw; ++k) {
+      cudaMemsetAsync(hd[k].J, 0, sizeof(double) * (size_t)hd[k].N * hd[k].N, cs);
+      // the slice store starts at zero: the last 32-vector block of a system is read whole by the update
+      if (hd[k].tc)
+        cudaMemsetAsync(hd[k].Ls, 0,
+                        (size_t)((hd[k].Mcap + kTcBK - 1) / kTcBK) * kTcSlices * (size_t)std::max<int64_t>(1, hd[k].n) *
+                            kTcBK * 2, cs);
+    }
+    cudaMemsetAsync(ctl_dev, 0, sizeof(BatchCtl), cs);
+    kfn<<<grid, kBT, kDynSmem, cs>>>(desc_dev, nw, ctl_dev, systems[0]->boys, wait_ns);
+    BP_CUDA(cudaStreamEndCapture(cs, &graph));
+    BP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    BP_CUDA(cudaEventRecord(e0, cs));
+    BP_CUDA(cudaGraphLaunch(exec, cs));
+    count_launch();
+    BP_CUDA(cudaEventRecord(e1, cs));
+    BP_CUDA(cudaStreamSynchronize(cs));
+    float kms = 0.0f;
+    cudaEventElapsedTime(&kms, e0, e1);
+    device_ms += kms;
+    BatchCtl hctl;
+    std::vector<SysState> hst(nw);
+    BP_CUDA(cudaMemcpy(&hctl, ctl_dev, sizeof(BatchCtl), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < nw; ++k) BP_CUDA(cudaMemcpy(&hst[k], hd[k].st, sizeof(SysState), cudaMemcpyDeviceToHost));
+    if (hctl.tc_err) {
+      set_error("cd_batch_persistent: a bounded tensor-core wait gave up (MMA completion)");
+      return fail(CD_ETIMEOUT);
+    }
+    if (hctl.timed_out) {
+      set_error("cd_batch_persistent: a CTA's wait for work gave up after the wait limit with no item completed");
+      return fail(CD_ETIMEOUT);
+    }
+    for (int k = 0; k < nw; ++k) {
+      const int i = members[k];
+      if (hst[k].status != CD_OK || hst[k].type != kJobNone) {
+        const int code = hst[k].status != CD_OK ? hst[k].status : CD_ETIMEOUT;
+        std::string why = code == CD_ENOTPSD ? "matrix not PSD (pivot diagonal <= 0 or residual below -1e-10 max D)"
+                          : code == CD_ENOMEM ? "number of vectors exceeds max_vectors = " + std::to_string(plan[i].Mcap)
+                                              : "decomposition did not finish";
+        set_error("cd_batch_persistent: system " + std::to_string(i) + ": " + why);
+        return fail(code);
+      }
+    }
+    for (int k = 0; k < nw; ++k) {
+      const int i = members[k];
+      const size_t N2 = (size_t)hd[k].N * hd[k].N;
+      BP_CUDA(cudaMemcpy(J[i], hd[k].J, sizeof(double) * N2, cudaMemcpyDeviceToHost));
+      BP_CUDA(cudaMemcpy(K[i], hd[k].Kx, sizeof(double) * N2, cudaMemcpyDeviceToHost));
+      if (M_out) M_out[i] = hst[k].K;
+    }
+    for (int k = 0; k < kJobKinds; ++k) {
+      sum.kind_ns[k] += hctl.kind_ns[k];
+      sum.kind_ops[k] += hctl.kind_ops[k];
+    }
+    sum.idle_ns += hctl.idle_ns;
+    for (int k = 0; k < 4; ++k) sum.tc_ns[k] += hctl.tc_ns[k];
+    free_wave();
+    launch_host_ms += now_ms() - tw1;
   }
-  for (int k = 0; k < n_sys; ++k) {
-    const int i = order[k];
-    const size_t N2 = (size_t)hd[k].N * hd[k].N;
-    BP_CUDA(cudaMemcpy(J[i], hd[k].J, sizeof(double) * N2, cudaMemcpyDeviceToHost));
-    BP_CUDA(cudaMemcpy(K[i], hd[k].Kx, sizeof(double) * N2, cudaMemcpyDeviceToHost));
-    if (M_out) M_out[i] = hst[k].K;
-  }
-  const double t_end = now_ms();
   if (stats) {
     stats[0] = t_setup - t0;       // system set-up (host workers)
-    stats[1] = t_upload - t_setup; // sizes, row lists, uploads
-    stats[2] = kms;                // the graph launch (one persistent kernel), device time
-    stats[3] = t_end - t_upload;   // launch, wait and read-back, host time
+    stats[1] = upload_ms;          // descriptors and uploads, all waves
+    stats[2] = device_ms;          // the graph launches (one persistent kernel each), device time
+    stats[3] = launch_host_ms;     // launches, waits and read-back, host time
     stats[4] = (double)grid;
-    stats[5] = (double)total;
+    stats[5] = (double)max_wave;   // bytes reserved (the largest wave's)
     // CTA-seconds per item kind: 1 select, 2 gather, 3 update, 4 step, 5 density, 6 v = L d,
     // 7 J_p = L^T v, 8 J unpack, 10 ERI columns, 13 B = L C, 14 partial K tiles, 15 K sum; 16 idle
     for (int k = 0; k < kJobKinds; ++k) stats[6 + k] = 0.0;
     const int kinds[][2] = {{1, kJobSelect}, {2, kJobCols}, {3, kJobUpdate}, {4, kJobStep}, {5, kJobJk1},
                             {6, kJobJk2}, {7, kJobJk3}, {8, kJobJk4}, {9, kJobSlice}, {10, kJobCols + 8},
                             {13, kJobJk1 + 8}, {14, kJobJk2 + 8}, {15, kJobJk3 + 8}};
-    for (auto& kk : kinds) stats[6 + kk[0]] = (double)hctl.kind_ns[kk[1]] * 1e-9;
-    stats[6 + 16] = (double)hctl.idle_ns * 1e-9;
+    for (auto& kk : kinds) stats[6 + kk[0]] = (double)sum.kind_ns[kk[1]] * 1e-9;
+    stats[6 + 16] = (double)sum.idle_ns * 1e-9;
     if (getenv("CDERI_DEBUG"))
       fprintf(stderr, "[cderi] tensor-core update items, thread-0 seconds: copies %.2f, MMA %.2f, drain %.2f, result %.2f\n",
-              hctl.tc_ns[0] * 1e-9, hctl.tc_ns[1] * 1e-9, hctl.tc_ns[2] * 1e-9, hctl.tc_ns[3] * 1e-9);
-    for (int k = 0; k < kJobKinds; ++k) stats[23 + k] = (double)hctl.kind_ops[k];
+              sum.tc_ns[0] * 1e-9, sum.tc_ns[1] * 1e-9, sum.tc_ns[2] * 1e-9, sum.tc_ns[3] * 1e-9);
+    for (int k = 0; k < kJobKinds; ++k) stats[23 + k] = (double)sum.kind_ops[k];
+    stats[39] = (double)waves.size();
   }
   cleanup();
-  return rc;
+  return CD_OK;
 #undef BP_CUDA
 }

@@ -3,7 +3,8 @@
 plain single-system FP64 call (same recursion, Sec. 2; J/K of Sec. 4.1 summed
 in another order), all seven are checked against the CPU oracle, and the
 error paths (M = 0, vector capacity, bad arguments, the bounded wait for
-work) return their codes without disturbing the device."""
+work) return their codes without disturbing the device.  A memory budget below
+the batch's buffers splits it into waves with the same results."""
 import numpy as np
 import pytest
 
@@ -97,6 +98,29 @@ def test_persistent_capacity_and_arguments():
     with pytest.raises(cd.CDError) as e:
         cd.batch_persistent(systems)
     assert e.value.code == cd.CD_EINVAL and "system 0" in str(e.value)
+
+
+@pytest.mark.parametrize("update", ["slice", "fp64"])
+def test_persistent_waves_under_a_small_budget(update):
+    # a budget below the whole batch's buffers: the systems run in several
+    # waves, one launch each on one reused device buffer (not cleared between
+    # waves), with the same vector counts and J/K as in one wave
+    import paper_2609_00306_b300 as cd
+    systems = _uneven_batch()
+    upd = cd.CD_UPDATE_SLICE if update == "slice" else cd.CD_UPDATE_FP64
+    J1, K1, M1, info1 = cd.batch_persistent(systems, update=upd)
+    assert info1["waves"] == 1
+    # the largest system (N = 96) holds about half of the bytes (they grow as N^3)
+    budget = 0.7 * info1["bytes"]
+    Jw, Kw, Mw, infow = cd.batch_persistent(systems, update=upd, mem_budget_gb=budget / 1e9)
+    assert infow["waves"] >= 2 and infow["bytes"] <= budget
+    assert Mw == M1
+    for k in range(len(systems)):
+        assert _rel(Jw[k], J1[k]) <= 1e-12 and _rel(Kw[k], K1[k]) <= 1e-12
+    # one system alone over the budget: CD_ENOMEM naming the system, before any device work
+    with pytest.raises(cd.CDError) as e:
+        cd.batch_persistent(systems, update=upd, mem_budget_gb=1e-6)
+    assert e.value.code == cd.CD_ENOMEM and "system" in str(e.value) and "budget" in str(e.value)
 
 
 def test_persistent_wait_limit_times_out_then_recovers():
