@@ -59,8 +59,9 @@ __global__ void __launch_bounds__(128) eri_diag_kernel(PairSet ps, int64_t s0, i
   if (r < 0) return;
   double v[1][9];
   const int kcs[1] = {c / 3}, kds[1] = {c % 3};
+  const int ax[3] = {0, 1, 2};
   unsigned n_table = 0;
-  quartet<LA, LB, LA, LB, 1>(ps, sp, ps, sp, kcs, kds, tab, v, n_table);
+  quartet<LA, LB, LA, LB, 1>(ps, sp, ps, sp, kcs, kds, ax, tab, v, n_table);
   diag[r] = v[0][c];
 }
 

@@ -75,10 +75,24 @@ __device__ __forceinline__ double sel3(const double (&v)[3], int k) {
 // belong to one ket shell pair).  out[c][i*3+j] receives (a_i b_j | c_kc d_kd)
 // for ket component c and the bra components (i on A, j on B).  The primitive
 // set-up, Boys function and bra recurrence are shared by the NC components.
-template <int LA, int LB, int LC, int LD, int NC>
+//
+// KC >= 0 (one ket component, NC = 1): the Cartesian axes are relabelled,
+// axis x of the computation being axis ax[x] of the input, so that the ket
+// component is (c_KC d_KD) with KC = 0 and KD = 0 (c = d) or 1 (c != d).  The
+// Gaussians are isotropic and the recurrences the same along every axis, so
+// the integrals of the relabelled frame are those of the input with the
+// component indices mapped through ax.  With the ket directions known at
+// compile time the terms of the recurrences that carry a Kronecker delta
+// (N_k(e) / 2s, delta_kl / 2q) exist only where they are non-zero.  out is then
+// indexed in the relabelled frame.
+template <int LA, int LB, int LC, int LD, int NC, int KC = -1, int KD = -1>
 __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const PairSet& ket, int64_t sk,
-                                        const int (&kcs)[NC], const int (&kds)[NC], const double* __restrict__ tab,
-                                        double (&out)[NC][9], unsigned& n_table) {
+                                        const int (&kcs)[NC], const int (&kds)[NC], const int (&ax)[3],
+                                        const double* __restrict__ tab, double (&out)[NC][9], unsigned& n_table) {
+  constexpr bool SPEC = KC >= 0;
+  static_assert(!SPEC || (NC == 1 && KC == 0 && (KD == 0 || KD == 1) && LC + LD >= 1), "bad ket specialisation");
+  // input offsets of the three axes (0, 1, 2 unless relabelled)
+  const int x0 = SPEC ? ax[0] : 0, x1 = SPEC ? ax[1] : 1, x2 = SPEC ? ax[2] : 2;
   constexpr int EB = LA + LB;
   constexpr int FK = LC + LD;
   constexpr int L = EB + FK;
@@ -96,16 +110,16 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
   const int k0 = __ldg(ket.pp_off + sk), k1 = __ldg(ket.pp_off + sk + 1);
   for (int ib = b0; ib < b1; ++ib) {
     const double p = __ldg(bra.zeta + ib);
-    const double Px = __ldg(bra.P + 3 * ib), Py = __ldg(bra.P + 3 * ib + 1), Pz = __ldg(bra.P + 3 * ib + 2);
+    const double Px = __ldg(bra.P + 3 * ib + x0), Py = __ldg(bra.P + 3 * ib + x1), Pz = __ldg(bra.P + 3 * ib + x2);
     double PA[3];
-    PA[0] = __ldg(bra.PA + 3 * ib); PA[1] = __ldg(bra.PA + 3 * ib + 1); PA[2] = __ldg(bra.PA + 3 * ib + 2);
+    PA[0] = __ldg(bra.PA + 3 * ib + x0); PA[1] = __ldg(bra.PA + 3 * ib + x1); PA[2] = __ldg(bra.PA + 3 * ib + x2);
     const double Kb = __ldg(bra.Kp + ib);
     for (int ik = k0; ik < k1; ++ik) {
       const double q = __ldg(ket.zeta + ik);
       double PQ[3];
-      PQ[0] = Px - __ldg(ket.P + 3 * ik);
-      PQ[1] = Py - __ldg(ket.P + 3 * ik + 1);
-      PQ[2] = Pz - __ldg(ket.P + 3 * ik + 2);
+      PQ[0] = Px - __ldg(ket.P + 3 * ik + x0);
+      PQ[1] = Py - __ldg(ket.P + 3 * ik + x1);
+      PQ[2] = Pz - __ldg(ket.P + 3 * ik + x2);
       const double s = p + q;
       // y = 1/sqrt(s): FP32 seed (rel. error < 2^-22), two Newton steps in FP64 (error < 2^-88)
       double y = (double)rsqrtf((float)s);
@@ -158,7 +172,7 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
       } else {
         const double pis = p * is;
         double QC[3];
-        QC[0] = __ldg(ket.PA + 3 * ik); QC[1] = __ldg(ket.PA + 3 * ik + 1); QC[2] = __ldg(ket.PA + 3 * ik + 2);
+        QC[0] = __ldg(ket.PA + 3 * ik + x0); QC[1] = __ldg(ket.PA + 3 * ik + x1); QC[2] = __ldg(ket.PA + 3 * ik + x2);
         double WQ3[3] = {pis * PQ[0], pis * PQ[1], pis * PQ[2]};
         const double o2s = 0.5 * is;
         constexpr int MF = FK;
@@ -183,8 +197,15 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
 #pragma unroll
                 for (int j = i; j < 3; ++j) {
                   double v = fma(QCk, e2[didx(i, j)][m], WQk * e2[didx(i, j)][m + 1]);
-                  double lower = (i == kc ? e1[j][m + 1] : 0.0) + (j == kc ? e1[i][m + 1] : 0.0);
-                  f1d[didx(i, j)][m] = fma(o2s, lower, v);
+                  if constexpr (SPEC) {
+                    if (i == KC && j == KC) v = fma(o2s, e1[i][m + 1] + e1[j][m + 1], v);
+                    else if (i == KC) v = fma(o2s, e1[j][m + 1], v);
+                    else if (j == KC) v = fma(o2s, e1[i][m + 1], v);
+                  } else {
+                    double lower = (i == kc ? e1[j][m + 1] : 0.0) + (j == kc ? e1[i][m + 1] : 0.0);
+                    v = fma(o2s, lower, v);
+                  }
+                  f1d[didx(i, j)][m] = v;
                 }
             }
           }
@@ -203,19 +224,22 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
             }
           } else {
             const double QCl = sel3(QC, kd), WQl = sel3(WQ3, kd);
-            const double o2q = __ldg(ket.o2z + ik), rq = pis;
-            const double dkl = (kc == kd) ? o2q : 0.0;
+            // d_kl / 2q: a runtime factor, or (relabelled frame) present only when KC == KD
+            constexpr bool DKL = !SPEC || KC == KD;
+            const double o2q = DKL ? __ldg(ket.o2z + ik) : 0.0, rq = pis;
+            const double dkl = SPEC ? o2q : ((kc == kd) ? o2q : 0.0);
             // [e|1k+1l] = QC_l [e|1k]^0 + WQ_l [e|1k]^1 + d_kl/(2q)([e|0]^0 - rho/q [e|0]^1) + e_l/(2s) [e-1_l|1k]^1
             if constexpr (EB == 0) {
               double v = fma(QCl, f1s[0], WQl * f1s[1]);
-              acc[cc][0][0] += fma(dkl, fma(-rq, S0[1], S0[0]), v);
+              if constexpr (DKL) v = fma(dkl, fma(-rq, S0[1], S0[0]), v);
+              acc[cc][0][0] += v;
               acc[cc][0][1] += f1s[0];
             }
             if constexpr (EB >= 1) {
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
                 double v = fma(QCl, f1p[i][0], WQl * f1p[i][1]);
-                v = fma(dkl, fma(-rq, e1[i][1], e1[i][0]), v);
+                if constexpr (DKL) v = fma(dkl, fma(-rq, e1[i][1], e1[i][0]), v);
                 if (i == kd) v = fma(o2s, f1s[1], v);
                 acc[cc][i][0] += v;
                 acc[cc][i][1] += f1p[i][0];
@@ -228,9 +252,15 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
                 for (int j = i; j < 3; ++j) {
                   const int t = didx(i, j);
                   double v = fma(QCl, f1d[t][0], WQl * f1d[t][1]);
-                  v = fma(dkl, fma(-rq, e2[t][1], e2[t][0]), v);
-                  double lower = (i == kd ? f1p[j][1] : 0.0) + (j == kd ? f1p[i][1] : 0.0);
-                  v = fma(o2s, lower, v);
+                  if constexpr (DKL) v = fma(dkl, fma(-rq, e2[t][1], e2[t][0]), v);
+                  if constexpr (SPEC) {
+                    if (i == KD && j == KD) v = fma(o2s, f1p[i][1] + f1p[j][1], v);
+                    else if (i == KD) v = fma(o2s, f1p[j][1], v);
+                    else if (j == KD) v = fma(o2s, f1p[i][1], v);
+                  } else {
+                    double lower = (i == kd ? f1p[j][1] : 0.0) + (j == kd ? f1p[i][1] : 0.0);
+                    v = fma(o2s, lower, v);
+                  }
                   acc[cc][3 + t][0] += v;
                   acc[cc][3 + t][1] += f1d[t][0];
                 }
@@ -253,8 +283,8 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
         } else {
 #pragma unroll
           for (int cc = 0; cc < NC; ++cc) {
-            level1(kcs[cc]);
-            accumulate(cc, kcs[cc], kds[cc]);
+            level1(SPEC ? KC : kcs[cc]);
+            accumulate(cc, SPEC ? KC : kcs[cc], SPEC ? KD : kds[cc]);
           }
         }
       }
@@ -262,18 +292,18 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
   }
   double CD3[3] = {0.0, 0.0, 0.0};
   if constexpr (FK == 2) {
-    CD3[0] = __ldg(ket.AB + 3 * sk); CD3[1] = __ldg(ket.AB + 3 * sk + 1); CD3[2] = __ldg(ket.AB + 3 * sk + 2);
+    CD3[0] = __ldg(ket.AB + 3 * sk + x0); CD3[1] = __ldg(ket.AB + 3 * sk + x1); CD3[2] = __ldg(ket.AB + 3 * sk + x2);
   }
   double AB3[3] = {0.0, 0.0, 0.0};
   if constexpr (LB == 1) {
-    AB3[0] = __ldg(bra.AB + 3 * sb); AB3[1] = __ldg(bra.AB + 3 * sb + 1); AB3[2] = __ldg(bra.AB + 3 * sb + 2);
+    AB3[0] = __ldg(bra.AB + 3 * sb + x0); AB3[1] = __ldg(bra.AB + 3 * sb + x1); AB3[2] = __ldg(bra.AB + 3 * sb + x2);
   }
 #pragma unroll
   for (int cc = 0; cc < NC; ++cc) {
     // ---- ket horizontal recurrence
     double val[NE];
     if constexpr (FK == 2) {
-      const double CDl = sel3(CD3, kds[cc]);
+      const double CDl = sel3(CD3, SPEC ? KD : kds[cc]);
 #pragma unroll
       for (int e = 0; e < NE; ++e) val[e] = fma(CDl, acc[cc][e][1], acc[cc][e][0]);
     } else {
@@ -306,24 +336,31 @@ __device__ __forceinline__ void quartet(const PairSet& bra, int64_t sb, const Pa
 //   branch 12 + 2L, both + (L+1) for S0; bra recurrence 4 + 6L (p) and
 //   1 + 18(L-1) more (d); ket: 5, level 1 per distinct kc FK x (2 | 9 | 33),
 //   per component NE adds (ket ss), NE adds (level 1 only) or 6 | 19 | 67 (pp).
-template <int EB, int FK, int NC>
+//   Relabelled frame (KC = 0): level 1 FK x (2 | 9 | 25); (pp) components
+//   6 | 19 | 59 when KD = KC, 4 | 13 | 41 when KD != KC.
+template <int EB, int FK, int NC, int KC = -1, int KD = -1>
 __device__ __forceinline__ unsigned fixed_ops(int n_level1) {
   constexpr int L = EB + FK;
   constexpr int NE = EB == 0 ? 1 : (EB == 1 ? 3 : 9);
+  constexpr bool SPEC = KC >= 0;
   int ops = 22 + (L + 1);
   if (EB >= 1) ops += 4 + 6 * L;
   if (EB == 2) ops += 1 + 18 * (L - 1);
   if (FK == 0) {
     ops += NE;
   } else {
-    const int lvl1 = FK * (EB == 0 ? 2 : (EB == 1 ? 9 : 33));
-    const int acc = FK == 1 ? NE : (EB == 0 ? 6 : (EB == 1 ? 19 : 67));
+    const int lvl1 = FK * (EB == 0 ? 2 : (EB == 1 ? 9 : (SPEC ? 25 : 33)));
+    int acc = FK == 1 ? NE : (EB == 0 ? 6 : (EB == 1 ? 19 : 67));
+    if (SPEC && FK == 2) acc = KC == KD ? (EB == 0 ? 6 : (EB == 1 ? 19 : 59)) : (EB == 0 ? 4 : (EB == 1 ? 13 : 41));
     ops += 5 + n_level1 * lvl1 + NC * acc;
   }
   return (unsigned)ops;
 }
 
-template <int LA, int LB, int LC, int LD, int NC>
+// KC >= 0: one ket component, evaluated in the relabelled frame of quartet()
+// (KD = 0 for c = d, 1 otherwise); the results are written back to the bra
+// rows of the input components.
+template <int LA, int LB, int LC, int LD, int NC, int KC = -1, int KD = -1>
 __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, const PairSet& ket, const KetGroup& kg,
                                              double* __restrict__ out, int64_t ld, const double* __restrict__ tab,
                                              unsigned long long& ops) {
@@ -333,9 +370,18 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     kcs[c] = c < kg.nc ? kg.kc[c] : kg.kc[0];
     kds[c] = c < kg.nc ? kg.kd[c] : kg.kd[0];
   }
+  // relabelled axes: computation axis x is input axis ax[x]; axis 0 carries the
+  // ket's c component and, for c != d, axis 1 its d component
+  int ax[3] = {0, 1, 2};
+  if constexpr (KC >= 0) {
+    const int c0 = kcs[0], d0 = kds[0];
+    ax[0] = c0;
+    ax[1] = (LC + LD == 2 && d0 != c0) ? d0 : (c0 == 2 ? 0 : c0 + 1);
+    ax[2] = 3 - ax[0] - ax[1];
+  }
   double v[NC][9];
   unsigned n_table = 0;
-  quartet<LA, LB, LC, LD, NC>(bra, sb, ket, kg.sp, kcs, kds, tab, v, n_table);
+  quartet<LA, LB, LC, LD, NC, KC, KD>(bra, sb, ket, kg.sp, kcs, kds, ax, tab, v, n_table);
   {
     constexpr int L = LA + LB + LC + LD;
     int n_level1 = NC;
@@ -349,7 +395,7 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     }
     const unsigned long long nq = (unsigned long long)(__ldg(bra.pp_off + sb + 1) - __ldg(bra.pp_off + sb)) *
                                   (unsigned long long)(__ldg(ket.pp_off + kg.sp + 1) - __ldg(ket.pp_off + kg.sp));
-    ops += nq * fixed_ops<LA + LB, LC + LD, NC>(n_level1) + (unsigned long long)n_table * (12 + (L == 1 ? 7 : (L > 1 ? 10 + 2 * L : 0))) +
+    ops += nq * fixed_ops<LA + LB, LC + LD, NC, KC, KD>(n_level1) + (unsigned long long)n_table * (12 + (L == 1 ? 7 : (L > 1 ? 10 + 2 * L : 0))) +
            (nq - n_table) * (12 + 2 * L);
   }
   const int32_t* rw = bra.row + 9 * sb;
@@ -361,7 +407,9 @@ __device__ __forceinline__ void column_block(const PairSet& bra, int64_t sb, con
     for (int c = 0; c < 9; ++c) {
       if (LA == 0 && c != 0) continue;
       if (LA == 1 && LB == 0 && (c % 3) != 0) continue;
-      const int32_t r = __ldg(rw + c);
+      // component c = 3 i + j of the computation frame is (ax[i], ax[j]) of the input
+      const int ci = KC < 0 ? c : (LA == 0 ? 0 : (LB == 0 ? 3 * ax[c / 3] : 3 * ax[c / 3] + ax[c % 3]));
+      const int32_t r = __ldg(rw + ci);
       if (r >= 0) o[r] = v[cc][c];
     }
   }
@@ -381,11 +429,14 @@ __device__ __forceinline__ void column_item(const PairSet& bra, const int64_t* _
     const int cls = kg.lc * 2 + kg.ld;
     if (cls == 0) column_block<LA, LB, 0, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
     else if (cls == 2) {
-      if (kg.nc == 1) column_block<LA, LB, 1, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
+      // single ket components in the relabelled frame (ket direction on axis 0)
+      if (kg.nc == 1) column_block<LA, LB, 1, 0, 1, 0, 0>(bra, sb, ket, kg, out, ld, tab, ops);
       else column_block<LA, LB, 1, 0, 3>(bra, sb, ket, kg, out, ld, tab, ops);
     } else {
-      if (kg.nc == 1) column_block<LA, LB, 1, 1, 1>(bra, sb, ket, kg, out, ld, tab, ops);
-      else if (kg.nc <= 3) column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab, ops);
+      if (kg.nc == 1) {
+        if (kg.kc[0] == kg.kd[0]) column_block<LA, LB, 1, 1, 1, 0, 0>(bra, sb, ket, kg, out, ld, tab, ops);
+        else column_block<LA, LB, 1, 1, 1, 0, 1>(bra, sb, ket, kg, out, ld, tab, ops);
+      } else if (kg.nc <= 3) column_block<LA, LB, 1, 1, 3>(bra, sb, ket, kg, out, ld, tab, ops);
       else column_block<LA, LB, 1, 1, kMaxKetGroup>(bra, sb, ket, kg, out, ld, tab, ops);
     }
   }
