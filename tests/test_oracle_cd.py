@@ -72,8 +72,11 @@ def test_residual_bounded_by_tau(s40, sp8):
         assert np.max(np.abs(R)) <= dmax + 1e-13
         # the tracked residual diagonal is the diagonal of the residual matrix
         assert np.max(np.abs(np.diag(R) - r.D)) < 1e-13
-        # diagonal is non-increasing: the pivot diagonals never increase by more than roundoff
+        # every residual diagonal only loses a square per step (fl(D - L^2) <= D), so the
+        # pivot diagonals, the running maxima, never increase, exactly; the last is >= tau
         assert np.all(r.pivD > 0)
+        assert np.all(np.diff(r.pivD) <= 0.0)
+        assert r.pivD[-1] >= s.tau > dmax
 
 
 def test_density_fitting_route(s40, sp8):
